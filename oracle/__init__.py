@@ -1,0 +1,146 @@
+"""CPU oracle for protein database search by Smith-Waterman/Gotoh scoring.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
+CPU-baseline leg of the benchmark, never by the library.  It shares no code
+with the CUDA path; the only thing both sides consume is the seeded inputs
+of the ``synth`` module.
+
+- ``score`` / ``score_pairs`` / ``all_scores``: the Gotoh recurrences of
+  Section 2.2 (Smith-Waterman local alignment) with affine gaps as in the
+  experiments of Section 4.1, written out in plain C (``gotoh.c``), int64.
+- ``top_k``: the k best database entries of a score row, ordered by score
+  descending and then database index ascending (the paper is silent on ties;
+  this order is the reading this build takes).
+
+Parity of every function here is pinned by tests/test_oracle_pins.py
+(brute-force enumeration, textbook reductions, hand-worked examples,
+invariants).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gotoh.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libgotoh.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile gotoh.c with gcc into oracle/_build/libgotoh.so."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
+                               _SRC, "-o", tmp])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            p = ctypes.c_void_p
+            i64 = ctypes.c_int64
+            lib.swo_score.restype = i64
+            lib.swo_score.argtypes = [p, i64, p, i64, p, ctypes.c_int32, i64, i64]
+            lib.swo_score_pairs.restype = ctypes.c_int
+            lib.swo_score_pairs.argtypes = [p, p, p, p, p, p, i64, p, ctypes.c_int32, i64, i64,
+                                            ctypes.c_int, p]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _matrix(S) -> np.ndarray:
+    S = np.ascontiguousarray(S, dtype=np.int32)
+    assert S.ndim == 2 and S.shape[0] == S.shape[1]
+    return S
+
+
+def score(q, t, S, gap_open: int, gap_extend: int) -> int:
+    """Local alignment score of query q against target t (uint8 codes)."""
+    lib = _load()
+    q = np.ascontiguousarray(q, dtype=np.uint8)
+    t = np.ascontiguousarray(t, dtype=np.uint8)
+    S = _matrix(S)
+    A = S.shape[0]
+    if len(q) and int(q.max()) >= A or len(t) and int(t.max()) >= A:
+        raise ValueError("residue code outside the matrix")
+    r = lib.swo_score(_ptr(q), len(q), _ptr(t), len(t), _ptr(S), A, int(gap_open), int(gap_extend))
+    if r < 0:
+        raise MemoryError("oracle scratch allocation failed")
+    return int(r)
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+def score_pairs(queries, db, q_idx, t_idx, S, gap_open: int, gap_extend: int,
+                threads: int | None = None) -> np.ndarray:
+    """Scores of the pairs (queries.seq(q_idx[k]), db.seq(t_idx[k])) as int64."""
+    lib = _load()
+    S = _matrix(S)
+    q_idx = np.ascontiguousarray(q_idx, dtype=np.int64)
+    t_idx = np.ascontiguousarray(t_idx, dtype=np.int64)
+    assert q_idx.shape == t_idx.shape
+    qres = np.ascontiguousarray(queries.residues, dtype=np.uint8)
+    qoff = np.ascontiguousarray(queries.offsets, dtype=np.int64)
+    tres = np.ascontiguousarray(db.residues, dtype=np.uint8)
+    toff = np.ascontiguousarray(db.offsets, dtype=np.int64)
+    if len(q_idx) and (q_idx.min() < 0 or q_idx.max() >= len(qoff) - 1
+                       or t_idx.min() < 0 or t_idx.max() >= len(toff) - 1):
+        raise IndexError("pair index out of range")
+    A = S.shape[0]
+    if (len(qres) and int(qres.max()) >= A) or (len(tres) and int(tres.max()) >= A):
+        raise ValueError("residue code outside the matrix")
+    out = np.empty(len(q_idx), dtype=np.int64)
+    if len(q_idx) == 0:
+        return out
+    if qres.size == 0:
+        qres = np.zeros(1, np.uint8)
+    if tres.size == 0:
+        tres = np.zeros(1, np.uint8)
+    rc = lib.swo_score_pairs(_ptr(qres), _ptr(qoff), _ptr(q_idx), _ptr(tres), _ptr(toff),
+                             _ptr(t_idx), len(q_idx), _ptr(S), A, int(gap_open), int(gap_extend),
+                             int(threads or default_threads()), _ptr(out))
+    if rc != 0 or (out < 0).any():
+        raise MemoryError("oracle failed")
+    return out
+
+
+def all_scores(queries, db, S, gap_open: int, gap_extend: int,
+               threads: int | None = None) -> np.ndarray:
+    """(n_queries, n_db) matrix of scores, database in its original order."""
+    nq, nt = queries.n, db.n
+    qi = np.repeat(np.arange(nq, dtype=np.int64), nt)
+    ti = np.tile(np.arange(nt, dtype=np.int64), nq)
+    return score_pairs(queries, db, qi, ti, S, gap_open, gap_extend, threads).reshape(nq, nt)
+
+
+def top_k(scores_row, k: int):
+    """The k best entries of one query's score row.
+
+    Order: score descending, then database index ascending.  Returns
+    (scores, indices) as int64 arrays padded with -1 when k > len(row).
+    """
+    row = np.asarray(scores_row, dtype=np.int64)
+    order = np.lexsort((np.arange(len(row)), -row))[:k]
+    s = np.full(k, -1, dtype=np.int64)
+    i = np.full(k, -1, dtype=np.int64)
+    s[:len(order)] = row[order]
+    i[:len(order)] = order
+    return s, i

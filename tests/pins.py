@@ -1,0 +1,97 @@
+"""Independent checks the oracle is pinned to (no dynamic programming on H/E/F).
+
+Each function computes, by a different route, a quantity that the
+Smith-Waterman/Gotoh score (Section 2.2; affine gaps as in Section 4.1)
+must equal in a special case:
+
+- ``brute_force_local``: explicit enumeration of every local alignment of
+  every pair of substrings, each gap run priced open + (k-1)*extend.
+- ``lcs_length``: the textbook longest-common-subsequence DP (the score when
+  S is the identity and gaps are free).
+- ``longest_common_substring``: by direct comparison of all substring pairs
+  (the score when mismatches and gaps are prohibitively expensive).
+- ``best_diagonal_kadane``: Kadane's maximum subarray along every diagonal
+  (the score when gaps are prohibitively expensive).
+"""
+from __future__ import annotations
+
+import sys
+
+import numpy as np
+
+
+def brute_force_local(q, t, S, gap_open: int, gap_extend: int, reopen: bool = False) -> int:
+    """Maximum over all local alignments, enumerated one by one.
+
+    An alignment is a path of columns: M (q_i over t_j, scores S[q_i][t_j]),
+    X (q_i over a gap) and Y (a gap over t_j).  A maximal run of X (or Y)
+    columns of length k costs open + (k-1)*extend.  With ``reopen`` a run may
+    also be priced as several adjacent gaps (each continuing column costs
+    min(open, extend)), which is what the recurrences give when open < extend.
+    The empty alignment scores 0.
+    """
+    q = [int(x) for x in q]
+    t = [int(x) for x in t]
+    m, n = len(q), len(t)
+    best = 0
+    cont = min(gap_open, gap_extend) if reopen else gap_extend
+    sys.setrecursionlimit(max(1000, 10 * (m + n) + 100))
+
+    def dfs(i, j, last, score):
+        nonlocal best
+        if last is not None and score > best:
+            best = score
+        if i < m and j < n:
+            dfs(i + 1, j + 1, "M", score + int(S[q[i]][t[j]]))
+        if i < m:
+            dfs(i + 1, j, "X", score - (cont if last == "X" else gap_open))
+        if j < n:
+            dfs(i, j + 1, "Y", score - (cont if last == "Y" else gap_open))
+
+    for i0 in range(m + 1):
+        for j0 in range(n + 1):
+            dfs(i0, j0, None, 0)
+    return best
+
+
+def lcs_length(a, b) -> int:
+    """Classic LCS DP: L[i][j] = L[i-1][j-1] + 1 on a match, else the max of L[i-1][j], L[i][j-1]."""
+    a = list(a)
+    b = list(b)
+    L = [[0] * (len(b) + 1) for _ in range(len(a) + 1)]
+    for i in range(1, len(a) + 1):
+        for j in range(1, len(b) + 1):
+            if a[i - 1] == b[j - 1]:
+                L[i][j] = L[i - 1][j - 1] + 1
+            else:
+                L[i][j] = max(L[i - 1][j], L[i][j - 1])
+    return L[len(a)][len(b)]
+
+
+def longest_common_substring(a, b) -> int:
+    a = bytes(bytearray(int(x) for x in a))
+    b = bytes(bytearray(int(x) for x in b))
+    best = 0
+    for i in range(len(a)):
+        for k in range(best + 1, len(a) - i + 1):
+            if a[i:i + k] in b:
+                best = k
+            else:
+                break
+    return best
+
+
+def best_diagonal_kadane(q, t, S) -> int:
+    """max(0, max over diagonals of the maximum-sum contiguous run of S(q_i, t_{i+d}))."""
+    q = np.asarray(q, dtype=np.int64)
+    t = np.asarray(t, dtype=np.int64)
+    m, n = len(q), len(t)
+    best = 0
+    for d in range(-(m - 1), n):
+        run = 0
+        for i in range(m):
+            j = i + d
+            if 0 <= j < n:
+                run = max(0, run + int(S[q[i]][t[j]]))
+                best = max(best, run)
+    return best
