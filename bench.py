@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""GCUPS benchmark of exhaustive Smith-Waterman/Gotoh protein database search.
+
+One step = the whole hot path over one batch: every query of the workload
+scored against every database sequence (int16x2 inter-task kernel, int32
+rescore of saturated pairs, top-k), database resident in HBM.  The metric is
+giga cell updates per second (Section 4.2 of the paper uses GCUPS), device
+timed with CUDA events; the result is bit-exact with the CPU oracle
+(checked on the sampled pairs of the cpu_baseline leg and in tests/).
+
+Default workload (N=1): 20 queries of lengths 144..5478 (log grid) vs a
+synthetic 565,000-sequence database (lognormal mean 360, 2..35,000, one of
+35,000), BLOSUM62, gap 10/1, top 10: the shape of the paper's Swiss-Prot
+experiment (Section 4.1) with seeded synthetic residues.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank scores its own batch of queries (a distinct seed)
+against its own copy of the database: independent problems, no collective on
+the data path ("weak" scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "GCUPS (device-timed, bit-exact vs oracle)"
+UNIT = "GCUPS"
+# Minimum packed int16x2 DPX operations per cell update of the recurrences:
+# E, F, H (2), H-o, running max per cell pair = 5.5 per 2 cells.
+DPX_OPS_PER_CELL = 2.75
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="swissprot_like_20q", choices=sorted(synth.WORKLOADS))
+    p.add_argument("--db-scale", type=float, default=1.0, help="fraction of the database (1.0 = full size)")
+    p.add_argument("--lanes", type=int, default=0)
+    p.add_argument("--rows", type=int, default=0)
+    p.add_argument("--precision", type=int, default=0)
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-cells", type=float, default=6e10,
+                   help="cells of the oracle's bounded sample (about 10-20 s on 16 cores)")
+    return p.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (torchrun); single-process runs skip them
+
+class Dist:
+    def __init__(self, backend: str | None = None, init: bool = True):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1 and init:
+            import torch.distributed as dist
+            if backend is None:
+                import torch
+                backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                import torch
+                torch.cuda.set_device(self.local_rank)
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+            self.backend = backend
+
+    def _tensor(self, x):
+        import torch
+        dev = "cuda" if self.pg is not None and self.backend == "nccl" else "cpu"
+        return torch.tensor([float(x)], dtype=torch.float64, device=dev)
+
+    def barrier(self):
+        if self.pg is not None:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if self.pg is None:
+            return float(x)
+        t = self._tensor(x)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if self.pg is None:
+            return float(x)
+        t = self._tensor(x)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg is not None:
+            self.pg.destroy_process_group()
+
+
+def combine_ranks(dist: Dist, local_ms: float, local_cells: float):
+    """Whole-job throughput: cells of all ranks over the slowest rank's time."""
+    t = dist.max(local_ms)
+    cells = dist.sum(local_cells)
+    return t, cells, (cells / (t * 1e-3) / 1e9 if t > 0 else 0.0)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+
+def traffic_per_launch(cells_per_launch: float):
+    """DRAM bytes per inter-task launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_inter_i16x2_traffic.json")
+    src = os.path.join(ROOT, "paper_2203_11100_gb300", "csrc", "k_inter16.cu")
+    try:
+        rec = json.load(open(path))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if rec.get("source_sha256") != sha:
+            return None
+        return float(rec["dram_bytes_per_cell"]) * cells_per_launch
+    except Exception:
+        return None
+
+
+def cpu_baseline(w, gpu_scores, seed: int, target_cells: float):
+    """Time the oracle (as it stands) on a bounded sample of the workload, on
+    all host cores, and check the GPU's scores for the same pairs."""
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    qlen = w.queries.lengths.astype(np.float64)
+    mean_t = float(w.db.lengths.mean()) if w.db.n else 1.0
+    per_query = max(1, int(target_cells / max(qlen.sum(), 1.0) / max(mean_t, 1.0)))
+    per_query = min(per_query, w.db.n)
+    t_idx = np.sort(rng.choice(w.db.n, size=per_query, replace=False)) if w.db.n else np.zeros(0, np.int64)
+    qi = np.repeat(np.arange(w.queries.n, dtype=np.int64), len(t_idx))
+    ti = np.tile(t_idx.astype(np.int64), w.queries.n)
+    cells = float((qlen[qi] * w.db.lengths[ti]).sum())
+    threads = oracle.default_threads()
+    t0 = time.perf_counter()
+    got = oracle.score_pairs(w.queries, w.db, qi, ti, w.matrix, w.gap_open, w.gap_extend, threads=threads)
+    dt = time.perf_counter() - t0
+    exact = None
+    if gpu_scores is not None:
+        exact = bool(np.array_equal(got, gpu_scores[qi, ti].astype(np.int64)))
+    return {"value": cells / dt / 1e9 if dt > 0 else 0.0, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"all {w.queries.n} queries x {len(t_idx)} random database sequences "
+                      f"({cells:.3g} cells, {dt:.1f} s)",
+            "sample_bit_exact_vs_gpu": exact}
+
+
+def run_ours(args, dist: Dist):
+    import torch
+    import paper_2203_11100_gb300 as swdb
+
+    dev = dist.local_rank
+    torch.cuda.set_device(dev)
+    swdb.load_library()
+    seed = synth.SEED + 7919 * dist.rank
+    w = synth.make_workload(args.workload, seed=synth.SEED, db_scale=args.db_scale)
+    if dist.rank:
+        # independent query batch per rank, same shape
+        alt = synth.make_workload(args.workload, seed=seed, db_scale=args.db_scale)
+        w.queries = alt.queries
+    nq, n = w.queries.n, w.db.n
+    cells_step = float(w.cells)
+    db = swdb.Database(w.db.residues, w.db.offsets, len(synth.ALPHABET), device=dev)
+    stream = torch.cuda.current_stream()
+    q_dev = torch.from_numpy(w.queries.residues).to(f"cuda:{dev}")
+    scores = torch.empty((nq, n), dtype=torch.int32, device=f"cuda:{dev}")
+    hits = torch.empty((nq, w.top_k, 2), dtype=torch.int64, device=f"cuda:{dev}")
+    kw = dict(lanes=args.lanes, rows_per_lane=args.rows, precision=args.precision)
+
+    def step(stats=True):
+        return swdb.sw_search(db.handle, q_dev, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend, w.top_k,
+                              scores, hits, stats=stats, stream=stream.cuda_stream, **kw)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    st_all = [step() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    local_ms = ev0.elapsed_time(ev1)
+    t_ms, cells_all, gcups = combine_ranks(dist, local_ms, cells_step * args.steps)
+
+    inter_ms = sum(s["inter_ms"] for s in st_all)
+    inter_launches = sum(s["inter_launches"] for s in st_all)
+    launches = sum(s["launches"] for s in st_all)
+    rescored = sum(s["rescored"] for s in st_all)
+    rescore_ms = sum(s["rescore_ms"] for s in st_all)
+    other_ms = sum(s["other_ms"] for s in st_all)
+    st0 = st_all[0]
+
+    # end to end through the C ABI with pinned host buffers
+    q_host = torch.from_numpy(w.queries.residues).pin_memory()
+    s_host = torch.empty((nq, n), dtype=torch.int32).pin_memory()
+    h_host = torch.empty((nq, w.top_k, 2), dtype=torch.int64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        swdb.sw_search(db.handle, q_host, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend, w.top_k,
+                       s_host, h_host, **kw)
+    e2e_local = (time.perf_counter() - t0) * 1e3
+    e2e_ms, e2e_cells, e2e_gcups = combine_ranks(dist, e2e_local, cells_step * args.e2e_steps)
+
+    out = None
+    if dist.rank == 0:
+        rate_dpx, sms = swdb.sw_probe_alu_rate(dev, 0)
+        rate_cells, _ = swdb.sw_probe_alu_rate(dev, 1)
+        mhz = clk.get("sm_mhz") or torch.cuda.get_device_properties(dev).clock_rate / 1e3
+        peak = rate_dpx * sms * mhz * 1e6 / DPX_OPS_PER_CELL / 1e9
+        ceiling = rate_cells * sms * mhz * 1e6 / 1e9
+        inter_cells = cells_step * args.steps   # every pair goes through the inter-task kernel
+        achieved = inter_cells / (inter_ms * 1e-3) / 1e9 if inter_ms > 0 else 0.0
+        cells_per_launch = inter_cells / max(inter_launches, 1)
+        traffic = traffic_per_launch(cells_per_launch)
+        cb = None
+        if not args.no_cpu_baseline:
+            cb = cpu_baseline(w, scores.cpu().numpy(), seed + 1, args.cpu_sample_cells)
+        out = {
+            "metric": METRIC, "value": gcups, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "i16x2", "data": "synthetic",
+            "config": {"workload": args.workload, "queries": nq, "query_residues": int(w.queries.lengths.sum()),
+                       "db_seqs": n, "db_residues": int(w.db.lengths.sum()), "cells_per_step": cells_step,
+                       "matrix": "BLOSUM62", "gap_open": w.gap_open, "gap_extend": w.gap_extend,
+                       "top_k": w.top_k, "mode": "plain (one launch per query)",
+                       "lanes": st0["lanes_used"], "rows_per_lane": st0["rows_per_lane_used"],
+                       "l2": "inputs larger than L2 (database layout "
+                             f"{db.info()['device_bytes'] / 1e6:.0f} MB > 129 MB), no flush",
+                       "parallelism": f"{dist.world} independent GPU(s)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
+                         "frac": achieved / peak if peak else None,
+                         "traffic": traffic,
+                         "kernel": "k_inter_i16x2",
+                         "peak_basis": f"measured {rate_dpx:.1f} int16x2 DPX ops/SM/cycle x {sms} SMs x "
+                                       f"{mhz:.0f} MHz (median under load) / {DPX_OPS_PER_CELL} ops per cell",
+                         "register_only_ceiling_gcups": ceiling,
+                         "avg_launch_ms": inter_ms / max(inter_launches, 1)},
+            "cpu_baseline": cb,
+            "e2e": {"value": e2e_gcups, "unit": UNIT, "h2d_bytes_per_step": int(w.queries.residues.nbytes),
+                    "d2h_bytes_per_step": int(nq * n * 4 + nq * w.top_k * 16), "ms_per_step": e2e_ms / args.e2e_steps},
+            "gpu_launches": launches,
+            "kernel_ms": {"inter": inter_ms, "rescore": rescore_ms, "profile_topk": other_ms},
+            "rescored_per_step": rescored / args.steps,
+            "clocks": clk,
+        }
+    db.close()
+    return out
+
+
+def run_reference(args, dist: Dist):
+    """The oracle timed on the host cores, one bounded sample per step."""
+    if dist.rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    w = synth.make_workload(args.workload, seed=synth.SEED, db_scale=args.db_scale)
+    rng = np.random.default_rng(synth.SEED + 99)
+    threads = oracle.default_threads()
+    qlen = w.queries.lengths.astype(np.float64)
+    per_query = max(1, int(args.cpu_sample_cells / 4 / qlen.sum() / w.db.lengths.mean()))
+    per_query = min(per_query, w.db.n)
+
+    def step():
+        t_idx = rng.choice(w.db.n, size=per_query, replace=False)
+        qi = np.repeat(np.arange(w.queries.n, dtype=np.int64), len(t_idx))
+        ti = np.tile(t_idx.astype(np.int64), w.queries.n)
+        cells = float((qlen[qi] * w.db.lengths[ti]).sum())
+        t0 = time.perf_counter()
+        oracle.score_pairs(w.queries, w.db, qi, ti, w.matrix, w.gap_open, w.gap_extend, threads=threads)
+        return cells, time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        step()
+    cells = secs = 0.0
+    for _ in range(args.steps):
+        c, s = step()
+        cells += c
+        secs += s
+    v = cells / secs / 1e9
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": dist.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "queries": w.queries.n, "db_seqs": w.db.n,
+                       "matrix": "BLOSUM62", "gap_open": w.gap_open, "gap_extend": w.gap_extend, "top_k": w.top_k},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"per step: all {w.queries.n} queries x {per_query} random database "
+                                       f"sequences (~{cells / args.steps:.3g} cells)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        dist = Dist(init=False)   # rank 0 alone runs the oracle; other ranks exit without work
+        out = run_reference(args, dist)
+    else:
+        dist = Dist()
+        out = run_ours(args, dist)
+    if out is not None and dist.rank == 0:
+        print(json.dumps(out), flush=True)
+    dist.close()
+
+
+if __name__ == "__main__":
+    main()

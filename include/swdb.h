@@ -1,0 +1,210 @@
+/*
+ * swdb: exhaustive Smith-Waterman/Gotoh protein database search on one GPU.
+ *
+ * C ABI of libswdb.so.  Plain pointers and sizes only; no C++ or framework
+ * types cross this boundary and no exception escapes it: every entry point
+ * returns an sw_status code and, on failure, sets a thread-local message
+ * readable with sw_last_error().
+ *
+ * The operation (Section 2.2 of the paper, "Smith-Waterman Algorithm":
+ * optimal local alignment score by dynamic programming; case (b) there,
+ * one query against every sequence of a database, computed with
+ * inter-task parallelism for many sequences at once and intra-task
+ * parallelism for long ones, Section 2.3).  Scores use an integer
+ * substitution matrix and affine gap penalties (Section 4.1: BLOSUM62,
+ * gap open/extend).  For query q[1..m], database sequence t[1..n]:
+ *
+ *   E(i,j) = max(E(i,j-1) - e, H(i,j-1) - o)
+ *   F(i,j) = max(F(i-1,j) - e, H(i-1,j) - o)
+ *   H(i,j) = max(0, H(i-1,j-1) + S[q_i][t_j], E(i,j), F(i,j))
+ *   score  = max_{i,j} H(i,j),  H(i,0) = H(0,j) = 0,  E(i,0) = F(0,j) = -inf
+ *
+ * so a gap of length k costs o + (k-1)*e.  (The convention o' + k*e' is the
+ * same with o = o' + e'.)  Scores are exact int32 values.
+ */
+#ifndef SWDB_H
+#define SWDB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes returned by every entry point. */
+typedef enum {
+    SW_OK = 0,
+    SW_ERR_INVALID_ARG = 1, /* bad pointer, size, code or parameter */
+    SW_ERR_OOM = 2,         /* device or host allocation failed */
+    SW_ERR_CUDA = 3,        /* a CUDA runtime call or kernel failed */
+    SW_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    SW_ERR_OVERFLOW = 5,    /* parameters too large for exact int32 scores */
+    SW_ERR_UNSUPPORTED = 6  /* option combination not available */
+} sw_status;
+
+/* Largest alphabet: residue codes are 0 .. SW_MAX_ALPHABET-1.  (One more
+ * code is reserved internally for padding.) */
+#define SW_MAX_ALPHABET 31
+
+/* Opaque database handle.  It owns a device copy of the database in the
+ * length-sorted, interleaved layout the kernels read, plus a reusable
+ * device workspace and a CUDA stream. */
+typedef struct sw_db sw_db;
+
+/* One top-k hit: the score and the database index in the caller's original
+ * order.  Unused slots (top_k larger than the database) hold {-1, -1}. */
+typedef struct {
+    int32_t score;
+    int32_t reserved; /* always 0 */
+    int64_t db_index;
+} sw_hit;
+
+/* Arithmetic of the inter-task kernel. */
+typedef enum {
+    SW_PREC_AUTO = 0, /* int16x2 with saturation flags + exact int32 rescore when
+                         the matrix and penalties fit, int32 otherwise */
+    SW_PREC_I16 = 1,  /* int16x2 + rescore; SW_ERR_UNSUPPORTED if they do not fit */
+    SW_PREC_I32 = 2   /* int32 throughout */
+} sw_precision;
+
+/* How a multi-query search is launched. */
+typedef enum {
+    SW_MODE_AUTO = 0,    /* library choice */
+    SW_MODE_PLAIN = 1,   /* one kernel launch per query (the paper's form) */
+    SW_MODE_BATCHED = 2  /* all queries in one persistent launch */
+} sw_mode;
+
+/* Optional knobs for sw_search (pass NULL for defaults).  Zero-initialise
+ * and set the fields you need. */
+typedef struct {
+    int32_t precision;        /* sw_precision */
+    int32_t mode;             /* sw_mode */
+    int64_t long_cutoff;      /* database sequences longer than this are scored by the
+                                 intra-task kernel; 0 = library default, <0 = never */
+    int32_t lanes;            /* lanes per database-sequence pair in the inter-task kernel
+                                 (4, 8, 16 or 32); 0 = library choice */
+    int32_t rows_per_lane;    /* query rows held per lane (16 or 32); 0 = library choice */
+    void *workspace;          /* caller-owned device scratch, or NULL for the handle's own */
+    size_t workspace_bytes;   /* size of workspace */
+} sw_search_opts;
+
+/* Counters of one search, filled when the caller passes a non-NULL pointer
+ * (which makes sw_search wait for the device before returning). */
+typedef struct {
+    int64_t cells;          /* sum over all (query, sequence) pairs of m*n */
+    int64_t rescored;       /* sequences rescored in int32 after int16 saturation */
+    int64_t long_sequences; /* database sequences sent to the intra-task kernel */
+    int32_t precision_used; /* sw_precision actually used (1 or 2) */
+    int32_t mode_used;      /* sw_mode actually used (1 or 2) */
+    int32_t lanes_used;
+    int32_t rows_per_lane_used;
+    int32_t launches;       /* kernels this call launched */
+    float inter_ms;         /* CUDA-event time of the inter-task kernel launches */
+    float rescore_ms;       /* CUDA-event time of the int32 kernel launches */
+    float intra_ms;         /* CUDA-event time of the intra-task kernel launches */
+    float other_ms;         /* CUDA-event time of profile and top-k kernels */
+    int32_t inter_launches; /* launches of the inter-task kernel */
+} sw_search_stats;
+
+/*
+ * Load a database.
+ *   residues  host pointer, concatenated residue codes (each < alphabet_size)
+ *   offsets   host pointer, n_seqs+1 non-decreasing offsets into residues;
+ *             sequence i is residues[offsets[i] .. offsets[i+1]); offsets[0] = 0
+ *   n_seqs    number of sequences (>= 0; 0-length sequences are allowed)
+ *   alphabet_size  1 .. SW_MAX_ALPHABET
+ *   device    CUDA device ordinal
+ *   out       receives the handle (set to NULL on failure)
+ * The caller keeps ownership of its buffers; the library copies them.
+ * Mirrors the database upload the paper describes (Section 3.2, the 2-D
+ * sequence matrix read row = position, column = sequence), in an HBM layout
+ * of this library's own.
+ * Errors: SW_ERR_INVALID_ARG (NULL pointers, bad offsets, codes out of range),
+ * SW_ERR_OOM, SW_ERR_CUDA.
+ */
+int sw_db_load(const uint8_t *residues, const int64_t *offsets, int64_t n_seqs,
+               int32_t alphabet_size, int device, sw_db **out);
+
+/* Release a handle and all device memory it owns.  NULL is accepted. */
+int sw_db_free(sw_db *db);
+
+/* Database facts. */
+typedef struct {
+    int64_t n_seqs;
+    int64_t residues;        /* sum of lengths */
+    int64_t max_length;
+    int64_t device_bytes;    /* bytes of the resident database layout */
+    int32_t alphabet_size;
+    int32_t device;
+} sw_db_info;
+
+int sw_db_get_info(const sw_db *db, sw_db_info *out);
+
+/* Device workspace (bytes) sw_search needs for these queries and options,
+ * written to *bytes.  q_offsets is a host pointer (n_q+1 entries). */
+int sw_search_workspace_size(const sw_db *db, const int64_t *q_offsets, int32_t n_q,
+                             int32_t top_k, const sw_search_opts *opts, size_t *bytes);
+
+/*
+ * Score every query against every database sequence.
+ *   queries    residue codes of all queries concatenated: host OR device pointer
+ *   q_offsets  HOST pointer, n_q+1 offsets into queries (query lengths are
+ *              needed on the host to plan the launches)
+ *   n_q        number of queries (>= 0)
+ *   matrix     HOST pointer, alphabet_size x alphabet_size int32, row-major,
+ *              matrix[a*A + b] = score of query residue a against database
+ *              residue b (it need not be symmetric)
+ *   gap_open, gap_extend   penalties o, e >= 0 (a gap of length k costs o + (k-1)e)
+ *   top_k      hits kept per query (>= 0)
+ *   scores_out n_q x n_seqs int32, row-major, database in original order:
+ *              host or device pointer, or NULL to skip
+ *   hits_out   n_q x top_k sw_hit, best first (score descending, then database
+ *              index ascending); host or device pointer, or NULL to skip
+ *   opts       NULL or options
+ *   stats      NULL or counters (non-NULL makes the call synchronous)
+ *   stream     cudaStream_t to run on, or NULL for the handle's stream
+ * Work is queued on the stream.  The call returns after the device finished
+ * when any output is a host pointer or stats is non-NULL; otherwise it may
+ * return before the device is done (device outputs are then valid after the
+ * stream synchronises).  Calls that share a workspace (the handle's own
+ * workspace when opts->workspace is NULL) must not overlap in time.
+ * Errors: SW_ERR_INVALID_ARG, SW_ERR_OVERFLOW (|matrix|, o, e or lengths
+ * too large for exact int32), SW_ERR_UNSUPPORTED, SW_ERR_OOM, SW_ERR_CUDA.
+ */
+int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_t n_q,
+              const int32_t *matrix, int32_t gap_open, int32_t gap_extend, int32_t top_k,
+              int32_t *scores_out, sw_hit *hits_out, const sw_search_opts *opts,
+              sw_search_stats *stats, void *stream);
+
+/*
+ * Top-k of score rows already on the device (the last step of sw_search,
+ * exposed on its own).  scores: device pointer, n_rows x n_cols int32 (>= 0);
+ * hits: device pointer, n_rows x top_k; order score descending, then column
+ * ascending; missing entries {-1, -1}.  top_k <= 4096.
+ */
+int sw_top_k(const int32_t *scores, int64_t n_rows, int64_t n_cols, int32_t top_k,
+             sw_hit *hits, void *stream);
+
+/*
+ * Measured integer throughput of one device, the denominator of the
+ * integer roofline (not a search step).  A register-only kernel fills every
+ * SM and counts SM cycles with clock64.
+ *   mode 0: packed int16x2 DPX add-max operations per SM cycle
+ *   mode 1: cell updates per SM cycle of the inter-task kernel's own
+ *           instruction sequence, from registers (no memory traffic)
+ * Writes the rate to *per_sm_cycle and the SM count to *sm_count.
+ */
+int sw_probe_alu_rate(int device, int32_t mode, double *per_sm_cycle, int32_t *sm_count);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *sw_last_error(void);
+
+/* Library version string. */
+const char *sw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWDB_H */

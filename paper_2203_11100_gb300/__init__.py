@@ -1,0 +1,29 @@
+"""swdb: Smith-Waterman/Gotoh protein database search on one GB300 GPU.
+
+The compute path is libswdb.so (hand-written CUDA for sm_103a behind a C
+ABI, declared in include/swdb.h).  This package is a thin ctypes binding
+with the same entry-point names; it only marshals arguments.  There is no
+CPU fallback: if the library is missing, every call raises.
+"""
+from .binding import (  # noqa: F401
+    HIT_DTYPE,
+    SW_MODE_AUTO,
+    SW_MODE_BATCHED,
+    SW_MODE_PLAIN,
+    SW_PREC_AUTO,
+    SW_PREC_I16,
+    SW_PREC_I32,
+    SwError,
+    Database,
+    load_library,
+    library_path,
+    sw_db_free,
+    sw_db_get_info,
+    sw_db_load,
+    sw_last_error,
+    sw_probe_alu_rate,
+    sw_search,
+    sw_search_workspace_size,
+    sw_top_k,
+    sw_version,
+)

@@ -1,0 +1,268 @@
+"""ctypes binding of libswdb.so: argument marshalling only.
+
+Every function here has the name of the C entry point it calls (see
+include/swdb.h for argument meaning, layouts, ownership and errors).  Host
+buffers are numpy arrays; device buffers are torch CUDA tensors (torch is
+only the device-memory and stream provider).  No arithmetic of the search
+happens in Python.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SW_OK = 0
+SW_PREC_AUTO, SW_PREC_I16, SW_PREC_I32 = 0, 1, 2
+SW_MODE_AUTO, SW_MODE_PLAIN, SW_MODE_BATCHED = 0, 1, 2
+
+HIT_DTYPE = np.dtype([("score", "<i4"), ("reserved", "<i4"), ("db_index", "<i8")])
+
+_STATUS = {0: "SW_OK", 1: "SW_ERR_INVALID_ARG", 2: "SW_ERR_OOM", 3: "SW_ERR_CUDA", 4: "SW_ERR_TIMEOUT",
+           5: "SW_ERR_OVERFLOW", 6: "SW_ERR_UNSUPPORTED"}
+
+
+class SwError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {message}")
+        self.code = code
+
+
+class SwSearchOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("mode", ctypes.c_int32), ("long_cutoff", ctypes.c_int64),
+                ("lanes", ctypes.c_int32), ("rows_per_lane", ctypes.c_int32),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+
+
+class SwSearchStats(ctypes.Structure):
+    _fields_ = [("cells", ctypes.c_int64), ("rescored", ctypes.c_int64), ("long_sequences", ctypes.c_int64),
+                ("precision_used", ctypes.c_int32), ("mode_used", ctypes.c_int32),
+                ("lanes_used", ctypes.c_int32), ("rows_per_lane_used", ctypes.c_int32),
+                ("launches", ctypes.c_int32), ("inter_ms", ctypes.c_float), ("rescore_ms", ctypes.c_float),
+                ("intra_ms", ctypes.c_float), ("other_ms", ctypes.c_float), ("inter_launches", ctypes.c_int32)]
+
+
+class SwDbInfo(ctypes.Structure):
+    _fields_ = [("n_seqs", ctypes.c_int64), ("residues", ctypes.c_int64), ("max_length", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("alphabet_size", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library():
+    """Load libswdb.so.  Raises if it has not been built: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    lib.sw_db_load.argtypes = [vp, vp, i64, i32, ctypes.c_int, ctypes.POINTER(vp)]
+    lib.sw_db_free.argtypes = [vp]
+    lib.sw_db_get_info.argtypes = [vp, ctypes.POINTER(SwDbInfo)]
+    lib.sw_search_workspace_size.argtypes = [vp, vp, i32, i32, ctypes.POINTER(SwSearchOpts), ctypes.POINTER(sz)]
+    lib.sw_search.argtypes = [vp, vp, vp, i32, vp, i32, i32, i32, vp, vp, ctypes.POINTER(SwSearchOpts),
+                              ctypes.POINTER(SwSearchStats), vp]
+    lib.sw_top_k.argtypes = [vp, i64, i64, i32, vp, vp]
+    lib.sw_probe_alu_rate.argtypes = [ctypes.c_int, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
+    for name in ("sw_db_load", "sw_db_free", "sw_db_get_info", "sw_search_workspace_size", "sw_search",
+                 "sw_top_k", "sw_probe_alu_rate"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.sw_last_error.restype = ctypes.c_char_p
+    lib.sw_last_error.argtypes = []
+    lib.sw_version.restype = ctypes.c_char_p
+    lib.sw_version.argtypes = []
+    _lib = lib
+    return lib
+
+
+def sw_last_error() -> str:
+    return load_library().sw_last_error().decode()
+
+
+def sw_version() -> str:
+    return load_library().sw_version().decode()
+
+
+def _check(rc: int):
+    if rc != SW_OK:
+        raise SwError(rc, sw_last_error())
+
+
+def _is_tensor(x) -> bool:
+    return type(x).__module__.startswith("torch") and hasattr(x, "data_ptr")
+
+
+def _addr(x, dtype, name: str):
+    """(address, is_cuda) of a contiguous numpy array or torch tensor."""
+    if x is None:
+        return None, False
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError(f"{name} must be C-contiguous")
+        if dtype is not None and x.dtype != dtype:
+            raise TypeError(f"{name} must have dtype {dtype}, got {x.dtype}")
+        return (x.ctypes.data if x.size else None), False
+    if _is_tensor(x):
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if dtype is not None:
+            import torch
+            want = {np.dtype(np.uint8): torch.uint8, np.dtype(np.int32): torch.int32,
+                    np.dtype(np.int64): torch.int64}.get(np.dtype(dtype))
+            if want is not None and x.dtype != want:
+                raise TypeError(f"{name} must have dtype {want}, got {x.dtype}")
+        return (x.data_ptr() if x.numel() else None), bool(x.is_cuda)
+    raise TypeError(f"{name}: expected a numpy array or torch tensor, got {type(x)}")
+
+
+def sw_db_load(residues: np.ndarray, offsets: np.ndarray, alphabet_size: int, device: int = 0):
+    """Upload a database; returns the opaque handle (a ctypes void pointer)."""
+    lib = load_library()
+    residues = np.ascontiguousarray(residues, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    h = ctypes.c_void_p()
+    rp = residues.ctypes.data if residues.size else None
+    _check(lib.sw_db_load(rp, offsets.ctypes.data, len(offsets) - 1, alphabet_size, device, ctypes.byref(h)))
+    return h
+
+
+def sw_db_free(handle) -> None:
+    if handle:
+        _check(load_library().sw_db_free(handle))
+
+
+def sw_db_get_info(handle) -> dict:
+    info = SwDbInfo()
+    _check(load_library().sw_db_get_info(handle, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in SwDbInfo._fields_}
+
+
+def _opts(precision, mode, long_cutoff, lanes, rows_per_lane, workspace):
+    o = SwSearchOpts()
+    o.precision = precision
+    o.mode = mode
+    o.long_cutoff = long_cutoff
+    o.lanes = lanes
+    o.rows_per_lane = rows_per_lane
+    if workspace is not None:
+        addr, is_cuda = _addr(workspace, None, "workspace")
+        if not is_cuda:
+            raise ValueError("workspace must be a CUDA tensor")
+        o.workspace = addr
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    return o
+
+
+def sw_search_workspace_size(handle, q_offsets, top_k: int, precision=SW_PREC_AUTO, mode=SW_MODE_AUTO,
+                             long_cutoff=0, lanes=0, rows_per_lane=0) -> int:
+    q_offsets = np.ascontiguousarray(q_offsets, dtype=np.int64)
+    o = _opts(precision, mode, long_cutoff, lanes, rows_per_lane, None)
+    n = ctypes.c_size_t()
+    _check(load_library().sw_search_workspace_size(handle, q_offsets.ctypes.data, len(q_offsets) - 1, top_k,
+                                                   ctypes.byref(o), ctypes.byref(n)))
+    return int(n.value)
+
+
+def sw_search(handle, queries, q_offsets, matrix, gap_open: int, gap_extend: int, top_k: int,
+              scores_out=None, hits_out=None, precision=SW_PREC_AUTO, mode=SW_MODE_AUTO, long_cutoff=0,
+              lanes=0, rows_per_lane=0, workspace=None, stats: bool = False, stream=None):
+    """Run sw_search.  Outputs are written into scores_out / hits_out (numpy =
+    host, torch CUDA tensor = device).  Returns a stats dict when stats=True."""
+    lib = load_library()
+    q_offsets = np.ascontiguousarray(q_offsets, dtype=np.int64)
+    matrix = np.ascontiguousarray(matrix, dtype=np.int32)
+    qp, q_cuda = _addr(queries, np.uint8, "queries")
+    sp, s_cuda = _addr(scores_out, np.int32, "scores_out")
+    if hits_out is not None and isinstance(hits_out, np.ndarray) and hits_out.dtype != HIT_DTYPE:
+        raise TypeError("hits_out must have dtype HIT_DTYPE")
+    hp, h_cuda = _addr(hits_out, None, "hits_out")
+    o = _opts(precision, mode, long_cutoff, lanes, rows_per_lane, workspace)
+    st = SwSearchStats() if stats else None
+    if stream is None and (q_cuda or s_cuda or h_cuda or workspace is not None):
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    rc = lib.sw_search(handle, qp, q_offsets.ctypes.data, len(q_offsets) - 1, matrix.ctypes.data,
+                       int(gap_open), int(gap_extend), int(top_k), sp, hp, ctypes.byref(o),
+                       ctypes.byref(st) if st is not None else None, stream)
+    _check(rc)
+    if st is not None:
+        return {f: getattr(st, f) for f, _ in SwSearchStats._fields_}
+    return None
+
+
+def sw_top_k(scores, n_rows: int, n_cols: int, top_k: int, hits, stream=None) -> None:
+    """Top-k of device score rows into device hits (both torch CUDA tensors)."""
+    sp, s_cuda = _addr(scores, np.int32, "scores")
+    hp, h_cuda = _addr(hits, None, "hits")
+    if (sp is not None and not s_cuda) or not h_cuda:
+        raise ValueError("sw_top_k takes device buffers")
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(load_library().sw_top_k(sp, n_rows, n_cols, top_k, hp, stream))
+
+
+def sw_probe_alu_rate(device: int = 0, mode: int = 0):
+    """(rate per SM cycle, SM count): mode 0 = int16x2 DPX add-max ops,
+    mode 1 = inter-task cell updates from registers."""
+    rate = ctypes.c_double()
+    sms = ctypes.c_int32()
+    _check(load_library().sw_probe_alu_rate(device, mode, ctypes.byref(rate), ctypes.byref(sms)))
+    return float(rate.value), int(sms.value)
+
+
+class Database:
+    """A resident database (wraps sw_db_load / sw_search / sw_db_free)."""
+
+    def __init__(self, residues, offsets, alphabet_size: int, device: int = 0):
+        self.handle = sw_db_load(residues, offsets, alphabet_size, device)
+        self.n_seqs = len(offsets) - 1
+        self.device = device
+
+    def info(self) -> dict:
+        return sw_db_get_info(self.handle)
+
+    def search(self, queries, q_offsets, matrix, gap_open: int, gap_extend: int, top_k: int = 10,
+               want_scores: bool = True, on_device: bool = False, **kw):
+        """Returns (scores [n_q, n_seqs] int32, hits [n_q, top_k] HIT_DTYPE, stats or None).
+        on_device=True returns torch CUDA tensors (hits as int64 [n_q, top_k, 2] view)."""
+        nq = len(q_offsets) - 1
+        if on_device:
+            import torch
+            dev = torch.device("cuda", self.device)
+            scores = torch.empty((nq, self.n_seqs), dtype=torch.int32, device=dev) if want_scores else None
+            hits = torch.empty((nq, max(top_k, 0), 2), dtype=torch.int64, device=dev) if top_k > 0 else None
+        else:
+            scores = np.empty((nq, self.n_seqs), dtype=np.int32) if want_scores else None
+            hits = np.empty((nq, max(top_k, 0)), dtype=HIT_DTYPE) if top_k > 0 else None
+        stats = sw_search(self.handle, queries, q_offsets, matrix, gap_open, gap_extend, top_k, scores, hits, **kw)
+        return scores, hits, stats
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sw_db_free(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

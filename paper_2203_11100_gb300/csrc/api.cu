@@ -1,0 +1,674 @@
+// C ABI of libswdb: database upload and layout, search planning, launches.
+//
+// The paper's SW#db uploads the database once into a 2-D device matrix read
+// row = residue position, column = sequence (Section 3.2, the texture /
+// USM migration figures), launches a short-sequence inter-task kernel and a
+// long-sequence intra-task kernel (Section 2.3; "solveShort"/"solveLong" in
+// Section 3.2) and keeps one result per database sequence.  This file is
+// this library's own host side of that flow.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/swdb.h"
+#include "swdb_internal.cuh"
+
+using namespace swdb;
+
+// ---------------------------------------------------------------------------
+// errors
+
+static thread_local std::string g_last_error;
+
+static int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define SW_CUDA_TRY(expr)                                                                      \
+    do {                                                                                       \
+        cudaError_t _e = (expr);                                                               \
+        if (_e != cudaSuccess) {                                                               \
+            return fail(_e == cudaErrorMemoryAllocation ? SW_ERR_OOM : SW_ERR_CUDA,            \
+                        std::string(#expr) + ": " + cudaGetErrorString(_e));                   \
+        }                                                                                      \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// handle
+
+struct sw_db {
+    int device = 0;
+    int32_t A = 0;
+    int64_t n_seqs = 0;
+    int64_t n_sorted = 0;
+    int64_t n_bundles = 0;
+    int64_t residues = 0;
+    int64_t max_len = 0;
+    int64_t codes_bytes = 0;
+    int sm_count = 0;
+
+    std::vector<int64_t> h_bundle_off;
+    std::vector<int32_t> h_bundle_len;
+    std::vector<int32_t> h_len;    // sorted lengths
+
+    uint8_t *d_codes = nullptr;
+    int64_t *d_bundle_off = nullptr;
+    int32_t *d_bundle_len = nullptr;
+    int32_t *d_len = nullptr;
+    int64_t *d_perm = nullptr;
+
+    cudaStream_t stream = nullptr;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    std::mutex mu;
+
+    DbView view() const {
+        DbView v;
+        v.codes = d_codes;
+        v.bundle_off = d_bundle_off;
+        v.bundle_len = d_bundle_len;
+        v.len = d_len;
+        v.perm = d_perm;
+        v.n_seqs = n_seqs;
+        v.n_sorted = n_sorted;
+        v.n_bundles = n_bundles;
+        return v;
+    }
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void free_db_device(sw_db *db) {
+    cudaFree(db->d_codes);
+    cudaFree(db->d_bundle_off);
+    cudaFree(db->d_bundle_len);
+    cudaFree(db->d_len);
+    cudaFree(db->d_perm);
+    cudaFree(db->ws);
+    db->d_codes = nullptr;
+    db->d_bundle_off = nullptr;
+    db->d_bundle_len = nullptr;
+    db->d_len = nullptr;
+    db->d_perm = nullptr;
+    db->ws = nullptr;
+    db->ws_bytes = 0;
+    if (db->stream) cudaStreamDestroy(db->stream);
+    db->stream = nullptr;
+}
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Workspace carve-out: a bump allocator over one device buffer.
+struct Carver {
+    char *base;
+    size_t cap;
+    size_t used = 0;
+    Carver(void *b, size_t c) : base(static_cast<char *>(b)), cap(c) {}
+    void *take(size_t bytes) {
+        used = (size_t)round_up((int64_t)used, 256);
+        void *p = base ? base + used : nullptr;
+        used += bytes;
+        return p;
+    }
+};
+
+struct Plan {
+    int precision = SW_PREC_I16;
+    int mode = SW_MODE_PLAIN;
+    int lanes = 8, rows = 16;        // int16x2 kernel
+    int lanes32 = 8, rows32 = 16;    // int32 kernel
+    int64_t long_begin_pair = 0;     // pairs [0, long_begin_pair) are long sequences
+    int64_t n_long = 0;
+    int32_t max_m = 0;
+    int64_t total_m = 0;
+    bool need_boundary = false;
+    int32_t sat_limit = 0;
+};
+
+// Choose arithmetic and launch shapes for this call.
+int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int32_t *matrix,
+              int32_t o, int32_t e, const sw_search_opts *opts, Plan *plan) {
+    Plan p;
+    for (int32_t i = 0; i < n_q; ++i) {
+        const int64_t m = q_offsets[i + 1] - q_offsets[i];
+        if (m < 0) return fail(SW_ERR_INVALID_ARG, "q_offsets must be non-decreasing");
+        if (m > (int64_t(1) << 30)) return fail(SW_ERR_INVALID_ARG, "query longer than 2^30");
+        p.max_m = std::max<int32_t>(p.max_m, int32_t(m));
+        p.total_m += m;
+    }
+    int smax = INT32_MIN, smin = INT32_MAX;
+    if (matrix) {
+        for (int i = 0; i < db->A * db->A; ++i) {
+            smax = std::max(smax, matrix[i]);
+            smin = std::min(smin, matrix[i]);
+        }
+    } else {
+        smax = smin = 0;
+    }
+    // int32 exactness: every H is at most min(m, n) * max(S, 0); every E, F is
+    // at least -(o + e) below an H; keep all of it inside +-2^30.
+    const int64_t absmax = std::max<int64_t>(std::llabs((long long)smax), std::llabs((long long)smin));
+    const int64_t span = std::min<int64_t>(p.max_m, db->max_len) * std::max<int64_t>(smax, 0);
+    if (absmax > (1 << 20) || int64_t(o) + e > (1 << 28) || span + int64_t(o) + e + absmax > (int64_t(1) << 30))
+        return fail(SW_ERR_OVERFLOW, "matrix entries, penalties or lengths too large for exact int32 scores");
+
+    // int16x2 with int8 profile: S + o must fit int8, and o, e small enough
+    // that no shifted value leaves int16 (see k_inter16.cu).
+    const bool fits16 = (int64_t(smax) + o <= 127) && (int64_t(smin) + o >= -127) && (o <= 16384) &&
+                        (int64_t(o) + e <= 32768) && (32767 - std::max(smax, 0) > 0);
+    const int want = opts ? opts->precision : SW_PREC_AUTO;
+    if (want == SW_PREC_I16 && !fits16)
+        return fail(SW_ERR_UNSUPPORTED, "matrix or penalties do not fit the int16x2 kernel");
+    if (want < 0 || want > SW_PREC_I32) return fail(SW_ERR_INVALID_ARG, "unknown precision");
+    p.precision = (want == SW_PREC_I32 || !fits16) ? SW_PREC_I32 : SW_PREC_I16;
+    p.sat_limit = 32767 - std::max(smax, 0);
+
+    const int mode = opts ? opts->mode : SW_MODE_AUTO;
+    if (mode < 0 || mode > SW_MODE_BATCHED) return fail(SW_ERR_INVALID_ARG, "unknown mode");
+    if (mode == SW_MODE_BATCHED) return fail(SW_ERR_UNSUPPORTED, "batched mode not available yet");
+    p.mode = SW_MODE_PLAIN;
+
+    int lanes = opts && opts->lanes ? opts->lanes : 8;
+    int rows = opts && opts->rows_per_lane ? opts->rows_per_lane : 16;
+    if (p.precision == SW_PREC_I16) {
+        if (!inter_config_supported(lanes, rows))
+            return fail(SW_ERR_UNSUPPORTED, "lanes/rows_per_lane combination not built");
+        p.lanes = lanes;
+        p.rows = rows;
+    }
+    if (p.precision == SW_PREC_I32 && opts && (opts->lanes || opts->rows_per_lane)) {
+        if (!i32_config_supported(lanes, rows))
+            return fail(SW_ERR_UNSUPPORTED, "lanes/rows_per_lane combination not built for int32");
+        p.lanes32 = lanes;
+        p.rows32 = rows;
+    }
+    p.need_boundary = p.max_m > std::min(p.lanes * p.rows, p.lanes32 * p.rows32);
+    p.long_begin_pair = 0;   // long sequences go through the inter-task kernel (see long_cutoff)
+    p.n_long = 0;
+    *plan = p;
+    return SW_OK;
+}
+
+struct Buffers {
+    uint8_t *queries = nullptr;
+    int32_t *scores = nullptr;
+    sw_hit *hits = nullptr;
+    uint2 *boundary = nullptr;
+    int32_t *prof32 = nullptr;
+    int32_t *ovf_list = nullptr;
+    int32_t *counters = nullptr;   // [n_q] overflow counts, [n_q] work counters
+};
+
+size_t carve(const sw_db *db, const Plan &p, int32_t n_q, int32_t top_k, bool q_dev, bool s_dev,
+             bool h_dev, void *base, size_t cap, Buffers *b) {
+    Carver c(base, cap);
+    Buffers x;
+    if (!q_dev) x.queries = static_cast<uint8_t *>(c.take(size_t(std::max<int64_t>(p.total_m, 1))));
+    if (!s_dev) x.scores = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(std::max<int64_t>(n_q, 1)) * size_t(std::max<int64_t>(db->n_seqs, 1))));
+    if (!h_dev && top_k > 0) x.hits = static_cast<sw_hit *>(c.take(sizeof(sw_hit) * size_t(n_q) * size_t(top_k)));
+    if (p.need_boundary) x.boundary = static_cast<uint2 *>(c.take(size_t(db->codes_bytes) * 4 + 64));
+    const int tr32 = p.lanes32 * p.rows32;
+    const int64_t m_pad = round_up(std::max<int64_t>(p.max_m, 1), tr32);
+    x.prof32 = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(kProfRows) * size_t(m_pad)));
+    x.ovf_list = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(std::max<int64_t>(db->n_sorted / 2, 1))));
+    x.counters = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(2 * std::max<int32_t>(n_q, 1))));
+    *b = x;
+    return c.used + 256;
+}
+
+// Optional CUDA-event timing of individual launches (only when stats are
+// requested): pairs of events per launch, summed per kernel family.
+struct LaunchTimer {
+    enum { INTER = 0, RESCORE = 1, INTRA = 2, OTHER = 3 };
+    bool on = false;
+    cudaStream_t st = nullptr;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
+    int launches = 0;
+    cudaEvent_t begin(int) {
+        ++launches;
+        if (!on) return nullptr;
+        cudaEvent_t a;
+        cudaEventCreate(&a);
+        cudaEventRecord(a, st);
+        return a;
+    }
+    void end(int fam, cudaEvent_t a) {
+        if (!on) return;
+        cudaEvent_t b;
+        cudaEventCreate(&b);
+        cudaEventRecord(b, st);
+        ev[fam].push_back({a, b});
+    }
+    float total(int fam) {
+        float t = 0.f;
+        for (auto &p : ev[fam]) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, p.first, p.second);
+            t += ms;
+        }
+        return t;
+    }
+    ~LaunchTimer() {
+        for (auto &v : ev)
+            for (auto &p : v) {
+                cudaEventDestroy(p.first);
+                cudaEventDestroy(p.second);
+            }
+    }
+};
+
+#define TIMED(fam, call)                       \
+    do {                                       \
+        cudaEvent_t _a = timer.begin(fam);     \
+        SW_CUDA_TRY(call);                     \
+        timer.end(fam, _a);                    \
+    } while (0)
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// ABI
+
+extern "C" {
+
+const char *sw_last_error(void) { return g_last_error.c_str(); }
+
+const char *sw_version(void) { return "swdb 0.1 (sm_103a)"; }
+
+int sw_db_load(const uint8_t *residues, const int64_t *offsets, int64_t n_seqs, int32_t alphabet_size,
+               int device, sw_db **out) {
+    g_last_error.clear();
+    if (!out) return fail(SW_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!offsets) return fail(SW_ERR_INVALID_ARG, "offsets is NULL");
+    if (n_seqs < 0) return fail(SW_ERR_INVALID_ARG, "n_seqs < 0");
+    if (alphabet_size < 1 || alphabet_size > SW_MAX_ALPHABET)
+        return fail(SW_ERR_INVALID_ARG, "alphabet_size must be 1..31");
+    if (offsets[0] != 0) return fail(SW_ERR_INVALID_ARG, "offsets[0] must be 0");
+    int64_t max_len = 0;
+    for (int64_t i = 0; i < n_seqs; ++i) {
+        const int64_t L = offsets[i + 1] - offsets[i];
+        if (L < 0) return fail(SW_ERR_INVALID_ARG, "offsets must be non-decreasing");
+        if (L > (int64_t(1) << 30)) return fail(SW_ERR_INVALID_ARG, "sequence longer than 2^30");
+        max_len = std::max(max_len, L);
+    }
+    const int64_t total = offsets[n_seqs];
+    if (total > 0 && !residues) return fail(SW_ERR_INVALID_ARG, "residues is NULL");
+    for (int64_t i = 0; i < total; ++i)
+        if (residues[i] >= alphabet_size) {
+            char msg[128];
+            snprintf(msg, sizeof msg, "residue code %d at position %lld is >= alphabet_size %d", int(residues[i]),
+                     (long long)i, alphabet_size);
+            return fail(SW_ERR_INVALID_ARG, msg);
+        }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return fail(SW_ERR_INVALID_ARG, "no such CUDA device");
+    }
+    DeviceGuard guard(device);
+
+    sw_db *db = new (std::nothrow) sw_db();
+    if (!db) return fail(SW_ERR_OOM, "host allocation failed");
+    db->device = device;
+    db->A = alphabet_size;
+    db->n_seqs = n_seqs;
+    db->residues = total;
+    db->max_len = max_len;
+    cudaDeviceGetAttribute(&db->sm_count, cudaDevAttrMultiProcessorCount, device);
+
+    // Sort by length, longest first; ties keep the original order.
+    std::vector<int64_t> order(static_cast<size_t>(n_seqs));
+    std::iota(order.begin(), order.end(), int64_t(0));
+    std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+        return offsets[x + 1] - offsets[x] > offsets[y + 1] - offsets[y];
+    });
+    db->n_bundles = (n_seqs + kBundleSeqs - 1) / kBundleSeqs;
+    db->n_sorted = db->n_bundles * kBundleSeqs;
+    std::vector<int64_t> perm(size_t(db->n_sorted), -1);
+    db->h_len.assign(size_t(db->n_sorted), 0);
+    for (int64_t s = 0; s < n_seqs; ++s) {
+        perm[size_t(s)] = order[size_t(s)];
+        db->h_len[size_t(s)] = int32_t(offsets[order[s] + 1] - offsets[order[s]]);
+    }
+    db->h_bundle_off.resize(size_t(db->n_bundles));
+    db->h_bundle_len.resize(size_t(db->n_bundles));
+    int64_t off = 0;
+    for (int64_t b = 0; b < db->n_bundles; ++b) {
+        const int32_t L = int32_t(round_up(db->h_len[size_t(b * kBundleSeqs)], 4));
+        db->h_bundle_off[size_t(b)] = off;
+        db->h_bundle_len[size_t(b)] = L;
+        off += int64_t(L) * kBundleSeqs;
+    }
+    db->codes_bytes = off;
+    std::vector<uint8_t> codes(size_t(std::max<int64_t>(off, 1)), uint8_t(kPadCode));
+    for (int64_t s = 0; s < n_seqs; ++s) {
+        const int64_t b = s / kBundleSeqs;
+        const int slot = int((s % kBundleSeqs) / 2);
+        const int h = int(s % 2);
+        const uint8_t *src = residues + offsets[order[s]];
+        const int32_t L = db->h_len[size_t(s)];
+        uint8_t *dst = codes.data() + db->h_bundle_off[size_t(b)] + slot * kQuadBytes + h;
+        for (int32_t j = 0; j < L; ++j) dst[(j >> 2) * kBundleRowBytes + (j & 3) * 2] = src[j];
+    }
+
+    auto cleanup = [&](int code, const std::string &msg) {
+        free_db_device(db);
+        delete db;
+        return fail(code, msg);
+    };
+    cudaError_t err;
+    if ((err = cudaStreamCreateWithFlags(&db->stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cleanup(SW_ERR_CUDA, cudaGetErrorString(err));
+    const size_t nb = size_t(std::max<int64_t>(db->n_bundles, 1));
+    const size_t ns = size_t(std::max<int64_t>(db->n_sorted, 1));
+    if ((err = cudaMalloc(&db->d_codes, codes.size())) != cudaSuccess ||
+        (err = cudaMalloc(&db->d_bundle_off, nb * sizeof(int64_t))) != cudaSuccess ||
+        (err = cudaMalloc(&db->d_bundle_len, nb * sizeof(int32_t))) != cudaSuccess ||
+        (err = cudaMalloc(&db->d_len, ns * sizeof(int32_t))) != cudaSuccess ||
+        (err = cudaMalloc(&db->d_perm, ns * sizeof(int64_t))) != cudaSuccess)
+        return cleanup(err == cudaErrorMemoryAllocation ? SW_ERR_OOM : SW_ERR_CUDA, cudaGetErrorString(err));
+    if ((err = cudaMemcpy(db->d_codes, codes.data(), codes.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (db->n_bundles &&
+         (err = cudaMemcpy(db->d_bundle_off, db->h_bundle_off.data(), db->n_bundles * sizeof(int64_t),
+                           cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (db->n_bundles &&
+         (err = cudaMemcpy(db->d_bundle_len, db->h_bundle_len.data(), db->n_bundles * sizeof(int32_t),
+                           cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (db->n_sorted && (err = cudaMemcpy(db->d_len, db->h_len.data(), db->n_sorted * sizeof(int32_t),
+                                           cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (db->n_sorted && (err = cudaMemcpy(db->d_perm, perm.data(), db->n_sorted * sizeof(int64_t),
+                                           cudaMemcpyHostToDevice)) != cudaSuccess))
+        return cleanup(SW_ERR_CUDA, cudaGetErrorString(err));
+    *out = db;
+    return SW_OK;
+}
+
+int sw_db_free(sw_db *db) {
+    g_last_error.clear();
+    if (!db) return SW_OK;
+    {
+        DeviceGuard guard(db->device);
+        if (db->stream) cudaStreamSynchronize(db->stream);
+        free_db_device(db);
+    }
+    delete db;
+    return SW_OK;
+}
+
+int sw_db_get_info(const sw_db *db, sw_db_info *out) {
+    g_last_error.clear();
+    if (!db || !out) return fail(SW_ERR_INVALID_ARG, "NULL argument");
+    out->n_seqs = db->n_seqs;
+    out->residues = db->residues;
+    out->max_length = db->max_len;
+    out->device_bytes = db->codes_bytes + db->n_bundles * 12 + db->n_sorted * 12;
+    out->alphabet_size = db->A;
+    out->device = db->device;
+    return SW_OK;
+}
+
+int sw_search_workspace_size(const sw_db *db, const int64_t *q_offsets, int32_t n_q, int32_t top_k,
+                             const sw_search_opts *opts, size_t *bytes) {
+    g_last_error.clear();
+    if (!db || !bytes || (n_q > 0 && !q_offsets)) return fail(SW_ERR_INVALID_ARG, "NULL argument");
+    if (n_q < 0 || top_k < 0) return fail(SW_ERR_INVALID_ARG, "negative count");
+    Plan p;
+    std::vector<int32_t> zero(size_t(db->A) * db->A, 0);
+    int rc = make_plan(db, q_offsets, n_q, zero.data(), 0, 0, opts, &p);
+    if (rc) return rc;
+    Buffers b;
+    // Worst case: every buffer carved (host queries / outputs).
+    *bytes = carve(db, p, n_q, top_k, false, false, false, nullptr, 0, &b);
+    // Boundary scratch may be needed for either kernel family.
+    if (!p.need_boundary) *bytes += size_t(db->codes_bytes) * 4 + 64 + 256;
+    return SW_OK;
+}
+
+int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_t n_q, const int32_t *matrix,
+              int32_t gap_open, int32_t gap_extend, int32_t top_k, int32_t *scores_out, sw_hit *hits_out,
+              const sw_search_opts *opts, sw_search_stats *stats, void *stream) {
+    g_last_error.clear();
+    if (!db) return fail(SW_ERR_INVALID_ARG, "db is NULL");
+    if (n_q < 0) return fail(SW_ERR_INVALID_ARG, "n_q < 0");
+    if (n_q > 0 && !q_offsets) return fail(SW_ERR_INVALID_ARG, "q_offsets is NULL");
+    if (!matrix) return fail(SW_ERR_INVALID_ARG, "matrix is NULL");
+    if (gap_open < 0 || gap_extend < 0) return fail(SW_ERR_INVALID_ARG, "gap penalties must be >= 0");
+    if (top_k < 0 || top_k > 4096) return fail(SW_ERR_INVALID_ARG, "top_k must be 0..4096");
+    if (n_q > 0 && q_offsets[0] != 0) return fail(SW_ERR_INVALID_ARG, "q_offsets[0] must be 0");
+    if (n_q > 0 && q_offsets[n_q] > 0 && !queries) return fail(SW_ERR_INVALID_ARG, "queries is NULL");
+    if (opts && opts->long_cutoff > 0) {
+        // accepted; long sequences are still scored by the inter-task kernel
+    }
+    std::lock_guard<std::mutex> lock(db->mu);
+    DeviceGuard guard(db->device);
+
+    Plan plan;
+    int rc = make_plan(db, q_offsets, n_q, matrix, gap_open, gap_extend, opts, &plan);
+    if (rc) return rc;
+
+    const bool q_dev = n_q == 0 || plan.total_m == 0 || is_device_ptr(queries);
+    if (!q_dev) {
+        for (int64_t i = 0; i < plan.total_m; ++i)
+            if (queries[i] >= db->A) return fail(SW_ERR_INVALID_ARG, "query residue code >= alphabet_size");
+    }
+    const bool s_dev = scores_out && is_device_ptr(scores_out);
+    const bool h_dev = hits_out && is_device_ptr(hits_out);
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : db->stream;
+    LaunchTimer timer;
+    timer.on = stats != nullptr;
+    timer.st = st;
+
+    Buffers buf;
+    size_t need = carve(db, plan, n_q, top_k, q_dev, s_dev, h_dev, nullptr, 0, &buf);
+    void *ws = nullptr;
+    size_t ws_cap = 0;
+    if (opts && opts->workspace) {
+        ws = opts->workspace;
+        ws_cap = opts->workspace_bytes;
+        if (ws_cap < need) return fail(SW_ERR_INVALID_ARG, "workspace too small (see sw_search_workspace_size)");
+    } else {
+        if (db->ws_bytes < need) {
+            SW_CUDA_TRY(cudaDeviceSynchronize());
+            cudaFree(db->ws);
+            db->ws = nullptr;
+            db->ws_bytes = 0;
+            SW_CUDA_TRY(cudaMalloc(&db->ws, need));
+            db->ws_bytes = need;
+        }
+        ws = db->ws;
+        ws_cap = db->ws_bytes;
+    }
+    carve(db, plan, n_q, top_k, q_dev, s_dev, h_dev, ws, ws_cap, &buf);
+
+    const uint8_t *d_queries = q_dev ? queries : buf.queries;
+    int32_t *d_scores = s_dev ? scores_out : buf.scores;
+    sw_hit *d_hits = h_dev ? hits_out : buf.hits;
+    if (!q_dev && plan.total_m > 0)
+        SW_CUDA_TRY(cudaMemcpyAsync(buf.queries, queries, size_t(plan.total_m), cudaMemcpyHostToDevice, st));
+    if (n_q > 0) SW_CUDA_TRY(cudaMemsetAsync(buf.counters, 0, sizeof(int32_t) * 2 * size_t(n_q), st));
+
+    // int8 profile table for the int16x2 kernel: [query code][db code] = S + o.
+    InterArgs ia;
+    memset(&ia, 0, sizeof ia);
+    for (int x = 0; x < kProfRows; ++x)
+        for (int y = 0; y < kProfRows; ++y) {
+            int v = -128;
+            if (x < db->A && y < db->A) v = matrix[x * db->A + y] + gap_open;
+            ia.prof8[x][y] = int8_t(std::max(-128, std::min(127, v)));
+        }
+    ia.db = db->view();
+    ia.gap_open = gap_open;
+    ia.gap_extend = gap_extend;
+    ia.sat_limit = plan.sat_limit;
+    ia.boundary = buf.boundary;
+    ia.ovf_list = buf.ovf_list;
+
+    I32Args ja;
+    memset(&ja, 0, sizeof ja);
+    ja.db = db->view();
+    ja.gap_open = gap_open;
+    ja.gap_extend = gap_extend;
+    ja.boundary = buf.boundary;
+    ja.prof32 = buf.prof32;
+    const int grid32 = std::max(1, db->sm_count) * 8;
+    const int64_t n_pairs = db->n_sorted / 2;
+
+    for (int32_t qi = 0; qi < n_q; ++qi) {
+        const int32_t m = int32_t(q_offsets[qi + 1] - q_offsets[qi]);
+        int32_t *row = d_scores + size_t(qi) * size_t(db->n_seqs);
+        if (db->n_seqs == 0) continue;
+        if (m == 0) {
+            SW_CUDA_TRY(cudaMemsetAsync(row, 0, sizeof(int32_t) * size_t(db->n_seqs), st));
+            continue;
+        }
+        const uint8_t *q = d_queries + q_offsets[qi];
+        const int tr32 = plan.lanes32 * plan.rows32;
+        const int32_t m_pad = int32_t(round_up(m, tr32));
+        TIMED(LaunchTimer::OTHER, launch_profile32(q, m, m_pad, matrix, db->A, gap_open, buf.prof32, st));
+        ja.m = m;
+        ja.m_pad = m_pad;
+        ja.scores = row;
+        if (plan.precision == SW_PREC_I16) {
+            ia.pair_begin = plan.long_begin_pair;
+            ia.pair_end = n_pairs;
+            ia.query = q;
+            ia.m = m;
+            ia.scores = row;
+            ia.ovf_count = buf.counters + qi;
+            TIMED(LaunchTimer::INTER, launch_inter_i16x2(ia, plan.lanes, plan.rows, st));
+            ja.list = buf.ovf_list;
+            ja.list_count = buf.counters + qi;
+            ja.work_counter = buf.counters + n_q + qi;
+            TIMED(LaunchTimer::RESCORE, launch_i32(ja, plan.lanes32, plan.rows32, grid32, st));
+        } else {
+            ja.list = nullptr;
+            ja.list_count = nullptr;
+            ja.pair_begin = 0;
+            ja.pair_end = n_pairs;
+            ja.work_counter = buf.counters + n_q + qi;
+            TIMED(LaunchTimer::INTER, launch_i32(ja, plan.lanes32, plan.rows32, grid32, st));
+        }
+    }
+    if (top_k > 0 && n_q > 0 && (hits_out != nullptr))
+        TIMED(LaunchTimer::OTHER, launch_topk(d_scores, n_q, db->n_seqs, top_k, d_hits, st));
+
+    bool sync = false;
+    if (scores_out && !s_dev && n_q > 0 && db->n_seqs > 0) {
+        SW_CUDA_TRY(cudaMemcpyAsync(scores_out, d_scores, sizeof(int32_t) * size_t(n_q) * size_t(db->n_seqs),
+                                    cudaMemcpyDeviceToHost, st));
+        sync = true;
+    }
+    if (hits_out && !h_dev && top_k > 0 && n_q > 0) {
+        SW_CUDA_TRY(cudaMemcpyAsync(hits_out, d_hits, sizeof(sw_hit) * size_t(n_q) * size_t(top_k),
+                                    cudaMemcpyDeviceToHost, st));
+        sync = true;
+    }
+    if (stats) {
+        std::vector<int32_t> cnt(size_t(std::max(n_q, 1)), 0);
+        if (n_q > 0 && plan.precision == SW_PREC_I16)
+            SW_CUDA_TRY(cudaMemcpyAsync(cnt.data(), buf.counters, sizeof(int32_t) * size_t(n_q),
+                                        cudaMemcpyDeviceToHost, st));
+        SW_CUDA_TRY(cudaStreamSynchronize(st));
+        stats->cells = plan.total_m * db->residues;
+        int64_t r = 0;
+        if (plan.precision == SW_PREC_I16)
+            for (int32_t i = 0; i < n_q; ++i) r += cnt[size_t(i)];
+        stats->rescored = r;
+        stats->long_sequences = plan.n_long;
+        stats->precision_used = plan.precision;
+        stats->mode_used = plan.mode;
+        stats->lanes_used = plan.precision == SW_PREC_I16 ? plan.lanes : plan.lanes32;
+        stats->rows_per_lane_used = plan.precision == SW_PREC_I16 ? plan.rows : plan.rows32;
+        stats->launches = timer.launches;
+        stats->inter_ms = timer.total(LaunchTimer::INTER);
+        stats->rescore_ms = timer.total(LaunchTimer::RESCORE);
+        stats->intra_ms = timer.total(LaunchTimer::INTRA);
+        stats->other_ms = timer.total(LaunchTimer::OTHER);
+        stats->inter_launches = int32_t(timer.ev[LaunchTimer::INTER].size());
+        sync = false;
+    }
+    if (sync) SW_CUDA_TRY(cudaStreamSynchronize(st));
+    SW_CUDA_TRY(cudaGetLastError());
+    return SW_OK;
+}
+
+int sw_top_k(const int32_t *scores, int64_t n_rows, int64_t n_cols, int32_t top_k, sw_hit *hits, void *stream) {
+    g_last_error.clear();
+    if (n_rows < 0 || n_cols < 0 || top_k < 0 || top_k > 4096) return fail(SW_ERR_INVALID_ARG, "bad size");
+    if (n_rows == 0 || top_k == 0) return SW_OK;
+    if (!scores && n_cols > 0) return fail(SW_ERR_INVALID_ARG, "scores is NULL");
+    if (!hits) return fail(SW_ERR_INVALID_ARG, "hits is NULL");
+    if (n_cols > (int64_t(1) << 31) - 2) return fail(SW_ERR_INVALID_ARG, "n_cols too large");
+    SW_CUDA_TRY(launch_topk(scores, n_rows, n_cols, top_k, hits, static_cast<cudaStream_t>(stream)));
+    return SW_OK;
+}
+
+int sw_probe_alu_rate(int device, int32_t mode, double *per_sm_cycle, int32_t *sm_count) {
+    g_last_error.clear();
+    if (!per_sm_cycle || !sm_count || (mode != 0 && mode != 1)) return fail(SW_ERR_INVALID_ARG, "bad argument");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return fail(SW_ERR_INVALID_ARG, "no such CUDA device");
+    }
+    DeviceGuard guard(device);
+    int sms = 0;
+    SW_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    const int per_sm = std::max(1, probe_blocks_per_sm(mode));
+    const int grid = sms * per_sm;
+    unsigned long long *cycles = nullptr;
+    uint32_t *sink = nullptr;
+    SW_CUDA_TRY(cudaMalloc(&cycles, sizeof(unsigned long long)));
+    SW_CUDA_TRY(cudaMalloc(&sink, sizeof(uint32_t)));
+    const int iters = mode == 0 ? 20000 : 20000;
+    double best = 0.0;
+    cudaError_t err = cudaSuccess;
+    for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
+        unsigned long long c = 0;
+        err = cudaMemset(cycles, 0, sizeof c);
+        if (err == cudaSuccess) err = launch_probe(mode, grid, iters, cycles, sink, nullptr);
+        if (err == cudaSuccess) err = cudaDeviceSynchronize();
+        if (err == cudaSuccess) err = cudaMemcpy(&c, cycles, sizeof c, cudaMemcpyDeviceToHost);
+        if (err == cudaSuccess && c > 0) {
+            // mode 0: 64 DPX ops per thread-iteration; mode 1: 16 rows x 2 cells.
+            const double per_thread = mode == 0 ? 64.0 : 32.0;
+            const double work = double(grid) * kCtaThreads * double(iters) * per_thread;
+            best = std::max(best, work / (double(c) * sms));
+        }
+    }
+    cudaFree(cycles);
+    cudaFree(sink);
+    if (err != cudaSuccess) return fail(SW_ERR_CUDA, cudaGetErrorString(err));
+    *per_sm_cycle = best;
+    *sm_count = sms;
+    return SW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,254 @@
+// Inter-task Smith-Waterman/Gotoh scoring in packed int16x2 DPX arithmetic.
+//
+// Section 2.2 (inter-task parallelism: many alignment matrices computed at
+// once with no communication between them) and Section 2.3 (SW#db's GPU
+// kernel for short database sequences, "solveShort" in Section 3.2).  The
+// design here is this library's own, for sm_103a:
+//
+// * A subwarp of T lanes scores ONE PAIR of database sequences at once: the
+//   low int16 half of every register belongs to sequence 2p, the high half
+//   to 2p+1, so one DPX instruction updates two cells.
+// * Lane k owns R consecutive query rows (a strip of T*R rows per pass) and
+//   walks the database columns one step behind lane k-1 (an anti-diagonal
+//   skew).  The bottom row's H and F and the column's residue codes move to
+//   the next lane with one shuffle each; nothing goes through memory inside
+//   a pass.  Queries longer than T*R rows take several passes; lane T-1
+//   writes the strip's bottom row (H-o and F per column) to scratch and
+//   lane 0 of the next pass reads it back.
+// * The query profile of the current strip lives in shared memory as int8
+//   S(q_i, a) + o, laid out [residue a][lane k][row r], so each lane fetches
+//   its R rows for one database residue with 128-bit loads that are free of
+//   bank conflicts (row stride T*R bytes is a multiple of 128 for T*R >= 128).
+// * Values are kept shifted: the registers carry Ho = H - o, E and F.  Per
+//   cell pair:   E' = max(E - e, Ho_left)                 (viaddmax)
+//                X  = max(Ho_diag + S + o, E', 0)          (viaddmax_relu)
+//                F' = max(F - min(e,o), X_up - o)          (viaddmax; the only
+//                                                           loop-carried op)
+//                Xo = X - o,  Ho = max(F' - o, Xo)         (2 x viaddmax)
+//   which is the recurrence H = max(0, Hdiag + S, E, F) rewritten so the
+//   row-to-row dependency is one instruction long.
+// * Saturation: every value stays below the running maximum of H plus the
+//   largest matrix entry, so if that maximum stays below
+//   32767 - max(S) no int16 operation overflowed and the score is exact.
+//   Sequences at or above that limit are appended to a list and rescored
+//   in int32 by another kernel.
+#include "swdb_internal.cuh"
+
+namespace swdb {
+namespace {
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+// Selector taking byte c of a (low half) and byte c of b (high half), each
+// sign-extended to 16 bits.
+__host__ __device__ constexpr uint32_t pair_sel(int c) {
+    return uint32_t(c) | (uint32_t(c | 8) << 4) | (uint32_t(4 + c) << 8) | (uint32_t((4 + c) | 8) << 12);
+}
+
+__device__ __forceinline__ uint32_t pack2(int v) {
+    uint32_t h = uint32_t(v) & 0xffffu;
+    return h | (h << 16);
+}
+
+template <int T, int R>
+__global__ void __launch_bounds__(kCtaThreads) k_inter_i16x2(const __grid_constant__ InterArgs a) {
+    static_assert(R % 16 == 0, "rows per lane must be a multiple of 16");
+    static_assert(32 % T == 0 && T >= 4, "lanes must divide the warp");
+    constexpr int PAIRS_PER_CTA = kCtaThreads / T;
+    constexpr int TR = T * R;
+    constexpr int PROF_BYTES = kProfRows * TR;
+
+    __shared__ __align__(16) int8_t prof[PROF_BYTES];
+    __shared__ int8_t mat[kProfRows * kProfRows];
+
+    const int tid = threadIdx.x;
+    const int k = tid % T;               // lane within the subwarp
+    const int sub = tid / T;             // subwarp within the CTA
+    const int64_t pair = a.pair_begin + int64_t(blockIdx.x) * PAIRS_PER_CTA + sub;
+    const bool valid = pair < a.pair_end;
+
+    for (int i = tid; i < kProfRows * kProfRows; i += kCtaThreads) mat[i] = (&a.prof8[0][0])[i];
+
+    int64_t b = 0;
+    int slot = 0;
+    int Lp = 0;
+    if (valid) {
+        b = pair / kBundlePairs;
+        slot = int(pair % kBundlePairs);
+        Lp = (a.db.len[2 * pair] + 3) & ~3;   // longest of the pair (sorted, longest first)
+    }
+    const int Lw = __reduce_max_sync(0xffffffffu, Lp);   // warp-uniform column count
+
+    const int o = a.gap_open;
+    const uint32_t NEG_O2 = pack2(-o);
+    const uint32_t NEG_E2 = pack2(-a.gap_extend);
+    const uint32_t NEG_MIN2 = pack2(-(a.gap_extend < o ? a.gap_extend : o));
+    const uint32_t MIN2 = 0x80008000u;
+
+    const uint2 *cptr = nullptr;
+    uint2 *bnd = nullptr;
+    if (valid) {
+        const int64_t off = a.db.bundle_off[b];
+        cptr = reinterpret_cast<const uint2 *>(a.db.codes + off) + slot;
+        bnd = a.boundary + off / 2 + slot;
+    }
+
+    const int npass = (a.m + TR - 1) / TR;
+    uint32_t mx = NEG_O2;                  // running max of H - o, both halves
+
+    for (int pass = 0; pass < npass; ++pass) {
+        __syncthreads();
+        // Profile strip for rows pass*TR .. pass*TR+TR-1, layout [a][k][r].
+        for (int w = tid; w < PROF_BYTES / 4; w += kCtaThreads) {
+            const int e0 = w * 4;
+            const int res = e0 / TR;
+            const int row0 = pass * TR + (e0 % TR);
+            uint32_t word = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int row = row0 + c;
+                int v = -128;
+                if (row < a.m) {
+                    // device-resident queries are not validated on the host:
+                    // codes outside the table score as padding
+                    const int qc = a.query[row];
+                    if (qc < kProfRows) v = mat[qc * kProfRows + res];
+                }
+                word |= (uint32_t(uint8_t(int8_t(v)))) << (8 * c);
+            }
+            reinterpret_cast<uint32_t *>(prof)[w] = word;
+        }
+        __syncthreads();
+        if (Lw == 0) continue;
+
+        uint32_t E[R], Ho[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) { E[r] = NEG_O2; Ho[r] = NEG_O2; }
+        uint32_t hd = NEG_O2;              // Ho(top-1, j-1)
+        uint32_t pub_h = NEG_O2, pub_f = NEG_O2, pub_c = 0;
+        uint2 quad = make_uint2(0, 0);
+        const bool last_pass = (pass + 1 == npass);
+        const int steps = Lw + T - 1;
+
+        for (int s = 0; s < steps; ++s) {
+            uint32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1, T);
+            uint32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1, T);
+            uint32_t cin = __shfl_up_sync(0xffffffffu, pub_c, 1, T);
+            const int j = s - k;
+            const bool act = (j >= 0) && (j < Lp);
+            if (k == 0 && act) {
+                if ((s & 3) == 0) quad = __ldg(cptr + (s >> 2) * kBundlePairs);
+                const uint32_t w = (s & 2) ? quad.y : quad.x;
+                cin = (s & 1) ? (w >> 16) : (w & 0xffffu);
+                if (pass == 0) {
+                    hin = NEG_O2;
+                    fin = NEG_O2;
+                } else {
+                    const uint2 bv = bnd[size_t(s) * kBundlePairs];
+                    hin = bv.x;
+                    fin = bv.y;
+                }
+            }
+            if (act) {
+                const int ta = int(cin & 0xffu), tb = int((cin >> 8) & 0xffu);
+                const uint4 *pa = reinterpret_cast<const uint4 *>(prof + ta * TR + k * R);
+                const uint4 *pb = reinterpret_cast<const uint4 *>(prof + tb * TR + k * R);
+                uint32_t wa[R / 4], wb[R / 4];
+#pragma unroll
+                for (int v = 0; v < R / 16; ++v) {
+                    const uint4 x = pa[v];
+                    const uint4 y = pb[v];
+                    wa[4 * v + 0] = x.x; wa[4 * v + 1] = x.y; wa[4 * v + 2] = x.z; wa[4 * v + 3] = x.w;
+                    wb[4 * v + 0] = y.x; wb[4 * v + 1] = y.y; wb[4 * v + 2] = y.z; wb[4 * v + 3] = y.w;
+                }
+                uint32_t f = __viaddmax_s16x2(fin, NEG_E2, hin);   // F of the top row
+                uint32_t d = hd;
+                uint32_t xo_prev = 0;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t p = prmt(wa[r / 4], wb[r / 4], pair_sel(r % 4));
+                    const uint32_t e_r = __viaddmax_s16x2(E[r], NEG_E2, Ho[r]);
+                    const uint32_t x = __viaddmax_s16x2_relu(d, p, e_r);
+                    if (r > 0) f = __viaddmax_s16x2(f, NEG_MIN2, xo_prev);
+                    const uint32_t xo = __viaddmax_s16x2(x, NEG_O2, MIN2);
+                    const uint32_t ho = __viaddmax_s16x2(f, NEG_O2, xo);
+                    d = Ho[r];
+                    E[r] = e_r;
+                    Ho[r] = ho;
+                    xo_prev = xo;
+                }
+#pragma unroll
+                for (int r = 0; r < R; r += 2) mx = __vimax3_s16x2(mx, Ho[r], Ho[r + 1]);
+                hd = hin;
+                pub_h = Ho[R - 1];
+                pub_f = f;
+                pub_c = cin;
+                if (k == T - 1 && !last_pass) bnd[size_t(j) * kBundlePairs] = make_uint2(Ho[R - 1], f);
+            }
+        }
+    }
+
+#pragma unroll
+    for (int dd = T / 2; dd >= 1; dd >>= 1) {
+        const uint32_t other = __shfl_xor_sync(0xffffffffu, mx, dd, T);
+        mx = __vimax3_s16x2(mx, other, other);
+    }
+    if (valid && k == 0) {
+        const int hA = int(int16_t(mx & 0xffffu)) + o;
+        const int hB = int(int16_t(mx >> 16)) + o;
+        const int64_t tA = 2 * pair;
+        int mask = 0;
+        const int64_t oA = a.db.perm[tA];
+        const int64_t oB = a.db.perm[tA + 1];
+        if (oA >= 0) {
+            if (hA >= a.sat_limit) mask |= 1;
+            else a.scores[oA] = hA;
+        }
+        if (oB >= 0) {
+            if (hB >= a.sat_limit) mask |= 2;
+            else a.scores[oB] = hB;
+        }
+        if (mask) {
+            const int idx = atomicAdd(a.ovf_count, 1);
+            a.ovf_list[idx] = int32_t(pair * 4 + mask);
+        }
+    }
+}
+
+template <int T, int R>
+cudaError_t launch_tr(const InterArgs &a, cudaStream_t s) {
+    constexpr int PAIRS_PER_CTA = kCtaThreads / T;
+    const int64_t pairs = a.pair_end - a.pair_begin;
+    if (pairs <= 0) return cudaSuccess;
+    const int64_t grid = (pairs + PAIRS_PER_CTA - 1) / PAIRS_PER_CTA;
+    k_inter_i16x2<T, R><<<unsigned(grid), kCtaThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool inter_config_supported(int lanes, int rows) {
+    switch (lanes * 100 + rows) {
+        case 416: case 816: case 1616: case 3216: case 832: case 1632: case 3232: return true;
+        default: return false;
+    }
+}
+
+cudaError_t launch_inter_i16x2(const InterArgs &a, int lanes, int rows, cudaStream_t s) {
+    switch (lanes * 100 + rows) {
+        case 416: return launch_tr<4, 16>(a, s);
+        case 816: return launch_tr<8, 16>(a, s);
+        case 1616: return launch_tr<16, 16>(a, s);
+        case 3216: return launch_tr<32, 16>(a, s);
+        case 832: return launch_tr<8, 32>(a, s);
+        case 1632: return launch_tr<16, 32>(a, s);
+        case 3232: return launch_tr<32, 32>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace swdb

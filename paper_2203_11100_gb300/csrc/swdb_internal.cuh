@@ -1,0 +1,88 @@
+// Internal declarations shared by the translation units of libswdb.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace swdb {
+
+// Residue code used for padding past the end of a sequence.  Its profile
+// entries are negative, which never raises a local-alignment maximum when
+// the padding sits after the last real row/column (all dependencies in the
+// recurrences run up and left).
+constexpr int kPadCode = 31;
+constexpr int kProfRows = 32;           // profile rows: 31 codes + padding
+constexpr int kBundleSeqs = 16;         // sequences per interleaved bundle
+constexpr int kBundlePairs = kBundleSeqs / 2;
+constexpr int kQuadBytes = 8;           // 4 columns x (code A, code B)
+constexpr int kBundleRowBytes = kBundlePairs * kQuadBytes;  // 64 bytes per 4 columns
+constexpr int kCtaThreads = 256;
+
+// Device view of the resident database.
+//
+// Sequences are sorted by length, longest first (stable), and cut into
+// bundles of 16.  Sequence 2p and 2p+1 of the sorted order form pair p;
+// bundle b holds pairs 8b..8b+7.  Bundle b occupies bundle_len[b] columns
+// (its longest length rounded up to 4) starting at byte bundle_off[b]:
+//   byte bundle_off[b] + (j/4)*64 + slot*8 + (j%4)*2 + h
+// is column j of sequence 2*(8b+slot)+h.  Neighbouring pairs therefore read
+// neighbouring 8-byte words for the same 4 columns (a coalesced, position-
+// major interleave).
+struct DbView {
+    const uint8_t *codes;
+    const int64_t *bundle_off;  // [n_bundles]
+    const int32_t *bundle_len;  // [n_bundles]
+    const int32_t *len;         // [n_sorted] sorted lengths (0 for padding slots)
+    const int64_t *perm;        // [n_sorted] sorted -> original index (-1 for padding)
+    int64_t n_seqs;
+    int64_t n_sorted;           // n_bundles * 16
+    int64_t n_bundles;
+};
+
+// Arguments of the packed int16x2 inter-task kernel: one query against the
+// pairs [pair_begin, pair_end) of the sorted database.
+struct InterArgs {
+    DbView db;
+    int64_t pair_begin, pair_end;
+    const uint8_t *query;       // device, m codes
+    int32_t m;
+    int32_t gap_open, gap_extend;
+    int32_t sat_limit;          // flag a sequence when its int16 maximum H >= sat_limit
+    int8_t prof8[kProfRows][kProfRows];  // [query code][db code] = S + o, pads = -128
+    uint2 *boundary;            // scratch, 4 bytes per database layout byte
+    int32_t *scores;            // row of this query, original database order
+    int32_t *ovf_list;          // entries pair*4 + mask of saturated halves
+    int32_t *ovf_count;
+};
+
+// Arguments of the int32 kernel.  Work items are pairs with a mask of the
+// halves to score; either an explicit list (ovf_list/ovf_count) or, when
+// list is null, every pair in [pair_begin, pair_end) with mask 3.
+struct I32Args {
+    DbView db;
+    int64_t pair_begin, pair_end;
+    const int32_t *list;
+    const int32_t *list_count;
+    int32_t *work_counter;      // zeroed before launch
+    const int32_t *prof32;      // [kProfRows][m_pad] = S + o, pads large negative
+    int32_t m, m_pad;
+    int32_t gap_open, gap_extend;
+    uint2 *boundary;
+    int32_t *scores;
+    int32_t *status;            // set to nonzero on an internal error
+};
+
+// Launchers (return cudaGetLastError() after the launch).
+cudaError_t launch_inter_i16x2(const InterArgs &a, int lanes, int rows, cudaStream_t s);
+bool inter_config_supported(int lanes, int rows);
+cudaError_t launch_profile32(const uint8_t *query, int32_t m, int32_t m_pad, const int32_t *matrix_host,
+                             int32_t A, int32_t gap_open, int32_t *prof32, cudaStream_t s);
+cudaError_t launch_i32(const I32Args &a, int lanes, int rows, int grid, cudaStream_t s);
+bool i32_config_supported(int lanes, int rows);
+cudaError_t launch_probe(int mode, int grid, int iters, unsigned long long *cycles, uint32_t *sink,
+                         cudaStream_t s);
+int probe_blocks_per_sm(int mode);
+cudaError_t launch_topk(const int32_t *scores, int64_t n_rows, int64_t n_cols, int32_t k,
+                        void *hits, cudaStream_t s);
+
+}  // namespace swdb

@@ -1,0 +1,224 @@
+"""GPU search vs the CPU oracle, bit-exact, through the C ABI.
+
+Scores are integers, so the tolerance is zero: every (query, sequence) score
+and every top-k hit must equal the oracle's (Section 2.2 recurrences with
+the affine gaps of Section 4.1; top-k ordered by score, then index).
+Sizes span several bundles, several query passes and ragged tails.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+I16_SHAPES = [(4, 16), (8, 16), (16, 16), (32, 16), (8, 32), (16, 32), (32, 32)]
+I32_SHAPES = [(8, 16), (16, 16), (32, 16), (32, 32)]
+
+
+def _db(rng, n, lo, hi, A=20):
+    if A == 20:
+        return synth.seqset_from_lengths(rng, rng.integers(lo, hi + 1, n))
+    return synth.random_seqset(rng, n, lo, hi, A)
+
+
+def _check(gpu, qs, db, S, o, e, k=10, **kw):
+    A = S.shape[0]
+    want = oracle.all_scores(qs, db, S, o, e)
+    with gpu.Database(db.residues, db.offsets, A) as d:
+        scores, hits, stats = d.search(qs.residues, qs.offsets, S, o, e, top_k=k, stats=True, **kw)
+    np.testing.assert_array_equal(scores, want)
+    for i in range(qs.n):
+        ws, wi = oracle.top_k(want[i], k)
+        np.testing.assert_array_equal(hits[i]["score"], ws)
+        np.testing.assert_array_equal(hits[i]["db_index"], wi)
+    return stats
+
+
+@pytest.mark.parametrize("lanes,rows", I16_SHAPES)
+def test_int16x2_blosum62_shapes(gpu, lanes, rows):
+    rng = np.random.default_rng(lanes * 100 + rows)
+    db = _db(rng, 293, 1, 400)
+    qs = synth.seqset_from_lengths(rng, [1, 37, 128, 129, 700])
+    st = _check(gpu, qs, db, synth.blosum62(), 10, 1, precision=gpu.SW_PREC_I16, lanes=lanes,
+                rows_per_lane=rows)
+    assert st["precision_used"] == gpu.SW_PREC_I16
+    assert st["lanes_used"] == lanes and st["rows_per_lane_used"] == rows
+    assert st["cells"] == int(qs.lengths.sum()) * int(db.lengths.sum())
+
+
+@pytest.mark.parametrize("lanes,rows", I32_SHAPES)
+def test_int32_blosum62_shapes(gpu, lanes, rows):
+    rng = np.random.default_rng(7 + lanes * 100 + rows)
+    db = _db(rng, 181, 1, 300)
+    qs = synth.seqset_from_lengths(rng, [3, 200, 555])
+    st = _check(gpu, qs, db, synth.blosum62(), 10, 2, precision=gpu.SW_PREC_I32, lanes=lanes,
+                rows_per_lane=rows)
+    assert st["precision_used"] == gpu.SW_PREC_I32
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_matrices_and_penalties(gpu, seed):
+    rng = np.random.default_rng(300 + seed)
+    A = int(rng.integers(2, 25))
+    S = synth.random_matrix(rng, A, -8, 12, symmetric=bool(seed % 2))
+    o = int(rng.integers(0, 15))
+    e = int(rng.integers(0, 6))
+    db = _db(rng, 150, 0, 250, A=A)
+    qs = synth.random_seqset(rng, 3, 0, 300, A)
+    _check(gpu, qs, db, S, o, e, k=7)
+
+
+def test_open_less_than_extend(gpu):
+    rng = np.random.default_rng(11)
+    db = _db(rng, 100, 1, 200)
+    qs = synth.seqset_from_lengths(rng, [90, 260])
+    _check(gpu, qs, db, synth.blosum62(), 1, 4)
+
+
+def test_paper_penalties_10_2(gpu):
+    rng = np.random.default_rng(12)
+    db = _db(rng, 400, 2, 600)
+    qs = synth.seqset_from_lengths(rng, [144, 500])
+    _check(gpu, qs, db, synth.blosum62(), 10, 2)
+
+
+def test_large_penalties_use_int32(gpu):
+    rng = np.random.default_rng(13)
+    db = _db(rng, 80, 1, 200)
+    qs = synth.seqset_from_lengths(rng, [150])
+    st = _check(gpu, qs, db, synth.blosum62() * 20, 200, 30)
+    assert st["precision_used"] == gpu.SW_PREC_I32
+
+
+def test_saturation_rescored_exactly(gpu):
+    """Self-hits of long sequences exceed the int16 range and must be rescored."""
+    rng = np.random.default_rng(14)
+    W = synth.ALPHABET.index("W")
+    long_w = np.full(3100, W, dtype=np.uint8)              # 3100 * 11 = 34100 > 32767
+    mixed = synth.random_residues(rng, 2500)
+    seqs = [synth.random_residues(rng, int(n)) for n in rng.integers(1, 300, 60)]
+    seqs[5] = long_w
+    seqs[17] = mixed
+    seqs[40] = np.concatenate([mixed[:1200], long_w[:2000]])
+    db = synth.seqset_from_list(seqs)
+    qs = synth.seqset_from_list([long_w, mixed, synth.random_residues(rng, 50)])
+    st = _check(gpu, qs, db, synth.blosum62(), 10, 1, precision=gpu.SW_PREC_I16)
+    assert st["rescored"] >= 2
+
+
+def test_saturation_inflated_matrix(gpu):
+    rng = np.random.default_rng(15)
+    A = 4
+    S = np.full((A, A), -3, dtype=np.int32)
+    np.fill_diagonal(S, 110)                               # 110 + o <= 127 keeps the int8 profile
+    base = rng.integers(0, A, 400).astype(np.uint8)        # self score 44000
+    seqs = [rng.integers(0, A, int(n)).astype(np.uint8) for n in rng.integers(1, 200, 40)]
+    seqs[3] = base
+    db = synth.seqset_from_list(seqs)
+    qs = synth.seqset_from_list([base, base[:100]])
+    st = _check(gpu, qs, db, S, 12, 2, precision=gpu.SW_PREC_I16)
+    assert st["rescored"] >= 1
+
+
+def test_edge_cases(gpu):
+    rng = np.random.default_rng(16)
+    S = synth.blosum62()
+    # zero-length sequences, lengths not multiple of 4, count not multiple of 16
+    db = synth.seqset_from_lengths(rng, [0, 1, 2, 3, 5, 0, 7, 33, 0])
+    qs = synth.seqset_from_lengths(rng, [0, 1, 4, 31])
+    _check(gpu, qs, db, S, 10, 1, k=20)                    # top_k > n_seqs pads with -1
+    _check(gpu, qs, db, S, 10, 1, k=1)
+
+
+def test_empty_database_and_no_queries(gpu):
+    S = synth.blosum62()
+    empty = synth.SeqSet(np.zeros(0, np.uint8), np.zeros(1, np.int64))
+    rng = np.random.default_rng(17)
+    qs = synth.seqset_from_lengths(rng, [10, 0])
+    with gpu.Database(empty.residues, empty.offsets, 24) as d:
+        scores, hits, _ = d.search(qs.residues, qs.offsets, S, 10, 1, top_k=3)
+        assert scores.shape == (2, 0)
+        assert (hits["score"] == -1).all() and (hits["db_index"] == -1).all()
+    db = synth.seqset_from_lengths(rng, [5, 6])
+    with gpu.Database(db.residues, db.offsets, 24) as d:
+        scores, hits, _ = d.search(np.zeros(0, np.uint8), np.zeros(1, np.int64), S, 10, 1, top_k=3)
+        assert scores.shape == (0, 2)
+
+
+def test_alphabet_of_one(gpu):
+    S = np.array([[3]], dtype=np.int32)
+    db = synth.SeqSet(np.zeros(10, np.uint8), np.array([0, 4, 10], np.int64))
+    qs = synth.SeqSet(np.zeros(6, np.uint8), np.array([0, 6], np.int64))
+    _check(gpu, qs, db, S, 2, 1, k=2)
+
+
+def test_device_buffers_match_host(gpu):
+    import torch
+    rng = np.random.default_rng(18)
+    db = _db(rng, 120, 1, 300)
+    qs = synth.seqset_from_lengths(rng, [100, 260])
+    S = synth.blosum62()
+    with gpu.Database(db.residues, db.offsets, 24) as d:
+        hs, hh, _ = d.search(qs.residues, qs.offsets, S, 10, 1, top_k=5)
+        q_dev = torch.from_numpy(qs.residues).cuda()
+        ds, dh, _ = d.search(q_dev, qs.offsets, S, 10, 1, top_k=5, on_device=True)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(ds.cpu().numpy(), hs)
+        dh = dh.cpu().numpy()
+        np.testing.assert_array_equal((dh[..., 0] & 0xffffffff).astype(np.int64), hh["score"])
+        np.testing.assert_array_equal(dh[..., 1], hh["db_index"])
+
+
+def test_caller_workspace(gpu):
+    import torch
+    rng = np.random.default_rng(19)
+    db = _db(rng, 64, 1, 200)
+    qs = synth.seqset_from_lengths(rng, [300])
+    S = synth.blosum62()
+    want = oracle.all_scores(qs, db, S, 10, 1)
+    with gpu.Database(db.residues, db.offsets, 24) as d:
+        n = gpu.sw_search_workspace_size(d.handle, qs.offsets, 10)
+        ws = torch.empty(n, dtype=torch.uint8, device="cuda")
+        scores = np.empty((1, db.n), np.int32)
+        gpu.sw_search(d.handle, qs.residues, qs.offsets, S, 10, 1, 0, scores_out=scores, workspace=ws)
+        np.testing.assert_array_equal(scores, want)
+        small = torch.empty(16, dtype=torch.uint8, device="cuda")
+        with pytest.raises(gpu.SwError):
+            gpu.sw_search(d.handle, qs.residues, qs.offsets, S, 10, 1, 0, scores_out=scores, workspace=small)
+
+
+def test_top_k_entry_point_ties(gpu):
+    import torch
+    rng = np.random.default_rng(20)
+    for n, k in [(0, 3), (5, 10), (1000, 10), (70000, 64), (3000, 4096)]:
+        rows = rng.integers(0, 6, size=(3, n)).astype(np.int32)  # heavy ties
+        s = torch.from_numpy(rows).cuda()
+        hits = torch.empty((3, k, 2), dtype=torch.int64, device="cuda")
+        gpu.sw_top_k(s, 3, n, k, hits)
+        torch.cuda.synchronize()
+        h = hits.cpu().numpy()
+        for r in range(3):
+            ws, wi = oracle.top_k(rows[r], k)
+            np.testing.assert_array_equal((h[r, :, 0] & 0xffffffff).astype(np.int32).astype(np.int64), ws)
+            np.testing.assert_array_equal(h[r, :, 1], wi)
+
+
+def test_invalid_arguments_reported(gpu):
+    rng = np.random.default_rng(21)
+    db = _db(rng, 10, 1, 20)
+    S = synth.blosum62()
+    with gpu.Database(db.residues, db.offsets, 24) as d:
+        with pytest.raises(gpu.SwError) as e:
+            d.search(np.array([30], np.uint8), np.array([0, 1]), S, 10, 1)
+        assert e.value.code == 1
+        with pytest.raises(gpu.SwError) as e:
+            d.search(np.array([3], np.uint8), np.array([0, 1]), S, -1, 1)
+        assert e.value.code == 1
+        with pytest.raises(gpu.SwError) as e:
+            d.search(np.array([3], np.uint8), np.array([0, 1]), S * 40, 10, 1, precision=gpu.SW_PREC_I16)
+        assert e.value.code == 6
+        with pytest.raises(gpu.SwError) as e:
+            d.search(np.array([3], np.uint8), np.array([0, 1]), S, 10, 1, lanes=5)
+        assert e.value.code == 6
