@@ -265,6 +265,7 @@ def run_ours(args, dist: Dist):
     launches = sum(s["launches"] for s in st_all)
     rescored = sum(s["rescored"] for s in st_all)
     rescore_ms = sum(s["rescore_ms"] for s in st_all)
+    long_ms = sum(s["intra_ms"] for s in st_all)
     other_ms = sum(s["other_ms"] for s in st_all)
     st0 = st_all[0]
 
@@ -287,7 +288,7 @@ def run_ours(args, dist: Dist):
         mhz = clk.get("sm_mhz") or torch.cuda.get_device_properties(dev).clock_rate / 1e3
         peak = rate_dpx * sms * mhz * 1e6 / DPX_OPS_PER_CELL / 1e9
         ceiling = rate_cells * sms * mhz * 1e6 / 1e9
-        inter_cells = cells_step * args.steps   # every pair goes through the inter-task kernel
+        inter_cells = float(sum(s["inter_cells"] for s in st_all))
         achieved = inter_cells / (inter_ms * 1e-3) / 1e9 if inter_ms > 0 else 0.0
         cells_per_launch = inter_cells / max(inter_launches, 1)
         traffic = traffic_per_launch(cells_per_launch)
@@ -318,7 +319,9 @@ def run_ours(args, dist: Dist):
             "e2e": {"value": e2e_gcups, "unit": UNIT, "h2d_bytes_per_step": int(w.queries.residues.nbytes),
                     "d2h_bytes_per_step": int(nq * n * 4 + nq * w.top_k * 16), "ms_per_step": e2e_ms / args.e2e_steps},
             "gpu_launches": launches,
-            "kernel_ms": {"inter": inter_ms, "rescore": rescore_ms, "profile_topk": other_ms},
+            "kernel_ms": {"inter": inter_ms, "long_side_stream": long_ms, "rescore": rescore_ms,
+                          "profile_topk": other_ms},
+            "long_sequences": st0["long_sequences"],
             "rescored_per_step": rescored / args.steps,
             "clocks": clk,
         }

@@ -102,9 +102,11 @@ typedef struct {
     int32_t launches;       /* kernels this call launched */
     float inter_ms;         /* CUDA-event time of the inter-task kernel launches */
     float rescore_ms;       /* CUDA-event time of the int32 kernel launches */
-    float intra_ms;         /* CUDA-event time of the intra-task kernel launches */
+    float intra_ms;         /* CUDA-event time of the long-sequence launches */
     float other_ms;         /* CUDA-event time of profile and top-k kernels */
     int32_t inter_launches; /* launches of the inter-task kernel */
+    int64_t inter_cells;    /* cells scored by the inter-task kernel launches */
+    int64_t long_cells;     /* cells of the long sequences (intra_ms launches) */
 } sw_search_stats;
 
 /*

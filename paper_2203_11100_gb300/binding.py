@@ -42,7 +42,8 @@ class SwSearchStats(ctypes.Structure):
                 ("precision_used", ctypes.c_int32), ("mode_used", ctypes.c_int32),
                 ("lanes_used", ctypes.c_int32), ("rows_per_lane_used", ctypes.c_int32),
                 ("launches", ctypes.c_int32), ("inter_ms", ctypes.c_float), ("rescore_ms", ctypes.c_float),
-                ("intra_ms", ctypes.c_float), ("other_ms", ctypes.c_float), ("inter_launches", ctypes.c_int32)]
+                ("intra_ms", ctypes.c_float), ("other_ms", ctypes.c_float), ("inter_launches", ctypes.c_int32),
+                ("inter_cells", ctypes.c_int64), ("long_cells", ctypes.c_int64)]
 
 
 class SwDbInfo(ctypes.Structure):

@@ -62,7 +62,11 @@ struct sw_db {
     int32_t *d_len = nullptr;
     int64_t *d_perm = nullptr;
 
+    std::vector<int64_t> h_bundle_res;   // residues per bundle
+
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;         // long sequences run here, concurrently
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     void *ws = nullptr;
     size_t ws_bytes = 0;
     std::mutex mu;
@@ -119,7 +123,12 @@ void free_db_device(sw_db *db) {
     db->ws = nullptr;
     db->ws_bytes = 0;
     if (db->stream) cudaStreamDestroy(db->stream);
+    if (db->side) cudaStreamDestroy(db->side);
+    if (db->ev_fork) cudaEventDestroy(db->ev_fork);
+    if (db->ev_join) cudaEventDestroy(db->ev_join);
     db->stream = nullptr;
+    db->side = nullptr;
+    db->ev_fork = db->ev_join = nullptr;
 }
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -143,8 +152,13 @@ struct Plan {
     int mode = SW_MODE_PLAIN;
     int lanes = 8, rows = 16;        // int16x2 kernel
     int lanes32 = 8, rows32 = 16;    // int32 kernel
-    int64_t long_begin_pair = 0;     // pairs [0, long_begin_pair) are long sequences
-    int64_t n_long = 0;
+    int64_t long_end_pair = 0;       // pairs [0, long_end_pair) hold the long sequences
+    int64_t n_long = 0;              // real sequences among them
+    int64_t long_residues = 0;
+    int lanes_long = 32, rows_long = 16;   // per warp of the intra-task kernel
+    int warps_long = 4;
+    int64_t long_codes_bytes = 0;          // layout bytes of the long bundles (a prefix)
+    bool need_long_boundary = false;
     int32_t max_m = 0;
     int64_t total_m = 0;
     bool need_boundary = false;
@@ -208,9 +222,20 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
         p.lanes32 = lanes;
         p.rows32 = rows;
     }
+    // Long sequences: the bundles (a prefix, the database being sorted longest
+    // first) whose length exceeds the cutoff are scored by a separate launch
+    // with wide subwarps on a second stream, concurrently with the rest, so a
+    // handful of very long sequences do not set the length of the main launch.
+    const int64_t cutoff = opts && opts->long_cutoff ? opts->long_cutoff : 3072;
+    int64_t nlb = 0;
+    if (cutoff > 0 && p.precision == SW_PREC_I16)
+        while (nlb < db->n_bundles && db->h_bundle_len[size_t(nlb)] > cutoff) ++nlb;
+    p.long_end_pair = nlb * kBundlePairs;
+    for (int64_t b = 0; b < nlb; ++b) p.long_residues += db->h_bundle_res[size_t(b)];
+    p.n_long = std::min<int64_t>(nlb * kBundleSeqs, db->n_seqs);
+    p.long_codes_bytes = nlb < db->n_bundles ? db->h_bundle_off[size_t(nlb)] : db->codes_bytes;
+    p.need_long_boundary = nlb > 0 && p.max_m > intra_rows_per_superpass(p.warps_long, p.rows_long);
     p.need_boundary = p.max_m > std::min(p.lanes * p.rows, p.lanes32 * p.rows32);
-    p.long_begin_pair = 0;   // long sequences go through the inter-task kernel (see long_cutoff)
-    p.n_long = 0;
     *plan = p;
     return SW_OK;
 }
@@ -220,9 +245,12 @@ struct Buffers {
     int32_t *scores = nullptr;
     sw_hit *hits = nullptr;
     uint2 *boundary = nullptr;
+    uint2 *long_boundary = nullptr;   // [n_q] regions of long_codes_bytes/2 entries
+    int64_t *q_off = nullptr;         // device copy of the query offsets
     int32_t *prof32 = nullptr;
     int32_t *ovf_list = nullptr;
-    int32_t *counters = nullptr;   // [n_q] overflow counts, [n_q] work counters
+    int32_t *counters = nullptr;   // [n_q] list lengths, [n_q] work counters, [n_q] flagged sequences,
+                                   // then one status word
 };
 
 size_t carve(const sw_db *db, const Plan &p, int32_t n_q, int32_t top_k, bool q_dev, bool s_dev,
@@ -236,8 +264,13 @@ size_t carve(const sw_db *db, const Plan &p, int32_t n_q, int32_t top_k, bool q_
     const int tr32 = p.lanes32 * p.rows32;
     const int64_t m_pad = round_up(std::max<int64_t>(p.max_m, 1), tr32);
     x.prof32 = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(kProfRows) * size_t(m_pad)));
-    x.ovf_list = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(std::max<int64_t>(db->n_sorted / 2, 1))));
-    x.counters = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(2 * std::max<int32_t>(n_q, 1))));
+    if (p.need_long_boundary)
+        x.long_boundary = static_cast<uint2 *>(c.take(size_t(p.long_codes_bytes) * 4 * size_t(n_q) + 64));
+    x.q_off = static_cast<int64_t *>(c.take(sizeof(int64_t) * size_t(n_q + 1)));
+    // one overflow list per query: queries run concurrently with the long-sequence launch
+    x.ovf_list = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(std::max<int32_t>(n_q, 1)) *
+                                               size_t(std::max<int64_t>(db->n_sorted / 2, 1))));
+    x.counters = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(3 * std::max<int32_t>(n_q, 1) + 1)));
     *b = x;
     return c.used + 256;
 }
@@ -250,19 +283,19 @@ struct LaunchTimer {
     cudaStream_t st = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
     int launches = 0;
-    cudaEvent_t begin(int) {
+    cudaEvent_t begin(int, cudaStream_t s) {
         ++launches;
         if (!on) return nullptr;
         cudaEvent_t a;
         cudaEventCreate(&a);
-        cudaEventRecord(a, st);
+        cudaEventRecord(a, s);
         return a;
     }
-    void end(int fam, cudaEvent_t a) {
+    void end(int fam, cudaEvent_t a, cudaStream_t s) {
         if (!on) return;
         cudaEvent_t b;
         cudaEventCreate(&b);
-        cudaEventRecord(b, st);
+        cudaEventRecord(b, s);
         ev[fam].push_back({a, b});
     }
     float total(int fam) {
@@ -283,12 +316,13 @@ struct LaunchTimer {
     }
 };
 
-#define TIMED(fam, call)                       \
+#define TIMED_ON(fam, strm, call)              \
     do {                                       \
-        cudaEvent_t _a = timer.begin(fam);     \
+        cudaEvent_t _a = timer.begin(fam, strm); \
         SW_CUDA_TRY(call);                     \
-        timer.end(fam, _a);                    \
+        timer.end(fam, _a, strm);              \
     } while (0)
+#define TIMED(fam, call) TIMED_ON(fam, st, call)
 
 }  // namespace
 
@@ -367,6 +401,8 @@ int sw_db_load(const uint8_t *residues, const int64_t *offsets, int64_t n_seqs, 
         off += int64_t(L) * kBundleSeqs;
     }
     db->codes_bytes = off;
+    db->h_bundle_res.assign(size_t(db->n_bundles), 0);
+    for (int64_t t = 0; t < n_seqs; ++t) db->h_bundle_res[size_t(t / kBundleSeqs)] += db->h_len[size_t(t)];
     std::vector<uint8_t> codes(size_t(std::max<int64_t>(off, 1)), uint8_t(kPadCode));
     for (int64_t s = 0; s < n_seqs; ++s) {
         const int64_t b = s / kBundleSeqs;
@@ -384,7 +420,10 @@ int sw_db_load(const uint8_t *residues, const int64_t *offsets, int64_t n_seqs, 
         return fail(code, msg);
     };
     cudaError_t err;
-    if ((err = cudaStreamCreateWithFlags(&db->stream, cudaStreamNonBlocking)) != cudaSuccess)
+    if ((err = cudaStreamCreateWithFlags(&db->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (err = cudaStreamCreateWithFlags(&db->side, cudaStreamNonBlocking)) != cudaSuccess ||
+        (err = cudaEventCreateWithFlags(&db->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (err = cudaEventCreateWithFlags(&db->ev_join, cudaEventDisableTiming)) != cudaSuccess)
         return cleanup(SW_ERR_CUDA, cudaGetErrorString(err));
     const size_t nb = size_t(std::max<int64_t>(db->n_bundles, 1));
     const size_t ns = size_t(std::max<int64_t>(db->n_sorted, 1));
@@ -512,7 +551,8 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
     sw_hit *d_hits = h_dev ? hits_out : buf.hits;
     if (!q_dev && plan.total_m > 0)
         SW_CUDA_TRY(cudaMemcpyAsync(buf.queries, queries, size_t(plan.total_m), cudaMemcpyHostToDevice, st));
-    if (n_q > 0) SW_CUDA_TRY(cudaMemsetAsync(buf.counters, 0, sizeof(int32_t) * 2 * size_t(n_q), st));
+    int32_t *d_status = buf.counters + 3 * size_t(std::max<int32_t>(n_q, 1));
+    SW_CUDA_TRY(cudaMemsetAsync(buf.counters, 0, sizeof(int32_t) * (3 * size_t(std::max<int32_t>(n_q, 1)) + 1), st));
 
     // int8 profile table for the int16x2 kernel: [query code][db code] = S + o.
     InterArgs ia;
@@ -529,6 +569,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
     ia.sat_limit = plan.sat_limit;
     ia.boundary = buf.boundary;
     ia.ovf_list = buf.ovf_list;
+    ia.status = d_status;
 
     I32Args ja;
     memset(&ja, 0, sizeof ja);
@@ -540,40 +581,91 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
     const int grid32 = std::max(1, db->sm_count) * 8;
     const int64_t n_pairs = db->n_sorted / 2;
 
-    for (int32_t qi = 0; qi < n_q; ++qi) {
+    const int64_t list_stride = std::max<int64_t>(n_pairs, 1);
+
+    // (1) Long sequences of every query: one intra-task launch on the side
+    //     stream, concurrent with the per-query launches below.
+    const bool split = plan.precision == SW_PREC_I16 && plan.long_end_pair > 0 && n_q > 0 && db->n_seqs > 0;
+    if (split) {
+        SW_CUDA_TRY(cudaMemcpyAsync(buf.q_off, q_offsets, sizeof(int64_t) * size_t(n_q + 1), cudaMemcpyHostToDevice, st));
+        IntraArgs la;
+        memset(&la, 0, sizeof la);
+        la.db = db->view();
+        la.pair_begin = 0;
+        la.pair_end = plan.long_end_pair;
+        la.n_q = n_q;
+        la.q_off = buf.q_off;
+        la.queries = d_queries;
+        la.gap_open = gap_open;
+        la.gap_extend = gap_extend;
+        la.sat_limit = plan.sat_limit;
+        memcpy(la.prof8, ia.prof8, sizeof la.prof8);
+        la.boundary = buf.long_boundary;
+        la.boundary_stride = plan.long_codes_bytes / 2;
+        la.scores = d_scores;
+        la.ovf_list = buf.ovf_list;
+        la.list_stride = list_stride;
+        la.ovf_count = buf.counters;
+        la.ovf_seqs = buf.counters + 2 * n_q;
+        la.status = d_status;
+        SW_CUDA_TRY(cudaEventRecord(db->ev_fork, st));
+        SW_CUDA_TRY(cudaStreamWaitEvent(db->side, db->ev_fork, 0));
+        TIMED_ON(LaunchTimer::INTRA, db->side, launch_intra_i16x2(la, plan.warps_long, plan.rows_long, db->side));
+        SW_CUDA_TRY(cudaEventRecord(db->ev_join, db->side));
+    }
+
+    // (2) One inter-task launch per query over the rest of the database.
+    for (int32_t qi = 0; qi < n_q && db->n_seqs > 0; ++qi) {
         const int32_t m = int32_t(q_offsets[qi + 1] - q_offsets[qi]);
         int32_t *row = d_scores + size_t(qi) * size_t(db->n_seqs);
-        if (db->n_seqs == 0) continue;
         if (m == 0) {
             SW_CUDA_TRY(cudaMemsetAsync(row, 0, sizeof(int32_t) * size_t(db->n_seqs), st));
             continue;
         }
         const uint8_t *q = d_queries + q_offsets[qi];
-        const int tr32 = plan.lanes32 * plan.rows32;
-        const int32_t m_pad = int32_t(round_up(m, tr32));
-        TIMED(LaunchTimer::OTHER, launch_profile32(q, m, m_pad, matrix, db->A, gap_open, buf.prof32, st));
-        ja.m = m;
-        ja.m_pad = m_pad;
-        ja.scores = row;
         if (plan.precision == SW_PREC_I16) {
-            ia.pair_begin = plan.long_begin_pair;
-            ia.pair_end = n_pairs;
             ia.query = q;
             ia.m = m;
             ia.scores = row;
+            ia.ovf_list = buf.ovf_list + size_t(qi) * size_t(list_stride);
             ia.ovf_count = buf.counters + qi;
+            ia.ovf_seqs = buf.counters + 2 * n_q + qi;
+            ia.pair_begin = plan.long_end_pair;
+            ia.pair_end = n_pairs;
             TIMED(LaunchTimer::INTER, launch_inter_i16x2(ia, plan.lanes, plan.rows, st));
-            ja.list = buf.ovf_list;
-            ja.list_count = buf.counters + qi;
-            ja.work_counter = buf.counters + n_q + qi;
-            TIMED(LaunchTimer::RESCORE, launch_i32(ja, plan.lanes32, plan.rows32, grid32, st));
         } else {
+            const int tr32 = plan.lanes32 * plan.rows32;
+            const int32_t m_pad = int32_t(round_up(m, tr32));
+            TIMED(LaunchTimer::OTHER, launch_profile32(q, m, m_pad, matrix, db->A, gap_open, buf.prof32, st));
+            ja.m = m;
+            ja.m_pad = m_pad;
+            ja.scores = row;
             ja.list = nullptr;
             ja.list_count = nullptr;
             ja.pair_begin = 0;
             ja.pair_end = n_pairs;
             ja.work_counter = buf.counters + n_q + qi;
             TIMED(LaunchTimer::INTER, launch_i32(ja, plan.lanes32, plan.rows32, grid32, st));
+        }
+    }
+    if (split) SW_CUDA_TRY(cudaStreamWaitEvent(st, db->ev_join, 0));
+
+    // (3) Exact int32 rescore of the sequences whose int16 maximum saturated.
+    if (plan.precision == SW_PREC_I16) {
+        for (int32_t qi = 0; qi < n_q && db->n_seqs > 0; ++qi) {
+            const int32_t m = int32_t(q_offsets[qi + 1] - q_offsets[qi]);
+            if (m == 0) continue;
+            const uint8_t *q = d_queries + q_offsets[qi];
+            const int tr32 = plan.lanes32 * plan.rows32;
+            const int32_t m_pad = int32_t(round_up(m, tr32));
+            TIMED(LaunchTimer::OTHER, launch_profile32(q, m, m_pad, matrix, db->A, gap_open, buf.prof32, st));
+            ja.m = m;
+            ja.m_pad = m_pad;
+            ja.scores = d_scores + size_t(qi) * size_t(db->n_seqs);
+            ja.list = buf.ovf_list + size_t(qi) * size_t(list_stride);
+            ja.list_count = buf.counters + qi;
+            ja.work_counter = buf.counters + n_q + qi;
+            TIMED(LaunchTimer::RESCORE, launch_i32(ja, plan.lanes32, plan.rows32, grid32, st));
         }
     }
     if (top_k > 0 && n_q > 0 && (hits_out != nullptr))
@@ -593,7 +685,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
     if (stats) {
         std::vector<int32_t> cnt(size_t(std::max(n_q, 1)), 0);
         if (n_q > 0 && plan.precision == SW_PREC_I16)
-            SW_CUDA_TRY(cudaMemcpyAsync(cnt.data(), buf.counters, sizeof(int32_t) * size_t(n_q),
+            SW_CUDA_TRY(cudaMemcpyAsync(cnt.data(), buf.counters + 2 * n_q, sizeof(int32_t) * size_t(n_q),
                                         cudaMemcpyDeviceToHost, st));
         SW_CUDA_TRY(cudaStreamSynchronize(st));
         stats->cells = plan.total_m * db->residues;
@@ -602,6 +694,8 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
             for (int32_t i = 0; i < n_q; ++i) r += cnt[size_t(i)];
         stats->rescored = r;
         stats->long_sequences = plan.n_long;
+        stats->long_cells = plan.total_m * plan.long_residues;
+        stats->inter_cells = stats->cells - stats->long_cells;
         stats->precision_used = plan.precision;
         stats->mode_used = plan.mode;
         stats->lanes_used = plan.precision == SW_PREC_I16 ? plan.lanes : plan.lanes32;
@@ -615,6 +709,11 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
         sync = false;
     }
     if (sync) SW_CUDA_TRY(cudaStreamSynchronize(st));
+    if (sync || stats) {
+        int32_t status = 0;
+        SW_CUDA_TRY(cudaMemcpy(&status, d_status, sizeof status, cudaMemcpyDeviceToHost));
+        if (status) return fail(SW_ERR_TIMEOUT, "a bounded device-side wait gave up (intra-task kernel)");
+    }
     SW_CUDA_TRY(cudaGetLastError());
     return SW_OK;
 }

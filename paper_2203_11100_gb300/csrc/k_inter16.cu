@@ -89,12 +89,15 @@ __global__ void __launch_bounds__(kCtaThreads) k_inter_i16x2(const __grid_consta
     const uint32_t NEG_MIN2 = pack2(-(a.gap_extend < o ? a.gap_extend : o));
     const uint32_t MIN2 = 0x80008000u;
 
+    // Boundary scratch of this bundle: 8*Lb uint2 entries starting at
+    // uint2 index off/2, grouped as [column/4][slot][column%4] so lane 0 of a
+    // pair reads 4 columns with two 16-byte loads.
     const uint2 *cptr = nullptr;
-    uint2 *bnd = nullptr;
+    uint4 *bnd = nullptr;
     if (valid) {
         const int64_t off = a.db.bundle_off[b];
         cptr = reinterpret_cast<const uint2 *>(a.db.codes + off) + slot;
-        bnd = a.boundary + off / 2 + slot;
+        bnd = reinterpret_cast<uint4 *>(a.boundary + off / 2) + slot * 2;
     }
 
     const int npass = (a.m + TR - 1) / TR;
@@ -130,9 +133,22 @@ __global__ void __launch_bounds__(kCtaThreads) k_inter_i16x2(const __grid_consta
         for (int r = 0; r < R; ++r) { E[r] = NEG_O2; Ho[r] = NEG_O2; }
         uint32_t hd = NEG_O2;              // Ho(top-1, j-1)
         uint32_t pub_h = NEG_O2, pub_f = NEG_O2, pub_c = 0;
-        uint2 quad = make_uint2(0, 0);
         const bool last_pass = (pass + 1 == npass);
         const int steps = Lw + T - 1;
+        // Lane 0 reads codes and (after the first pass) the previous strip's
+        // bottom row in groups of 4 columns, one group ahead of use, so the
+        // global-load latency stays off the per-column critical path.
+        uint2 quad = make_uint2(0, 0), quad_next = make_uint2(0, 0);
+        uint4 bc0 = make_uint4(0, 0, 0, 0), bc1 = bc0, bn0 = bc0, bn1 = bc0;
+        // Lane T-1 collects 4 columns of its bottom row before one 32-byte store.
+        uint2 sb0 = make_uint2(0, 0), sb1 = sb0, sb2 = sb0, sb3 = sb0;
+        if (k == 0 && Lp > 0) {
+            quad_next = __ldg(cptr);
+            if (pass > 0) {
+                bn0 = bnd[0];
+                bn1 = bnd[1];
+            }
+        }
 
         for (int s = 0; s < steps; ++s) {
             uint32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1, T);
@@ -141,16 +157,28 @@ __global__ void __launch_bounds__(kCtaThreads) k_inter_i16x2(const __grid_consta
             const int j = s - k;
             const bool act = (j >= 0) && (j < Lp);
             if (k == 0 && act) {
-                if ((s & 3) == 0) quad = __ldg(cptr + (s >> 2) * kBundlePairs);
+                if ((s & 3) == 0) {
+                    quad = quad_next;
+                    bc0 = bn0;
+                    bc1 = bn1;
+                    if (s + 4 < Lp) {
+                        quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
+                        if (pass > 0) {
+                            const uint4 *g = bnd + size_t((s >> 2) + 1) * (kBundlePairs * 2);
+                            bn0 = g[0];
+                            bn1 = g[1];
+                        }
+                    }
+                }
                 const uint32_t w = (s & 2) ? quad.y : quad.x;
                 cin = (s & 1) ? (w >> 16) : (w & 0xffffu);
                 if (pass == 0) {
                     hin = NEG_O2;
                     fin = NEG_O2;
                 } else {
-                    const uint2 bv = bnd[size_t(s) * kBundlePairs];
-                    hin = bv.x;
-                    fin = bv.y;
+                    const uint4 bq = (s & 2) ? bc1 : bc0;
+                    hin = (s & 1) ? bq.z : bq.x;
+                    fin = (s & 1) ? bq.w : bq.y;
                 }
             }
             if (act) {
@@ -187,7 +215,17 @@ __global__ void __launch_bounds__(kCtaThreads) k_inter_i16x2(const __grid_consta
                 pub_h = Ho[R - 1];
                 pub_f = f;
                 pub_c = cin;
-                if (k == T - 1 && !last_pass) bnd[size_t(j) * kBundlePairs] = make_uint2(Ho[R - 1], f);
+                if (k == T - 1 && !last_pass) {
+                    sb0 = sb1;
+                    sb1 = sb2;
+                    sb2 = sb3;
+                    sb3 = make_uint2(Ho[R - 1], f);
+                    if ((j & 3) == 3) {   // Lp is a multiple of 4, so every group completes
+                        uint4 *g = bnd + size_t(j >> 2) * (kBundlePairs * 2);
+                        g[0] = make_uint4(sb0.x, sb0.y, sb1.x, sb1.y);
+                        g[1] = make_uint4(sb2.x, sb2.y, sb3.x, sb3.y);
+                    }
+                }
             }
         }
     }
@@ -215,6 +253,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_inter_i16x2(const __grid_consta
         if (mask) {
             const int idx = atomicAdd(a.ovf_count, 1);
             a.ovf_list[idx] = int32_t(pair * 4 + mask);
+            atomicAdd(a.ovf_seqs, __popc(mask));
         }
     }
 }

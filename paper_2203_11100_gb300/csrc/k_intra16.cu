@@ -1,0 +1,349 @@
+// Intra-task Smith-Waterman/Gotoh scoring of long database sequences.
+//
+// Section 2.2 (intra-task parallelism: all processing elements work on one
+// alignment matrix and exchange border elements) and Section 2.3 (SW#db
+// uses it for long sequences; "solveLong" in Section 3.2).  This kernel is
+// this library's own design for sm_103a:
+//
+// * One CTA scores one PAIR of long database sequences (packed int16x2, as
+//   in the inter-task kernel: the database is sorted, so the two sequences
+//   of a pair have similar lengths).
+// * The CTA's NW warps split the query: in each super-pass of NW*32*R rows,
+//   warp w owns rows [w*32*R, (w+1)*32*R) and its 32 lanes own R rows each.
+//   Inside a warp the lanes form the same skewed wavefront as the inter-task
+//   kernel (lane k works on column j one step after lane k-1; H/F/codes move
+//   lane to lane by shuffle).
+// * Between warps the bottom row of warp w (H-o and F per column) goes to
+//   warp w+1 through a shared-memory ring of D chunks of C columns: a
+//   bounded producer/consumer pipeline with acquire/release flags, so the
+//   warps advance as a wavefront of their own.  Between super-passes the
+//   last warp's bottom row goes through global scratch and a CTA barrier.
+// * Every wait is bounded: if a flag does not arrive within the spin limit
+//   the kernel records SW_ERR_TIMEOUT in a status word, tells the other
+//   warps to stop waiting, and finishes without hanging.
+// Per cell pair the arithmetic is the same five DPX operations and one byte
+// permute as the inter-task kernel (see k_inter16.cu for the derivation).
+#include "swdb_internal.cuh"
+
+namespace swdb {
+namespace {
+
+constexpr int kChunk = 64;      // columns per ring chunk
+constexpr int kDepth = 4;       // chunks per ring
+constexpr long long kSpinLimit = 1ll << 25;   // x ~32 ns sleep: about a second
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+__host__ __device__ constexpr uint32_t pair_sel(int c) {
+    return uint32_t(c) | (uint32_t(c | 8) << 4) | (uint32_t(4 + c) << 8) | (uint32_t((4 + c) | 8) << 12);
+}
+
+__device__ __forceinline__ uint32_t pack2(int v) {
+    uint32_t h = uint32_t(v) & 0xffffu;
+    return h | (h << 16);
+}
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.cta.shared.u32 [%0], %1;" :: "r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+}
+
+// Spin (all lanes of a warp) until *flag >= target, the CTA aborts, or the
+// spin limit runs out (then record a timeout and abort the CTA).
+__device__ bool wait_flag(const int *flag, int target, int *abort_flag, int32_t *status) {
+    for (long long it = 0; it < kSpinLimit; ++it) {
+        if (ld_acquire(flag) >= target) return true;
+        if (*reinterpret_cast<volatile int *>(abort_flag)) return false;
+        __nanosleep(32);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicExch(status, int32_t(4));   // SW_ERR_TIMEOUT
+        *reinterpret_cast<volatile int *>(abort_flag) = 1;
+    }
+    __syncwarp();
+    return false;
+}
+
+template <int R, int NW>
+__global__ void __launch_bounds__(NW * 32) k_intra_i16x2(const __grid_constant__ IntraArgs a) {
+    constexpr int T = 32;
+    constexpr int TR = T * R;
+    constexpr int SPR = NW * TR;
+    constexpr int C = kChunk;
+    constexpr int D = kDepth;
+    extern __shared__ __align__(16) uint8_t smem[];
+    int8_t *prof_all = reinterpret_cast<int8_t *>(smem);                      // [NW][32][TR]
+    uint2 *ring_all = reinterpret_cast<uint2 *>(smem + NW * kProfRows * TR);  // [NW][D*C], link into warp w
+    int8_t *mat = reinterpret_cast<int8_t *>(ring_all + NW * D * C);          // [32*32]
+    int *full = reinterpret_cast<int *>(mat + kProfRows * kProfRows);         // [NW] chunks written into link w
+    int *empty = full + NW;                                                   // [NW] chunks read from link w
+    int *abort_flag = empty + NW;
+    __shared__ uint32_t red[NW];
+
+    const int w = threadIdx.x >> 5;
+    const int k = threadIdx.x & 31;
+    // Pair-major order: the longest pairs of every query are dispatched first.
+    const int64_t pair = a.pair_begin + blockIdx.x / a.n_q;
+    const int q = int(blockIdx.x % a.n_q);
+    const int64_t q0 = a.q_off[q];
+    const int m = int(a.q_off[q + 1] - q0);
+    if (m == 0) return;   // the host writes zero scores for empty queries
+    const uint8_t *query = a.queries + q0;
+    int32_t *scores = a.scores + int64_t(q) * a.db.n_seqs;
+    int32_t *ovf_list = a.ovf_list + int64_t(q) * a.list_stride;
+
+    for (int i = threadIdx.x; i < kProfRows * kProfRows; i += NW * 32) mat[i] = (&a.prof8[0][0])[i];
+    if (threadIdx.x < NW) {
+        full[threadIdx.x] = 0;
+        empty[threadIdx.x] = 0;
+    }
+    if (threadIdx.x == 0) *abort_flag = 0;
+
+    const int64_t b = pair / kBundlePairs;
+    const int slot = int(pair % kBundlePairs);
+    const int Lp = (a.db.len[2 * pair] + 3) & ~3;
+    const int64_t off = a.db.bundle_off[b];
+    const uint2 *cptr = reinterpret_cast<const uint2 *>(a.db.codes + off) + slot;
+    uint4 *gbnd = a.boundary ? reinterpret_cast<uint4 *>(a.boundary + int64_t(q) * a.boundary_stride + off / 2) + slot * 2
+                             : nullptr;
+
+    const int o = a.gap_open;
+    const uint32_t NEG_O2 = pack2(-o);
+    const uint32_t NEG_E2 = pack2(-a.gap_extend);
+    const uint32_t NEG_MIN2 = pack2(-(a.gap_extend < o ? a.gap_extend : o));
+    const uint32_t MIN2 = 0x80008000u;
+
+    int8_t *prof = prof_all + w * kProfRows * TR;
+    uint2 *ring_in = ring_all + w * D * C;
+    uint2 *ring_out = ring_all + ((w + 1) % NW) * D * C;
+
+    const int nsp = (m + SPR - 1) / SPR;
+    uint32_t mx = NEG_O2;
+    int g_in = 0, g_out = 0;   // chunk sequence numbers on the incoming / outgoing link
+
+    for (int sp = 0; sp < nsp; ++sp) {
+        __syncthreads();
+        const int row0 = sp * SPR + w * TR;
+        if (row0 >= m || Lp == 0) continue;
+        const bool from_ring = w > 0;
+        const bool to_ring = (w + 1 < NW) && (row0 + TR < m);
+        const bool from_global = (w == 0) && sp > 0;
+        const bool to_global = !to_ring && (sp + 1 < nsp);
+
+        // This warp's profile slice, layout [a][k][r] for rows row0 .. row0+TR-1.
+        for (int wi = k; wi < kProfRows * TR / 4; wi += 32) {
+            const int e0 = wi * 4;
+            const int res = e0 / TR;
+            const int rr = row0 + (e0 % TR);
+            uint32_t word = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int row = rr + c;
+                int v = -128;
+                if (row < m) {
+                    const int qc = query[row];
+                    if (qc < kProfRows) v = mat[qc * kProfRows + res];
+                }
+                word |= (uint32_t(uint8_t(int8_t(v)))) << (8 * c);
+            }
+            reinterpret_cast<uint32_t *>(prof)[wi] = word;
+        }
+        __syncwarp();
+
+        uint32_t E[R], Ho[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) { E[r] = NEG_O2; Ho[r] = NEG_O2; }
+        uint32_t hd = NEG_O2;
+        uint32_t pub_h = NEG_O2, pub_f = NEG_O2, pub_c = 0;
+        uint2 quad = make_uint2(0, 0), quad_next = make_uint2(0, 0);
+        uint4 bc0 = make_uint4(0, 0, 0, 0), bc1 = bc0, bn0 = bc0, bn1 = bc0;
+        uint2 sb0 = make_uint2(0, 0), sb1 = sb0, sb2 = sb0, sb3 = sb0;
+        if (k == 0) {
+            quad_next = __ldg(cptr);
+            if (from_global) {
+                bn0 = gbnd[0];
+                bn1 = gbnd[1];
+            }
+        }
+        const int steps = Lp + T - 1;
+        for (int s = 0; s < steps; ++s) {
+            const int j31 = s - (T - 1);
+            // Flow control (warp-uniform): wait for the producer's chunk before
+            // lane 0 enters it, and for ring space before lane 31 starts writing one.
+            if (from_ring && s < Lp && (s % C) == 0) wait_flag(&full[w], g_in + 1, abort_flag, a.status);
+            if (to_ring && j31 >= 0 && (j31 % C) == 0)
+                wait_flag(&empty[(w + 1) % NW], g_out - D + 1, abort_flag, a.status);
+
+            uint32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1, T);
+            uint32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1, T);
+            uint32_t cin = __shfl_up_sync(0xffffffffu, pub_c, 1, T);
+            const int j = s - k;
+            const bool act = (j >= 0) && (j < Lp);
+            if (k == 0 && act) {
+                if ((s & 3) == 0) {
+                    quad = quad_next;
+                    bc0 = bn0;
+                    bc1 = bn1;
+                    if (s + 4 < Lp) {
+                        quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
+                        if (from_global) {
+                            const uint4 *g = gbnd + size_t((s >> 2) + 1) * (kBundlePairs * 2);
+                            bn0 = g[0];
+                            bn1 = g[1];
+                        }
+                    }
+                }
+                const uint32_t wd = (s & 2) ? quad.y : quad.x;
+                cin = (s & 1) ? (wd >> 16) : (wd & 0xffffu);
+                if (from_ring) {
+                    const uint2 v = ring_in[(g_in % D) * C + (s % C)];
+                    hin = v.x;
+                    fin = v.y;
+                } else if (from_global) {
+                    const uint4 bq = (s & 2) ? bc1 : bc0;
+                    hin = (s & 1) ? bq.z : bq.x;
+                    fin = (s & 1) ? bq.w : bq.y;
+                } else {
+                    hin = NEG_O2;
+                    fin = NEG_O2;
+                }
+            }
+            if (act) {
+                const int ta = int(cin & 0xffu), tb = int((cin >> 8) & 0xffu);
+                const uint4 *pa = reinterpret_cast<const uint4 *>(prof + ta * TR + k * R);
+                const uint4 *pb = reinterpret_cast<const uint4 *>(prof + tb * TR + k * R);
+                uint32_t wa[R / 4], wb[R / 4];
+#pragma unroll
+                for (int v = 0; v < R / 16; ++v) {
+                    const uint4 x = pa[v];
+                    const uint4 y = pb[v];
+                    wa[4 * v + 0] = x.x; wa[4 * v + 1] = x.y; wa[4 * v + 2] = x.z; wa[4 * v + 3] = x.w;
+                    wb[4 * v + 0] = y.x; wb[4 * v + 1] = y.y; wb[4 * v + 2] = y.z; wb[4 * v + 3] = y.w;
+                }
+                uint32_t f = __viaddmax_s16x2(fin, NEG_E2, hin);
+                uint32_t d = hd;
+                uint32_t xo_prev = 0;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t p = prmt(wa[r / 4], wb[r / 4], pair_sel(r % 4));
+                    const uint32_t e_r = __viaddmax_s16x2(E[r], NEG_E2, Ho[r]);
+                    const uint32_t x = __viaddmax_s16x2_relu(d, p, e_r);
+                    if (r > 0) f = __viaddmax_s16x2(f, NEG_MIN2, xo_prev);
+                    const uint32_t xo = __viaddmax_s16x2(x, NEG_O2, MIN2);
+                    const uint32_t ho = __viaddmax_s16x2(f, NEG_O2, xo);
+                    d = Ho[r];
+                    E[r] = e_r;
+                    Ho[r] = ho;
+                    xo_prev = xo;
+                }
+#pragma unroll
+                for (int r = 0; r < R; r += 2) mx = __vimax3_s16x2(mx, Ho[r], Ho[r + 1]);
+                hd = hin;
+                pub_h = Ho[R - 1];
+                pub_f = f;
+                pub_c = cin;
+                if (k == T - 1) {
+                    if (to_ring) {
+                        ring_out[(g_out % D) * C + (j % C)] = make_uint2(Ho[R - 1], f);
+                    } else if (to_global) {
+                        sb0 = sb1;
+                        sb1 = sb2;
+                        sb2 = sb3;
+                        sb3 = make_uint2(Ho[R - 1], f);
+                        if ((j & 3) == 3) {
+                            uint4 *g = gbnd + size_t(j >> 2) * (kBundlePairs * 2);
+                            g[0] = make_uint4(sb0.x, sb0.y, sb1.x, sb1.y);
+                            g[1] = make_uint4(sb2.x, sb2.y, sb3.x, sb3.y);
+                        }
+                    }
+                }
+            }
+            // Release a consumed chunk (lane 0 has used its last column) and
+            // publish a produced one (lane 31 wrote its last column).
+            if (from_ring && s < Lp && ((s % C) == C - 1 || s == Lp - 1)) {
+                if (k == 0) st_release(&empty[w], g_in + 1);
+                ++g_in;
+            }
+            if (to_ring && j31 >= 0 && j31 < Lp && ((j31 % C) == C - 1 || j31 == Lp - 1)) {
+                __syncwarp();
+                if (k == T - 1) st_release(&full[(w + 1) % NW], g_out + 1);
+                ++g_out;
+            }
+        }
+    }
+
+#pragma unroll
+    for (int dd = 16; dd >= 1; dd >>= 1) {
+        const uint32_t other = __shfl_xor_sync(0xffffffffu, mx, dd);
+        mx = __vimax3_s16x2(mx, other, other);
+    }
+    if (k == 0) red[w] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 1; i < NW; ++i) mx = __vimax3_s16x2(mx, red[i], red[i]);
+        const int hA = int(int16_t(mx & 0xffffu)) + o;
+        const int hB = int(int16_t(mx >> 16)) + o;
+        const int64_t tA = 2 * pair;
+        int mask = 0;
+        const int64_t oA = a.db.perm[tA];
+        const int64_t oB = a.db.perm[tA + 1];
+        if (oA >= 0) {
+            if (hA >= a.sat_limit) mask |= 1;
+            else scores[oA] = hA;
+        }
+        if (oB >= 0) {
+            if (hB >= a.sat_limit) mask |= 2;
+            else scores[oB] = hB;
+        }
+        if (mask) {
+            const int idx = atomicAdd(a.ovf_count + q, 1);
+            ovf_list[idx] = int32_t(pair * 4 + mask);
+            atomicAdd(a.ovf_seqs + q, __popc(mask));
+        }
+    }
+}
+
+template <int R, int NW>
+size_t intra_smem() {
+    return size_t(NW) * kProfRows * 32 * R + size_t(NW) * kDepth * kChunk * sizeof(uint2) + kProfRows * kProfRows +
+           sizeof(int) * (2 * NW + 1);
+}
+
+template <int R, int NW>
+cudaError_t launch_rn(const IntraArgs &a, cudaStream_t s) {
+    const int64_t pairs = a.pair_end - a.pair_begin;
+    if (pairs <= 0 || a.n_q <= 0) return cudaSuccess;
+    const int64_t grid = pairs * a.n_q;
+    if (grid >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
+    const size_t smem = intra_smem<R, NW>();
+    cudaError_t e = cudaFuncSetAttribute(k_intra_i16x2<R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    k_intra_i16x2<R, NW><<<unsigned(grid), NW * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool intra_config_supported(int warps, int rows) {
+    return (warps == 4 || warps == 8) && rows == 16;
+}
+
+int intra_rows_per_superpass(int warps, int rows) { return warps * 32 * rows; }
+
+cudaError_t launch_intra_i16x2(const IntraArgs &a, int warps, int rows, cudaStream_t s) {
+    if (rows == 16 && warps == 4) return launch_rn<16, 4>(a, s);
+    if (rows == 16 && warps == 8) return launch_rn<16, 8>(a, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace swdb

@@ -53,6 +53,29 @@ struct InterArgs {
     int32_t *scores;            // row of this query, original database order
     int32_t *ovf_list;          // entries pair*4 + mask of saturated halves
     int32_t *ovf_count;
+    int32_t *ovf_seqs;          // sequences flagged (one or two per list entry)
+    int32_t *status;            // nonzero after a bounded wait gave up (intra-task kernel)
+};
+
+// Arguments of the intra-task kernel: every query against the long pairs
+// [pair_begin, pair_end) in one launch, one CTA per (pair, query).
+struct IntraArgs {
+    DbView db;
+    int64_t pair_begin, pair_end;
+    int32_t n_q;
+    const int64_t *q_off;       // device, n_q+1 query offsets
+    const uint8_t *queries;     // device, all query codes
+    int32_t gap_open, gap_extend;
+    int32_t sat_limit;
+    int8_t prof8[kProfRows][kProfRows];
+    uint2 *boundary;            // per-query scratch regions (null when no query needs one)
+    int64_t boundary_stride;    // uint2 entries per query
+    int32_t *scores;            // [n_q][n_seqs]
+    int32_t *ovf_list;          // [n_q][list_stride]
+    int64_t list_stride;
+    int32_t *ovf_count;         // [n_q]
+    int32_t *ovf_seqs;          // [n_q]
+    int32_t *status;
 };
 
 // Arguments of the int32 kernel.  Work items are pairs with a mask of the
@@ -75,6 +98,9 @@ struct I32Args {
 // Launchers (return cudaGetLastError() after the launch).
 cudaError_t launch_inter_i16x2(const InterArgs &a, int lanes, int rows, cudaStream_t s);
 bool inter_config_supported(int lanes, int rows);
+cudaError_t launch_intra_i16x2(const IntraArgs &a, int warps, int rows, cudaStream_t s);
+int intra_rows_per_superpass(int warps, int rows);
+bool intra_config_supported(int warps, int rows);
 cudaError_t launch_profile32(const uint8_t *query, int32_t m, int32_t m_pad, const int32_t *matrix_host,
                              int32_t A, int32_t gap_open, int32_t *prof32, cudaStream_t s);
 cudaError_t launch_i32(const I32Args &a, int lanes, int rows, int grid, cudaStream_t s);

@@ -101,7 +101,7 @@ def test_saturation_rescored_exactly(gpu):
     seqs = [synth.random_residues(rng, int(n)) for n in rng.integers(1, 300, 60)]
     seqs[5] = long_w
     seqs[17] = mixed
-    seqs[40] = np.concatenate([mixed[:1200], long_w[:2000]])
+    seqs[40] = np.concatenate([mixed[:1200], long_w[:3000]])  # W run alone scores 33000
     db = synth.seqset_from_list(seqs)
     qs = synth.seqset_from_list([long_w, mixed, synth.random_residues(rng, 50)])
     st = _check(gpu, qs, db, synth.blosum62(), 10, 1, precision=gpu.SW_PREC_I16)
@@ -120,6 +120,34 @@ def test_saturation_inflated_matrix(gpu):
     qs = synth.seqset_from_list([base, base[:100]])
     st = _check(gpu, qs, db, S, 12, 2, precision=gpu.SW_PREC_I16)
     assert st["rescored"] >= 1
+
+
+@pytest.mark.parametrize("cutoff", [-1, 0, 64, 300])
+def test_long_sequence_split(gpu, cutoff):
+    """Sequences longer than the cutoff run in a concurrent launch; scores
+    must not depend on where the split falls."""
+    rng = np.random.default_rng(22)
+    lens = np.concatenate([rng.integers(1, 200, 100), rng.integers(400, 1500, 21), [3500, 3100]])
+    rng.shuffle(lens)
+    db = synth.seqset_from_lengths(rng, lens)
+    qs = synth.seqset_from_lengths(rng, [90, 700])
+    st = _check(gpu, qs, db, synth.blosum62(), 10, 1, long_cutoff=cutoff)
+    if cutoff > 0:
+        assert st["long_sequences"] >= (lens > cutoff).sum()
+        assert st["long_cells"] + st["inter_cells"] == st["cells"]
+    if cutoff < 0:
+        assert st["long_sequences"] == 0
+
+
+def test_intra_task_multi_superpass(gpu):
+    """Queries longer than one super-pass of the intra-task kernel (4 warps x
+    512 rows), against long sequences of ragged lengths."""
+    rng = np.random.default_rng(23)
+    lens = np.concatenate([rng.integers(65, 900, 40), rng.integers(1, 64, 30), [1, 2, 3, 4, 5]])
+    db = synth.seqset_from_lengths(rng, lens)
+    qs = synth.seqset_from_lengths(rng, [2047, 2048, 2049, 4200])
+    st = _check(gpu, qs, db, synth.blosum62(), 10, 1, long_cutoff=64)
+    assert st["long_sequences"] >= 40
 
 
 def test_edge_cases(gpu):
