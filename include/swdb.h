@@ -199,6 +199,44 @@ int sw_top_k(const int32_t *scores, int64_t n_rows, int64_t n_cols, int32_t top_
  */
 int sw_probe_alu_rate(int device, int32_t mode, double *per_sm_cycle, int32_t *sm_count);
 
+/*
+ * Score one query against a loaded database without allocating any device
+ * memory during the call.  (The paper has no counterpart: this entry point
+ * exists for callers of this library that cannot allocate at search time.)
+ *
+ * Who needs it: code that searches while a CUDA stream is being captured
+ * into a graph (allocation calls may not appear inside a capture), serving
+ * loops that must not call the allocator after start-up (an allocation can
+ * synchronise the device and has unbounded latency), and processes whose
+ * device memory is owned by another framework's pool.  sw_search allocates
+ * a workspace unless the caller passes one; this call never does.
+ *
+ *   db          a handle from sw_db_load (loading allocates; do it at set-up)
+ *   query       DEVICE pointer, m residue codes (codes >= alphabet_size
+ *               score as padding and are not checked)
+ *   m           query length (>= 0)
+ *   matrix      HOST pointer, alphabet_size^2 int32, as for sw_search
+ *   gap_open, gap_extend   as for sw_search
+ *   scores      DEVICE pointer, n_seqs int32, database in original order
+ *   stream      cudaStream_t, or NULL for the legacy default stream
+ * Results equal sw_search's for the same arguments.  The work is queued on
+ * the stream and the call returns without waiting.
+ *
+ * Scratch comes from one array of SW_NO_ALLOC_SCRATCH_BYTES in device
+ * memory that the library defines; every GPU that loads the library holds
+ * it until the process exits.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Calls share the array: calls whose work
+ * overlaps on the GPU race.  A query/database combination that needs more
+ * scratch than the array holds (multi-pass queries, m > 128, need about 4
+ * bytes per byte of the database layout) is rejected with
+ * SW_ERR_INVALID_ARG and a message; use sw_search with a workspace then.
+ * Errors: SW_ERR_INVALID_ARG, SW_ERR_OVERFLOW, SW_ERR_CUDA.
+ */
+#define SW_NO_ALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int sw_search_no_alloc(const sw_db *db, const uint8_t *query, int32_t m, const int32_t *matrix,
+                       int32_t gap_open, int32_t gap_extend, int32_t *scores, void *stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char *sw_last_error(void);
 

@@ -23,6 +23,7 @@ from .binding import (  # noqa: F401
     sw_last_error,
     sw_probe_alu_rate,
     sw_search,
+    sw_search_no_alloc,
     sw_search_workspace_size,
     sw_top_k,
     sw_version,

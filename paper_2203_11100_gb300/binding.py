@@ -77,8 +77,9 @@ def load_library():
                               ctypes.POINTER(SwSearchStats), vp]
     lib.sw_top_k.argtypes = [vp, i64, i64, i32, vp, vp]
     lib.sw_probe_alu_rate.argtypes = [ctypes.c_int, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
+    lib.sw_search_no_alloc.argtypes = [vp, vp, i32, vp, i32, i32, vp, vp]
     for name in ("sw_db_load", "sw_db_free", "sw_db_get_info", "sw_search_workspace_size", "sw_search",
-                 "sw_top_k", "sw_probe_alu_rate"):
+                 "sw_top_k", "sw_probe_alu_rate", "sw_search_no_alloc"):
         getattr(lib, name).restype = ctypes.c_int
     lib.sw_last_error.restype = ctypes.c_char_p
     lib.sw_last_error.argtypes = []
@@ -222,6 +223,25 @@ def sw_probe_alu_rate(device: int = 0, mode: int = 0):
     sms = ctypes.c_int32()
     _check(load_library().sw_probe_alu_rate(device, mode, ctypes.byref(rate), ctypes.byref(sms)))
     return float(rate.value), int(sms.value)
+
+
+def sw_search_no_alloc(handle, query, matrix, gap_open: int, gap_extend: int, scores, stream=None) -> None:
+    """One query (torch CUDA uint8 tensor) against a loaded database into a
+    device score row (torch CUDA int32 tensor of n_seqs), with no device
+    allocation during the call.  For callers that cannot allocate at search
+    time (inside CUDA graph capture, allocation-free serving loops, memory
+    owned by another pool); scratch is a fixed library-owned device array."""
+    qp, q_cuda = _addr(query, np.uint8, "query")
+    sp, s_cuda = _addr(scores, np.int32, "scores")
+    if (qp is not None and not q_cuda) or not s_cuda:
+        raise ValueError("sw_search_no_alloc takes device buffers")
+    matrix = np.ascontiguousarray(matrix, dtype=np.int32)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    m = query.numel() if query is not None else 0
+    _check(load_library().sw_search_no_alloc(handle, qp, m, matrix.ctypes.data, int(gap_open), int(gap_extend),
+                                             sp, stream))
 
 
 class Database:

@@ -326,6 +326,21 @@ struct LaunchTimer {
 
 }  // namespace
 
+// Read-only facts of a loaded database, for entry points defined in other
+// translation units.
+namespace swdb {
+bool db_describe(const sw_db *db, DbView *view, int *device, int32_t *alphabet, int64_t *codes_bytes) {
+    if (!db) return false;
+    *view = db->view();
+    *device = db->device;
+    *alphabet = db->A;
+    *codes_bytes = db->codes_bytes;
+    return true;
+}
+
+int set_error(int code, const char *msg) { return fail(code, msg); }
+}  // namespace swdb
+
 // ---------------------------------------------------------------------------
 // ABI
 

@@ -111,4 +111,11 @@ int probe_blocks_per_sm(int mode);
 cudaError_t launch_topk(const int32_t *scores, int64_t n_rows, int64_t n_cols, int32_t k,
                         void *hits, cudaStream_t s);
 
+// Facts of a loaded database (defined with the handle, in api.cu).
+}  // namespace swdb
+struct sw_db;
+namespace swdb {
+bool db_describe(const sw_db *db, DbView *view, int *device, int32_t *alphabet, int64_t *codes_bytes);
+// Record a thread-local error message and return code.
+int set_error(int code, const char *msg);
 }  // namespace swdb
