@@ -56,6 +56,9 @@ def parse_args(argv=None):
     p.add_argument("--lanes", type=int, default=0)
     p.add_argument("--rows", type=int, default=0)
     p.add_argument("--precision", type=int, default=0)
+    p.add_argument("--mode", choices=["plain", "batched"], default="plain",
+                   help="plain: one inter-task launch per query (the paper's form); "
+                        "batched: all queries in one persistent launch")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-cells", type=float, default=6e10,
@@ -235,7 +238,8 @@ def run_ours(args, dist: Dist):
     q_dev = torch.from_numpy(w.queries.residues).to(f"cuda:{dev}")
     scores = torch.empty((nq, n), dtype=torch.int32, device=f"cuda:{dev}")
     hits = torch.empty((nq, w.top_k, 2), dtype=torch.int64, device=f"cuda:{dev}")
-    kw = dict(lanes=args.lanes, rows_per_lane=args.rows, precision=args.precision)
+    kw = dict(lanes=args.lanes, rows_per_lane=args.rows, precision=args.precision,
+              mode=swdb.SW_MODE_BATCHED if args.mode == "batched" else swdb.SW_MODE_PLAIN)
 
     def step(stats=True):
         return swdb.sw_search(db.handle, q_dev, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend, w.top_k,
@@ -302,8 +306,11 @@ def run_ours(args, dist: Dist):
             "config": {"workload": args.workload, "queries": nq, "query_residues": int(w.queries.lengths.sum()),
                        "db_seqs": n, "db_residues": int(w.db.lengths.sum()), "cells_per_step": cells_step,
                        "matrix": "BLOSUM62", "gap_open": w.gap_open, "gap_extend": w.gap_extend,
-                       "top_k": w.top_k, "mode": "plain (one launch per query)",
-                       "lanes": st0["lanes_used"], "rows_per_lane": st0["rows_per_lane_used"],
+                       "top_k": w.top_k,
+                       "mode": "plain (one launch per query)" if args.mode == "plain"
+                               else "batched (query pairs, one persistent launch)",
+                       "launch_shape": "lanes x rows per lane chosen per query by the library's rate model"
+                                       if not (args.lanes or args.rows) else f"{args.lanes}x{args.rows}",
                        "l2": "inputs larger than L2 (database layout "
                              f"{db.info()['device_bytes'] / 1e6:.0f} MB > 129 MB), no flush",
                        "parallelism": f"{dist.world} independent GPU(s)"},

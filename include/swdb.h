@@ -83,8 +83,8 @@ typedef struct {
     int64_t long_cutoff;      /* database sequences longer than this are scored by the
                                  intra-task kernel; 0 = library default, <0 = never */
     int32_t lanes;            /* lanes per database-sequence pair in the inter-task kernel
-                                 (4, 8, 16 or 32); 0 = library choice */
-    int32_t rows_per_lane;    /* query rows held per lane (16 or 32); 0 = library choice */
+                                 (4, 8, 16 or 32); 0 = chosen per query by the library */
+    int32_t rows_per_lane;    /* query rows held per lane (16 or 32); 0 = chosen per query */
     void *workspace;          /* caller-owned device scratch, or NULL for the handle's own */
     size_t workspace_bytes;   /* size of workspace */
 } sw_search_opts;
@@ -97,7 +97,7 @@ typedef struct {
     int64_t long_sequences; /* database sequences sent to the intra-task kernel */
     int32_t precision_used; /* sw_precision actually used (1 or 2) */
     int32_t mode_used;      /* sw_mode actually used (1 or 2) */
-    int32_t lanes_used;
+    int32_t lanes_used;     /* inter-task launch shape of the last query */
     int32_t rows_per_lane_used;
     int32_t launches;       /* kernels this call launched */
     float inter_ms;         /* CUDA-event time of the inter-task kernel launches */

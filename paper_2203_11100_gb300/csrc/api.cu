@@ -147,10 +147,36 @@ struct Carver {
     }
 };
 
+// Launch shapes of the int16x2 inter-task kernel that the planner chooses
+// from, with their measured cell-update rates on GB300 (GCUPS, long queries,
+// database without long sequences).  A query of m rows is padded to whole
+// strips of lanes*rows rows, so the predicted time is
+// ceil(m / (lanes*rows)) * lanes*rows / rate.
+struct ShapeRate {
+    int lanes, rows;
+    double gcups;
+};
+constexpr ShapeRate kShapes[] = {{8, 16, 4600.0}, {16, 16, 4900.0}, {8, 32, 5600.0}, {16, 32, 5450.0}};
+
+void choose_shape(int64_t m, int *lanes, int *rows) {
+    double best = 1e300;
+    for (const ShapeRate &c : kShapes) {
+        const int64_t tr = int64_t(c.lanes) * c.rows;
+        const double t = double((m + tr - 1) / tr * tr) / c.gcups;
+        if (t < best) {
+            best = t;
+            *lanes = c.lanes;
+            *rows = c.rows;
+        }
+    }
+}
+
 struct Plan {
     int precision = SW_PREC_I16;
     int mode = SW_MODE_PLAIN;
-    int lanes = 8, rows = 16;        // int16x2 kernel
+    bool auto_shape = true;          // int16x2 kernel: shape chosen per query ...
+    int lanes = 8, rows = 16;        // ... unless the caller fixed it
+    int min_tr = 128;                // smallest strip height used
     int lanes32 = 8, rows32 = 16;    // int32 kernel
     int64_t long_end_pair = 0;       // pairs [0, long_end_pair) hold the long sequences
     int64_t n_long = 0;              // real sequences among them
@@ -159,6 +185,13 @@ struct Plan {
     int warps_long = 4;
     int64_t long_codes_bytes = 0;          // layout bytes of the long bundles (a prefix)
     bool need_long_boundary = false;
+    // batched mode: query pairs (a = longer, b = next, -1 if none), persistent grid
+    std::vector<int32_t> qp_a, qp_b;
+    int32_t batch_grid = 0;
+    int64_t batch_seq_begin = 0;
+    int32_t batch_max_cols = 0;
+    int32_t batch_max_m = 0;
+    bool batch_scratch = false;
     int32_t max_m = 0;
     int64_t total_m = 0;
     bool need_boundary = false;
@@ -205,16 +238,36 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
 
     const int mode = opts ? opts->mode : SW_MODE_AUTO;
     if (mode < 0 || mode > SW_MODE_BATCHED) return fail(SW_ERR_INVALID_ARG, "unknown mode");
-    if (mode == SW_MODE_BATCHED) return fail(SW_ERR_UNSUPPORTED, "batched mode not available yet");
-    p.mode = SW_MODE_PLAIN;
+    // The batched kernel is int16x2 only; an int32 search runs in the plain form.
+    p.mode = (mode == SW_MODE_BATCHED && p.precision == SW_PREC_I16) ? SW_MODE_BATCHED : SW_MODE_PLAIN;
 
     int lanes = opts && opts->lanes ? opts->lanes : 8;
     int rows = opts && opts->rows_per_lane ? opts->rows_per_lane : 16;
-    if (p.precision == SW_PREC_I16) {
-        if (!inter_config_supported(lanes, rows))
-            return fail(SW_ERR_UNSUPPORTED, "lanes/rows_per_lane combination not built");
+    if (p.mode == SW_MODE_BATCHED) {
+        if (!(opts && (opts->lanes || opts->rows_per_lane))) rows = 32;
+        if (!batch_config_supported(lanes, rows))
+            return fail(SW_ERR_UNSUPPORTED, "lanes/rows_per_lane combination not built for the batched kernel");
+        p.auto_shape = false;
         p.lanes = lanes;
         p.rows = rows;
+        p.min_tr = lanes * rows;
+    } else if (p.precision == SW_PREC_I16) {
+        p.auto_shape = !(opts && (opts->lanes || opts->rows_per_lane));
+        if (!p.auto_shape) {
+            if (!inter_config_supported(lanes, rows))
+                return fail(SW_ERR_UNSUPPORTED, "lanes/rows_per_lane combination not built");
+            p.lanes = lanes;
+            p.rows = rows;
+            p.min_tr = lanes * rows;
+        } else {
+            p.min_tr = 1 << 30;
+            for (int32_t i = 0; i < n_q; ++i) {
+                int l = 8, r = 16;
+                choose_shape(q_offsets[i + 1] - q_offsets[i], &l, &r);
+                p.min_tr = std::min(p.min_tr, l * r);
+            }
+            if (n_q == 0) p.min_tr = 128;
+        }
     }
     if (p.precision == SW_PREC_I32 && opts && (opts->lanes || opts->rows_per_lane)) {
         if (!i32_config_supported(lanes, rows))
@@ -235,7 +288,30 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
     p.n_long = std::min<int64_t>(nlb * kBundleSeqs, db->n_seqs);
     p.long_codes_bytes = nlb < db->n_bundles ? db->h_bundle_off[size_t(nlb)] : db->codes_bytes;
     p.need_long_boundary = nlb > 0 && p.max_m > intra_rows_per_superpass(p.warps_long, p.rows_long);
-    p.need_boundary = p.max_m > std::min(p.lanes * p.rows, p.lanes32 * p.rows32);
+    p.need_boundary = p.max_m > std::min(p.min_tr, p.lanes32 * p.rows32);
+
+    if (p.mode == SW_MODE_BATCHED) {
+        // Pair queries of similar length: sort the non-empty ones longest first
+        // and pair neighbours, so the shorter of a pair pads few rows.
+        std::vector<int32_t> idx;
+        for (int32_t i = 0; i < n_q; ++i)
+            if (q_offsets[i + 1] > q_offsets[i]) idx.push_back(i);
+        std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) {
+            return q_offsets[x + 1] - q_offsets[x] > q_offsets[y + 1] - q_offsets[y];
+        });
+        for (size_t i = 0; i < idx.size(); i += 2) {
+            p.qp_a.push_back(idx[i]);
+            p.qp_b.push_back(i + 1 < idx.size() ? idx[i + 1] : -1);
+        }
+        p.batch_max_m = idx.empty() ? 0 : int32_t(q_offsets[idx[0] + 1] - q_offsets[idx[0]]);
+        p.batch_grid = batch_slots(p.lanes, p.rows, std::max(1, db->sm_count));
+        if (p.batch_grid <= 0) return fail(SW_ERR_CUDA, "could not size the persistent grid");
+        p.batch_seq_begin = p.long_end_pair * 2;
+        p.batch_max_cols = p.batch_seq_begin < db->n_sorted
+                               ? int32_t(round_up(db->h_len[size_t(p.batch_seq_begin)], 4))
+                               : 0;
+        p.batch_scratch = p.batch_max_m > p.lanes * p.rows && p.batch_max_cols > 0;
+    }
     *plan = p;
     return SW_OK;
 }
@@ -248,6 +324,8 @@ struct Buffers {
     uint2 *long_boundary = nullptr;   // [n_q] regions of long_codes_bytes/2 entries
     int64_t *q_off = nullptr;         // device copy of the query offsets
     int32_t *prof32 = nullptr;
+    int32_t *qp = nullptr;            // batched mode: qp_a then qp_b
+    uint2 *batch_scratch = nullptr;   // batched mode: per CTA slot boundary rows
     int32_t *ovf_list = nullptr;
     int32_t *counters = nullptr;   // [n_q] list lengths, [n_q] work counters, [n_q] flagged sequences,
                                    // then one status word
@@ -270,7 +348,14 @@ size_t carve(const sw_db *db, const Plan &p, int32_t n_q, int32_t top_k, bool q_
     // one overflow list per query: queries run concurrently with the long-sequence launch
     x.ovf_list = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(std::max<int32_t>(n_q, 1)) *
                                                size_t(std::max<int64_t>(db->n_sorted / 2, 1))));
-    x.counters = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(3 * std::max<int32_t>(n_q, 1) + 1)));
+    if (p.mode == SW_MODE_BATCHED) {
+        x.qp = static_cast<int32_t *>(c.take(sizeof(int32_t) * 2 * std::max<size_t>(p.qp_a.size(), 1)));
+        if (p.batch_scratch)
+            x.batch_scratch = static_cast<uint2 *>(c.take(sizeof(uint2) * size_t(p.batch_grid) *
+                                                          size_t(kCtaThreads / p.lanes) * size_t(p.batch_max_cols)));
+    }
+    // [n_q] list lengths, [n_q] work counters, [n_q] flagged, status, tile counter
+    x.counters = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(3 * std::max<int32_t>(n_q, 1) + 2)));
     *b = x;
     return c.used + 256;
 }
@@ -494,6 +579,7 @@ int sw_search_workspace_size(const sw_db *db, const int64_t *q_offsets, int32_t 
     if (!db || !bytes || (n_q > 0 && !q_offsets)) return fail(SW_ERR_INVALID_ARG, "NULL argument");
     if (n_q < 0 || top_k < 0) return fail(SW_ERR_INVALID_ARG, "negative count");
     Plan p;
+    DeviceGuard guard(db->device);
     std::vector<int32_t> zero(size_t(db->A) * db->A, 0);
     int rc = make_plan(db, q_offsets, n_q, zero.data(), 0, 0, opts, &p);
     if (rc) return rc;
@@ -567,7 +653,8 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
     if (!q_dev && plan.total_m > 0)
         SW_CUDA_TRY(cudaMemcpyAsync(buf.queries, queries, size_t(plan.total_m), cudaMemcpyHostToDevice, st));
     int32_t *d_status = buf.counters + 3 * size_t(std::max<int32_t>(n_q, 1));
-    SW_CUDA_TRY(cudaMemsetAsync(buf.counters, 0, sizeof(int32_t) * (3 * size_t(std::max<int32_t>(n_q, 1)) + 1), st));
+    int32_t *d_tiles = d_status + 1;
+    SW_CUDA_TRY(cudaMemsetAsync(buf.counters, 0, sizeof(int32_t) * (3 * size_t(std::max<int32_t>(n_q, 1)) + 2), st));
 
     // int8 profile table for the int16x2 kernel: [query code][db code] = S + o.
     InterArgs ia;
@@ -601,8 +688,9 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
     // (1) Long sequences of every query: one intra-task launch on the side
     //     stream, concurrent with the per-query launches below.
     const bool split = plan.precision == SW_PREC_I16 && plan.long_end_pair > 0 && n_q > 0 && db->n_seqs > 0;
-    if (split) {
+    if ((split || plan.mode == SW_MODE_BATCHED) && n_q > 0)
         SW_CUDA_TRY(cudaMemcpyAsync(buf.q_off, q_offsets, sizeof(int64_t) * size_t(n_q + 1), cudaMemcpyHostToDevice, st));
+    if (split) {
         IntraArgs la;
         memset(&la, 0, sizeof la);
         la.db = db->view();
@@ -629,8 +717,50 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
         SW_CUDA_TRY(cudaEventRecord(db->ev_join, db->side));
     }
 
-    // (2) One inter-task launch per query over the rest of the database.
-    for (int32_t qi = 0; qi < n_q && db->n_seqs > 0; ++qi) {
+    // (2b) Batched form: every query pair against the rest of the database in
+    //      one persistent launch.
+    int last_lanes = plan.lanes, last_rows = plan.rows;
+    if (plan.mode == SW_MODE_BATCHED && db->n_seqs > 0) {
+        for (int32_t qi = 0; qi < n_q; ++qi)
+            if (q_offsets[qi + 1] == q_offsets[qi])
+                SW_CUDA_TRY(cudaMemsetAsync(d_scores + size_t(qi) * size_t(db->n_seqs), 0,
+                                            sizeof(int32_t) * size_t(db->n_seqs), st));
+        const int32_t n_qp = int32_t(plan.qp_a.size());
+        const int spc = kCtaThreads / plan.lanes;
+        if (n_qp > 0 && plan.batch_seq_begin < db->n_sorted) {
+            std::vector<int32_t> qp(plan.qp_a);
+            qp.insert(qp.end(), plan.qp_b.begin(), plan.qp_b.end());
+            SW_CUDA_TRY(cudaMemcpyAsync(buf.qp, qp.data(), sizeof(int32_t) * qp.size(), cudaMemcpyHostToDevice, st));
+            BatchArgs ba;
+            memset(&ba, 0, sizeof ba);
+            ba.db = db->view();
+            ba.seq_begin = plan.batch_seq_begin;
+            ba.seq_end = db->n_sorted;
+            ba.n_chunks = int32_t((db->n_sorted - plan.batch_seq_begin + spc - 1) / spc);
+            ba.n_qp = n_qp;
+            ba.qp_a = buf.qp;
+            ba.qp_b = buf.qp + n_qp;
+            ba.q_off = buf.q_off;
+            ba.queries = d_queries;
+            ba.gap_open = gap_open;
+            ba.gap_extend = gap_extend;
+            ba.sat_limit = plan.sat_limit;
+            memcpy(ba.prof8, ia.prof8, sizeof ba.prof8);
+            ba.scratch = buf.batch_scratch;
+            ba.max_cols = plan.batch_max_cols;
+            ba.scratch_stride = int64_t(spc) * plan.batch_max_cols;
+            ba.scores = d_scores;
+            ba.ovf_list = buf.ovf_list;
+            ba.list_stride = list_stride;
+            ba.ovf_count = buf.counters;
+            ba.ovf_seqs = buf.counters + 2 * n_q;
+            ba.tile_counter = d_tiles;
+            TIMED(LaunchTimer::INTER, launch_batch_i16x2(ba, plan.lanes, plan.rows, plan.batch_grid, st));
+        }
+    }
+
+    // (2) Plain form: one inter-task launch per query over the rest of the database.
+    for (int32_t qi = 0; qi < n_q && db->n_seqs > 0 && plan.mode == SW_MODE_PLAIN; ++qi) {
         const int32_t m = int32_t(q_offsets[qi + 1] - q_offsets[qi]);
         int32_t *row = d_scores + size_t(qi) * size_t(db->n_seqs);
         if (m == 0) {
@@ -647,7 +777,11 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
             ia.ovf_seqs = buf.counters + 2 * n_q + qi;
             ia.pair_begin = plan.long_end_pair;
             ia.pair_end = n_pairs;
-            TIMED(LaunchTimer::INTER, launch_inter_i16x2(ia, plan.lanes, plan.rows, st));
+            int lanes = plan.lanes, rows = plan.rows;
+            if (plan.auto_shape) choose_shape(m, &lanes, &rows);
+            last_lanes = lanes;
+            last_rows = rows;
+            TIMED(LaunchTimer::INTER, launch_inter_i16x2(ia, lanes, rows, st));
         } else {
             const int tr32 = plan.lanes32 * plan.rows32;
             const int32_t m_pad = int32_t(round_up(m, tr32));
@@ -713,8 +847,8 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
         stats->inter_cells = stats->cells - stats->long_cells;
         stats->precision_used = plan.precision;
         stats->mode_used = plan.mode;
-        stats->lanes_used = plan.precision == SW_PREC_I16 ? plan.lanes : plan.lanes32;
-        stats->rows_per_lane_used = plan.precision == SW_PREC_I16 ? plan.rows : plan.rows32;
+        stats->lanes_used = plan.precision == SW_PREC_I16 ? last_lanes : plan.lanes32;
+        stats->rows_per_lane_used = plan.precision == SW_PREC_I16 ? last_rows : plan.rows32;
         stats->launches = timer.launches;
         stats->inter_ms = timer.total(LaunchTimer::INTER);
         stats->rescore_ms = timer.total(LaunchTimer::RESCORE);

@@ -1,0 +1,313 @@
+// Batched inter-task scoring: many queries in one persistent launch.
+//
+// Same recurrences and biased int16x2 arithmetic as k_inter16.cu (Section
+// 2.2 inter-task parallelism; affine gaps as in Section 4.1), packed the
+// other way round: the two halves of a register hold TWO QUERIES (of similar
+// length, paired by the host) against the SAME database sequence.  Their
+// profile is then one int16x2 word per (residue, row) -- S(q1_i, a) + o in
+// the low half, S(q2_i, a) + o in the high half -- loaded ready to add, so
+// the byte permute the sequence-pair packing needs disappears.
+//
+// The launch is persistent: one CTA per resident slot pulls tiles
+// (database chunk, query pair) from an atomic counter, longest chunks first
+// and all query pairs of a chunk together (the chunk's codes stay in L2).
+// A chunk is 256/T consecutive sorted sequences, one per subwarp of T lanes.
+// Queries longer than one strip (T*R rows) take several passes; the strip
+// boundary of each subwarp goes to a scratch region owned by the CTA slot,
+// reused tile after tile, so it stays in L2.
+//
+// Saturated (query, sequence) results are appended to per-query lists, with
+// the two sequences of a database pair merged into one entry (pair*4 + mask)
+// because the int32 rescore uses the pair's boundary region for both.
+#include "swdb_internal.cuh"
+
+namespace swdb {
+namespace {
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gmem_src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack2(int v) {
+    uint32_t h = uint32_t(v) & 0xffffu;
+    return h | (h << 16);
+}
+
+template <int T, int R>
+__global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_batch_i16x2(const __grid_constant__ BatchArgs a) {
+    static_assert(R % 4 == 0, "rows per lane must be a multiple of 4");
+    constexpr int SPC = kCtaThreads / T;        // sequences per chunk (one per subwarp)
+    constexpr int TR = T * R;
+    extern __shared__ __align__(16) uint32_t prof[];   // [32 residues][TR words], see the fill
+    __shared__ int8_t mat[kProfRows * kProfRows];
+    __shared__ __align__(16) uint2 bstage[SPC][8];
+    __shared__ int sh_tile;
+    __shared__ int sh_mask[SPC / 2];
+
+    const int tid = threadIdx.x;
+    const int k = tid % T;
+    const int sub = tid / T;
+    for (int i = tid; i < kProfRows * kProfRows; i += kCtaThreads) mat[i] = (&a.prof8[0][0])[i];
+
+    const int o = a.gap_open;
+    const uint32_t BNEG_O2 = pack2(32768 - o);
+    const uint32_t ADD_NEG_E = pack2(-a.gap_extend);
+    const uint32_t OO = uint32_t(o) | (uint32_t(o) << 16);
+    const uint32_t BZERO2 = 0x80008000u;
+    const int64_t n_tiles = int64_t(a.n_chunks) * a.n_qp;
+    uint2 *slot_scratch = a.scratch ? a.scratch + int64_t(blockIdx.x) * a.scratch_stride + int64_t(sub) * a.max_cols
+                                    : nullptr;
+
+    for (;;) {
+        __syncthreads();   // previous tile done with shared state
+        if (tid == 0) sh_tile = atomicAdd(a.tile_counter, 1);
+        if (tid < SPC / 2) sh_mask[tid] = 0;
+        __syncthreads();
+        const int64_t tile = sh_tile;
+        if (tile >= n_tiles) break;
+        const int chunk = int(tile / a.n_qp);
+        const int qp = int(tile % a.n_qp);
+        const int qa = a.qp_a[qp], qb = a.qp_b[qp];
+        const int64_t qa0 = a.q_off[qa];
+        const int ma = int(a.q_off[qa + 1] - qa0);
+        int64_t qb0 = 0;
+        int mb = 0;
+        if (qb >= 0) {
+            qb0 = a.q_off[qb];
+            mb = int(a.q_off[qb + 1] - qb0);
+        }
+        const int m = ma > mb ? ma : mb;
+        const int npass = (m + TR - 1) / TR;
+
+        const int64_t t = a.seq_begin + int64_t(chunk) * SPC + sub;   // this subwarp's sorted sequence
+        const bool valid = t < a.seq_end;
+        int Lp = 0;
+        int64_t pair = 0;
+        int h = 0;
+        const uint2 *cptr = nullptr;
+        if (valid) {
+            pair = t >> 1;
+            h = int(t & 1);
+            Lp = (a.db.len[t] + 3) & ~3;
+            const int64_t b = pair / kBundlePairs;
+            cptr = reinterpret_cast<const uint2 *>(a.db.codes + a.db.bundle_off[b]) + int(pair % kBundlePairs);
+        }
+        const int Lw = __reduce_max_sync(0xffffffffu, Lp);
+        uint32_t mx = BZERO2;
+
+        for (int pass = 0; pass < npass; ++pass) {
+            __syncthreads();
+            // Profile strip, word layout [a][row group v][lane k][row%4]: lane k's
+            // rows 4v..4v+3 are one 16-byte slot at a*TR + v*4T + 4k (quarter-warp
+            // lanes read consecutive slots).  Word = S(qa_i, a)+o | S(qb_i, a)+o << 16.
+            for (int w = tid; w < kProfRows * TR; w += kCtaThreads) {
+                const int res = w / TR;
+                const int rem = w % TR;
+                const int v = rem / (4 * T);
+                const int rem2 = rem % (4 * T);
+                const int kk = rem2 >> 2;
+                const int row = pass * TR + kk * R + v * 4 + (rem2 & 3);
+                int lo = -128, hi = -128;
+                if (row < ma) {
+                    const int c = a.queries[qa0 + row];
+                    if (c < kProfRows) lo = mat[c * kProfRows + res];
+                }
+                if (row < mb) {
+                    const int c = a.queries[qb0 + row];
+                    if (c < kProfRows) hi = mat[c * kProfRows + res];
+                }
+                prof[w] = (uint32_t(lo) & 0xffffu) | (uint32_t(hi) << 16);
+            }
+            __syncthreads();
+            if (Lw == 0) continue;
+
+            uint32_t E[R], Ho[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) { E[r] = BNEG_O2; Ho[r] = BNEG_O2; }
+            uint32_t hd = BNEG_O2;
+            uint32_t pub_h = BNEG_O2, pub_f = BNEG_O2, pub_c = 0;
+            const bool last_pass = (pass + 1 == npass);
+            uint2 quad = make_uint2(0, 0), quad_next = make_uint2(0, 0);
+            uint2 *stg = bstage[sub];
+            const uint4 *gsrc = reinterpret_cast<const uint4 *>(slot_scratch);
+            if (k == 0 && Lp > 0) {
+                quad_next = __ldg(cptr);
+                if (pass > 0) {
+                    cp_async16(stg + 0, gsrc);
+                    cp_async16(stg + 2, gsrc + 1);
+                    cp_async_commit();
+                    if (4 < Lp) {
+                        cp_async16(stg + 4, gsrc + 2);
+                        cp_async16(stg + 6, gsrc + 3);
+                    }
+                    cp_async_commit();
+                }
+            }
+            const int steps = Lw + T - 1;
+            for (int s = 0; s < steps; ++s) {
+                uint32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1, T);
+                uint32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1, T);
+                uint32_t cin = __shfl_up_sync(0xffffffffu, pub_c, 1, T);
+                const int j = s - k;
+                const bool act = (j >= 0) && (j < Lp);
+                if (k == 0 && act) {
+                    if ((s & 3) == 0) {
+                        quad = quad_next;
+                        if (s + 4 < Lp) quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
+                        if (pass > 0) cp_async_wait1();
+                    }
+                    const uint32_t wd = (s & 2) ? quad.y : quad.x;
+                    cin = (wd >> (16 * (s & 1) + 8 * h)) & 0xffu;
+                    if (pass == 0) {
+                        hin = BNEG_O2;
+                        fin = BNEG_O2;
+                    } else {
+                        const uint2 bv = stg[((s >> 2) & 1) * 4 + (s & 3)];
+                        hin = bv.x;
+                        fin = bv.y;
+                        if ((s & 3) == 3) {
+                            if (s + 5 < Lp) {
+                                const uint4 *g = gsrc + size_t((s >> 2) + 2) * 2;
+                                cp_async16(stg + ((s >> 2) & 1) * 4, g);
+                                cp_async16(stg + ((s >> 2) & 1) * 4 + 2, g + 1);
+                            }
+                            cp_async_commit();
+                        }
+                    }
+                }
+                if (act) {
+                    const uint4 *pp = reinterpret_cast<const uint4 *>(prof + cin * TR + k * 4);
+                    uint32_t P[R];
+#pragma unroll
+                    for (int v = 0; v < R / 4; ++v) {
+                        const uint4 x = pp[v * T];
+                        P[4 * v + 0] = x.x; P[4 * v + 1] = x.y; P[4 * v + 2] = x.z; P[4 * v + 3] = x.w;
+                    }
+                    uint32_t f = fin;
+                    uint32_t d = hd;
+                    uint32_t yprev = 0;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const uint32_t e_r = __viaddmax_u16x2(E[r], ADD_NEG_E, Ho[r]);
+                        const uint32_t x = __viaddmax_u16x2(d, P[r], e_r);
+                        const uint32_t y = __vimax3_u16x2(f, x, BZERO2);
+                        const uint32_t ho = y - OO;
+                        f = __viaddmax_u16x2(f, ADD_NEG_E, ho);
+                        d = Ho[r];
+                        E[r] = e_r;
+                        Ho[r] = ho;
+                        if (r & 1) mx = __vimax3_u16x2(mx, yprev, y);
+                        yprev = y;
+                    }
+                    hd = hin;
+                    pub_h = Ho[R - 1];
+                    pub_f = f;
+                    pub_c = cin;
+                    if (k == T - 1 && !last_pass) slot_scratch[j] = make_uint2(Ho[R - 1], f);
+                }
+            }
+        }
+
+#pragma unroll
+        for (int dd = T / 2; dd >= 1; dd >>= 1) {
+            const uint32_t other = __shfl_xor_sync(0xffffffffu, mx, dd, T);
+            mx = __vimax3_u16x2(mx, other, other);
+        }
+        int64_t orig = -1;
+        if (valid && k == 0) {
+            orig = a.db.perm[t];
+            if (orig >= 0) {
+                const int ha = int(mx & 0xffffu) - 32768;
+                const int hb = int(mx >> 16) - 32768;
+                if (ha >= a.sat_limit) atomicOr(&sh_mask[sub >> 1], 1 << (2 * h));
+                else a.scores[int64_t(qa) * a.db.n_seqs + orig] = ha;
+                if (qb >= 0) {
+                    if (hb >= a.sat_limit) atomicOr(&sh_mask[sub >> 1], 2 << (2 * h));
+                    else a.scores[int64_t(qb) * a.db.n_seqs + orig] = hb;
+                }
+            }
+        }
+        __syncthreads();
+        // One list entry per (query, database pair) with the mask of saturated halves.
+        if (tid < SPC / 2 && sh_mask[tid]) {
+            const int mk = sh_mask[tid];
+            const int64_t p = (a.seq_begin + int64_t(chunk) * SPC) / 2 + tid;
+            const int m_a = (mk & 1) | ((mk >> 1) & 2);          // bits for query qa: halves 0,1
+            const int m_b = ((mk >> 1) & 1) | ((mk >> 2) & 2);   // bits for query qb
+            if (m_a) {
+                const int idx = atomicAdd(a.ovf_count + qa, 1);
+                a.ovf_list[int64_t(qa) * a.list_stride + idx] = int32_t(p * 4 + m_a);
+                atomicAdd(a.ovf_seqs + qa, __popc(m_a));
+            }
+            if (m_b) {
+                const int idx = atomicAdd(a.ovf_count + qb, 1);
+                a.ovf_list[int64_t(qb) * a.list_stride + idx] = int32_t(p * 4 + m_b);
+                atomicAdd(a.ovf_seqs + qb, __popc(m_b));
+            }
+        }
+    }
+}
+
+template <int T, int R>
+size_t batch_smem() {
+    return size_t(kProfRows) * T * R * sizeof(uint32_t);
+}
+
+template <int T, int R>
+cudaError_t launch_tr(const BatchArgs &a, int grid, cudaStream_t s) {
+    const size_t smem = batch_smem<T, R>();
+    cudaError_t e = cudaFuncSetAttribute(k_batch_i16x2<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    k_batch_i16x2<T, R><<<grid, kCtaThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int T, int R>
+int slots_tr(int sms) {
+    int per_sm = 0;
+    const size_t smem = batch_smem<T, R>();
+    if (cudaFuncSetAttribute(k_batch_i16x2<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_i16x2<T, R>, kCtaThreads, smem) != cudaSuccess)
+        return 0;
+    return per_sm * sms;
+}
+
+}  // namespace
+
+bool batch_config_supported(int lanes, int rows) {
+    switch (lanes * 100 + rows) {
+        case 816: case 824: case 832: case 1616: case 1624: case 1632: return true;
+        default: return false;
+    }
+}
+
+int batch_slots(int lanes, int rows, int sms) {
+    switch (lanes * 100 + rows) {
+        case 816: return slots_tr<8, 16>(sms);
+        case 824: return slots_tr<8, 24>(sms);
+        case 832: return slots_tr<8, 32>(sms);
+        case 1624: return slots_tr<16, 24>(sms);
+        case 1616: return slots_tr<16, 16>(sms);
+        case 1632: return slots_tr<16, 32>(sms);
+        default: return 0;
+    }
+}
+
+cudaError_t launch_batch_i16x2(const BatchArgs &a, int lanes, int rows, int grid, cudaStream_t s) {
+    switch (lanes * 100 + rows) {
+        case 816: return launch_tr<8, 16>(a, grid, s);
+        case 824: return launch_tr<8, 24>(a, grid, s);
+        case 832: return launch_tr<8, 32>(a, grid, s);
+        case 1624: return launch_tr<16, 24>(a, grid, s);
+        case 1616: return launch_tr<16, 16>(a, grid, s);
+        case 1632: return launch_tr<16, 32>(a, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace swdb

@@ -19,14 +19,20 @@
 //   S(q_i, a) + o, laid out [residue a][lane k][row r], so each lane fetches
 //   its R rows for one database residue with 128-bit loads that are free of
 //   bank conflicts (row stride T*R bytes is a multiple of 128 for T*R >= 128).
-// * Values are kept shifted: the registers carry Ho = H - o, E and F.  Per
-//   cell pair:   E' = max(E - e, Ho_left)                 (viaddmax)
-//                X  = max(Ho_diag + S + o, E', 0)          (viaddmax_relu)
-//                F' = max(F - min(e,o), X_up - o)          (viaddmax; the only
-//                                                           loop-carried op)
-//                Xo = X - o,  Ho = max(F' - o, Xo)         (2 x viaddmax)
-//   which is the recurrence H = max(0, Hdiag + S, E, F) rewritten so the
-//   row-to-row dependency is one instruction long.
+// * Values are kept shifted and biased: every int16 quantity v is held as
+//   the unsigned halfword v + 32768 (offset binary), so unsigned DPX max/add
+//   orders them correctly, adding a negative constant is a modular add, and
+//   subtracting the gap-open penalty from a non-negative H is a plain 32-bit
+//   integer subtraction that never borrows across the halves.  That last
+//   operation runs outside the ALU pipe the DPX instructions saturate.  The
+//   registers carry Ho = H - o and E per row; F flows down the rows.  Per
+//   cell pair:   E' = max(E - e, Ho_left)            (viaddmax)
+//                X  = max(Ho_diag + S + o, E')       (viaddmax)
+//                H  = max(F, X, 0)                   (vimax3)
+//                Ho = H - o                          (32-bit subtract)
+//                F_below = max(F - e, Ho)            (viaddmax)
+//   which is the recurrence H = max(0, Hdiag + S, E, F) with Hdiag + S =
+//   Ho_diag + (S + o).  The running maximum takes two rows per vimax3.
 // * Saturation: every value stays below the running maximum of H plus the
 //   largest matrix entry, so if that maximum stays below
 //   32767 - max(S) no int16 operation overflowed and the score is exact.
@@ -49,6 +55,16 @@ __host__ __device__ constexpr uint32_t pair_sel(int c) {
     return uint32_t(c) | (uint32_t(c | 8) << 4) | (uint32_t(4 + c) << 8) | (uint32_t((4 + c) | 8) << 12);
 }
 
+// 16-byte global -> shared copy that completes asynchronously (no registers
+// held while it is in flight), and the matching commit / wait.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gmem_src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t pack2(int v) {
     uint32_t h = uint32_t(v) & 0xffffu;
     return h | (h << 16);
@@ -64,6 +80,9 @@ __global__ void __launch_bounds__(kCtaThreads) k_inter_i16x2(const __grid_consta
 
     __shared__ __align__(16) int8_t prof[PROF_BYTES];
     __shared__ int8_t mat[kProfRows * kProfRows];
+    // Per subwarp: two 4-column groups of the previous strip's bottom row
+    // (B(Ho), B(F) per column), filled by lane 0 with cp.async one group ahead.
+    __shared__ __align__(16) uint2 bstage[PAIRS_PER_CTA][8];
 
     const int tid = threadIdx.x;
     const int k = tid % T;               // lane within the subwarp
@@ -84,10 +103,11 @@ __global__ void __launch_bounds__(kCtaThreads) k_inter_i16x2(const __grid_consta
     const int Lw = __reduce_max_sync(0xffffffffu, Lp);   // warp-uniform column count
 
     const int o = a.gap_open;
-    const uint32_t NEG_O2 = pack2(-o);
-    const uint32_t NEG_E2 = pack2(-a.gap_extend);
-    const uint32_t NEG_MIN2 = pack2(-(a.gap_extend < o ? a.gap_extend : o));
-    const uint32_t MIN2 = 0x80008000u;
+    // Biased constants (see the header comment): B(v) = v + 32768 per half.
+    const uint32_t BNEG_O2 = pack2(32768 - o);        // B(-o)
+    const uint32_t ADD_NEG_E = pack2(-a.gap_extend);  // modular addend "- e"
+    const uint32_t OO = uint32_t(o) | (uint32_t(o) << 16);
+    const uint32_t BZERO2 = 0x80008000u;              // B(0)
 
     // Boundary scratch of this bundle: 8*Lb uint2 entries starting at
     // uint2 index off/2, grouped as [column/4][slot][column%4] so lane 0 of a
@@ -101,15 +121,22 @@ __global__ void __launch_bounds__(kCtaThreads) k_inter_i16x2(const __grid_consta
     }
 
     const int npass = (a.m + TR - 1) / TR;
-    uint32_t mx = NEG_O2;                  // running max of H - o, both halves
+    uint32_t mx = BZERO2;                  // running max of B(H), both halves
 
     for (int pass = 0; pass < npass; ++pass) {
         __syncthreads();
-        // Profile strip for rows pass*TR .. pass*TR+TR-1, layout [a][k][r].
+        // Profile strip for rows pass*TR .. pass*TR+TR-1, layout
+        // [residue a][half h][lane k][16 rows]: lane k's rows 16h..16h+15 sit at
+        // a*TR + h*T*16 + k*16, so the 8 lanes of a quarter-warp read 8
+        // consecutive 16-byte slots (no bank conflicts) and a lane's second
+        // half is a compile-time offset from its first.
         for (int w = tid; w < PROF_BYTES / 4; w += kCtaThreads) {
             const int e0 = w * 4;
             const int res = e0 / TR;
-            const int row0 = pass * TR + (e0 % TR);
+            const int within = e0 % TR;
+            const int row0 = pass * TR + within;
+            const int kk = within / R, rr = within % R;
+            const int phys = res * TR + (rr >> 4) * (T * 16) + kk * 16 + (rr & 15);
             uint32_t word = 0;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -123,30 +150,35 @@ __global__ void __launch_bounds__(kCtaThreads) k_inter_i16x2(const __grid_consta
                 }
                 word |= (uint32_t(uint8_t(int8_t(v)))) << (8 * c);
             }
-            reinterpret_cast<uint32_t *>(prof)[w] = word;
+            reinterpret_cast<uint32_t *>(prof)[phys / 4] = word;
         }
         __syncthreads();
         if (Lw == 0) continue;
 
         uint32_t E[R], Ho[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) { E[r] = NEG_O2; Ho[r] = NEG_O2; }
-        uint32_t hd = NEG_O2;              // Ho(top-1, j-1)
-        uint32_t pub_h = NEG_O2, pub_f = NEG_O2, pub_c = 0;
+        for (int r = 0; r < R; ++r) { E[r] = BNEG_O2; Ho[r] = BNEG_O2; }
+        uint32_t hd = BNEG_O2;             // B(Ho(top-1, j-1))
+        // pub_h: B(Ho) of this lane's bottom row; pub_f: B(F) of the next lane's top row
+        uint32_t pub_h = BNEG_O2, pub_f = BNEG_O2, pub_c = 0;
         const bool last_pass = (pass + 1 == npass);
         const int steps = Lw + T - 1;
         // Lane 0 reads codes and (after the first pass) the previous strip's
         // bottom row in groups of 4 columns, one group ahead of use, so the
         // global-load latency stays off the per-column critical path.
         uint2 quad = make_uint2(0, 0), quad_next = make_uint2(0, 0);
-        uint4 bc0 = make_uint4(0, 0, 0, 0), bc1 = bc0, bn0 = bc0, bn1 = bc0;
-        // Lane T-1 collects 4 columns of its bottom row before one 32-byte store.
-        uint2 sb0 = make_uint2(0, 0), sb1 = sb0, sb2 = sb0, sb3 = sb0;
+        uint2 *stg = bstage[sub];
         if (k == 0 && Lp > 0) {
             quad_next = __ldg(cptr);
             if (pass > 0) {
-                bn0 = bnd[0];
-                bn1 = bnd[1];
+                cp_async16(stg + 0, bnd);
+                cp_async16(stg + 2, bnd + 1);
+                cp_async_commit();
+                if (4 < Lp) {
+                    cp_async16(stg + 4, bnd + kBundlePairs * 2);
+                    cp_async16(stg + 6, bnd + kBundlePairs * 2 + 1);
+                }
+                cp_async_commit();
             }
         }
 
@@ -159,73 +191,64 @@ __global__ void __launch_bounds__(kCtaThreads) k_inter_i16x2(const __grid_consta
             if (k == 0 && act) {
                 if ((s & 3) == 0) {
                     quad = quad_next;
-                    bc0 = bn0;
-                    bc1 = bn1;
-                    if (s + 4 < Lp) {
-                        quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
-                        if (pass > 0) {
-                            const uint4 *g = bnd + size_t((s >> 2) + 1) * (kBundlePairs * 2);
-                            bn0 = g[0];
-                            bn1 = g[1];
-                        }
-                    }
+                    if (s + 4 < Lp) quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
+                    if (pass > 0) cp_async_wait1();      // group s/4 has landed
                 }
                 const uint32_t w = (s & 2) ? quad.y : quad.x;
                 cin = (s & 1) ? (w >> 16) : (w & 0xffffu);
-                if (pass == 0) {
-                    hin = NEG_O2;
-                    fin = NEG_O2;
+                if (pass == 0) {          // H(0,j) = 0, F(1,j) = -o
+                    hin = BNEG_O2;
+                    fin = BNEG_O2;
                 } else {
-                    const uint4 bq = (s & 2) ? bc1 : bc0;
-                    hin = (s & 1) ? bq.z : bq.x;
-                    fin = (s & 1) ? bq.w : bq.y;
+                    const uint2 bv = stg[((s >> 2) & 1) * 4 + (s & 3)];
+                    hin = bv.x;
+                    fin = bv.y;
+                    if ((s & 3) == 3) {   // buffer of group s/4 is free: fetch group s/4 + 2 into it
+                        if (s + 5 < Lp) {
+                            const uint4 *g = bnd + size_t((s >> 2) + 2) * (kBundlePairs * 2);
+                            cp_async16(stg + ((s >> 2) & 1) * 4, g);
+                            cp_async16(stg + ((s >> 2) & 1) * 4 + 2, g + 1);
+                        }
+                        cp_async_commit();
+                    }
                 }
             }
             if (act) {
                 const int ta = int(cin & 0xffu), tb = int((cin >> 8) & 0xffu);
-                const uint4 *pa = reinterpret_cast<const uint4 *>(prof + ta * TR + k * R);
-                const uint4 *pb = reinterpret_cast<const uint4 *>(prof + tb * TR + k * R);
+                const uint4 *pa = reinterpret_cast<const uint4 *>(prof + ta * TR + k * 16);
+                const uint4 *pb = reinterpret_cast<const uint4 *>(prof + tb * TR + k * 16);
                 uint32_t wa[R / 4], wb[R / 4];
 #pragma unroll
                 for (int v = 0; v < R / 16; ++v) {
-                    const uint4 x = pa[v];
-                    const uint4 y = pb[v];
+                    const uint4 x = pa[v * T];
+                    const uint4 y = pb[v * T];
                     wa[4 * v + 0] = x.x; wa[4 * v + 1] = x.y; wa[4 * v + 2] = x.z; wa[4 * v + 3] = x.w;
                     wb[4 * v + 0] = y.x; wb[4 * v + 1] = y.y; wb[4 * v + 2] = y.z; wb[4 * v + 3] = y.w;
                 }
-                uint32_t f = __viaddmax_s16x2(fin, NEG_E2, hin);   // F of the top row
+                uint32_t f = fin;                 // B(F) of this lane's top row
                 uint32_t d = hd;
-                uint32_t xo_prev = 0;
+                uint32_t yprev = 0;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const uint32_t p = prmt(wa[r / 4], wb[r / 4], pair_sel(r % 4));
-                    const uint32_t e_r = __viaddmax_s16x2(E[r], NEG_E2, Ho[r]);
-                    const uint32_t x = __viaddmax_s16x2_relu(d, p, e_r);
-                    if (r > 0) f = __viaddmax_s16x2(f, NEG_MIN2, xo_prev);
-                    const uint32_t xo = __viaddmax_s16x2(x, NEG_O2, MIN2);
-                    const uint32_t ho = __viaddmax_s16x2(f, NEG_O2, xo);
+                    const uint32_t e_r = __viaddmax_u16x2(E[r], ADD_NEG_E, Ho[r]);
+                    const uint32_t x = __viaddmax_u16x2(d, p, e_r);
+                    const uint32_t y = __vimax3_u16x2(f, x, BZERO2);   // B(H)
+                    const uint32_t ho = y - OO;                         // B(H - o), no borrow: y >= 0x8000
+                    f = __viaddmax_u16x2(f, ADD_NEG_E, ho);           // B(F) of the row below
                     d = Ho[r];
                     E[r] = e_r;
                     Ho[r] = ho;
-                    xo_prev = xo;
+                    if (r & 1) mx = __vimax3_u16x2(mx, yprev, y);
+                    yprev = y;
                 }
-#pragma unroll
-                for (int r = 0; r < R; r += 2) mx = __vimax3_s16x2(mx, Ho[r], Ho[r + 1]);
                 hd = hin;
                 pub_h = Ho[R - 1];
                 pub_f = f;
                 pub_c = cin;
-                if (k == T - 1 && !last_pass) {
-                    sb0 = sb1;
-                    sb1 = sb2;
-                    sb2 = sb3;
-                    sb3 = make_uint2(Ho[R - 1], f);
-                    if ((j & 3) == 3) {   // Lp is a multiple of 4, so every group completes
-                        uint4 *g = bnd + size_t(j >> 2) * (kBundlePairs * 2);
-                        g[0] = make_uint4(sb0.x, sb0.y, sb1.x, sb1.y);
-                        g[1] = make_uint4(sb2.x, sb2.y, sb3.x, sb3.y);
-                    }
-                }
+                if (k == T - 1 && !last_pass)   // 4 consecutive columns fill one 32-byte sector
+                    reinterpret_cast<uint2 *>(bnd)[size_t(j >> 2) * (kBundlePairs * 4) + (j & 3)] =
+                        make_uint2(Ho[R - 1], f);
             }
         }
     }
@@ -233,11 +256,11 @@ __global__ void __launch_bounds__(kCtaThreads) k_inter_i16x2(const __grid_consta
 #pragma unroll
     for (int dd = T / 2; dd >= 1; dd >>= 1) {
         const uint32_t other = __shfl_xor_sync(0xffffffffu, mx, dd, T);
-        mx = __vimax3_s16x2(mx, other, other);
+        mx = __vimax3_u16x2(mx, other, other);
     }
     if (valid && k == 0) {
-        const int hA = int(int16_t(mx & 0xffffu)) + o;
-        const int hB = int(int16_t(mx >> 16)) + o;
+        const int hA = int(mx & 0xffffu) - 32768;
+        const int hB = int(mx >> 16) - 32768;
         const int64_t tA = 2 * pair;
         int mask = 0;
         const int64_t oA = a.db.perm[tA];

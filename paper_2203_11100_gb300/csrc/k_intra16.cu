@@ -21,8 +21,9 @@
 // * Every wait is bounded: if a flag does not arrive within the spin limit
 //   the kernel records SW_ERR_TIMEOUT in a status word, tells the other
 //   warps to stop waiting, and finishes without hanging.
-// Per cell pair the arithmetic is the same five DPX operations and one byte
-// permute as the inter-task kernel (see k_inter16.cu for the derivation).
+// Per cell pair the arithmetic is the same biased-domain sequence as the
+// inter-task kernel (four DPX operations, one 32-bit subtraction, one byte
+// permute and half a running max; see k_inter16.cu for the derivation).
 #include "swdb_internal.cuh"
 
 namespace swdb {
@@ -117,17 +118,18 @@ __global__ void __launch_bounds__(NW * 32) k_intra_i16x2(const __grid_constant__
                              : nullptr;
 
     const int o = a.gap_open;
-    const uint32_t NEG_O2 = pack2(-o);
-    const uint32_t NEG_E2 = pack2(-a.gap_extend);
-    const uint32_t NEG_MIN2 = pack2(-(a.gap_extend < o ? a.gap_extend : o));
-    const uint32_t MIN2 = 0x80008000u;
+    // Biased constants: B(v) = v + 32768 per half (see k_inter16.cu).
+    const uint32_t BNEG_O2 = pack2(32768 - o);
+    const uint32_t ADD_NEG_E = pack2(-a.gap_extend);
+    const uint32_t OO = uint32_t(o) | (uint32_t(o) << 16);
+    const uint32_t BZERO2 = 0x80008000u;
 
     int8_t *prof = prof_all + w * kProfRows * TR;
     uint2 *ring_in = ring_all + w * D * C;
     uint2 *ring_out = ring_all + ((w + 1) % NW) * D * C;
 
     const int nsp = (m + SPR - 1) / SPR;
-    uint32_t mx = NEG_O2;
+    uint32_t mx = BZERO2;      // running max of B(H)
     int g_in = 0, g_out = 0;   // chunk sequence numbers on the incoming / outgoing link
 
     for (int sp = 0; sp < nsp; ++sp) {
@@ -161,9 +163,10 @@ __global__ void __launch_bounds__(NW * 32) k_intra_i16x2(const __grid_constant__
 
         uint32_t E[R], Ho[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) { E[r] = NEG_O2; Ho[r] = NEG_O2; }
-        uint32_t hd = NEG_O2;
-        uint32_t pub_h = NEG_O2, pub_f = NEG_O2, pub_c = 0;
+        for (int r = 0; r < R; ++r) { E[r] = BNEG_O2; Ho[r] = BNEG_O2; }
+        uint32_t hd = BNEG_O2;
+        // pub_h: B(Ho) of this lane's bottom row; pub_f: B(F) of the next lane's top row
+        uint32_t pub_h = BNEG_O2, pub_f = BNEG_O2, pub_c = 0;
         uint2 quad = make_uint2(0, 0), quad_next = make_uint2(0, 0);
         uint4 bc0 = make_uint4(0, 0, 0, 0), bc1 = bc0, bn0 = bc0, bn1 = bc0;
         uint2 sb0 = make_uint2(0, 0), sb1 = sb0, sb2 = sb0, sb3 = sb0;
@@ -212,9 +215,9 @@ __global__ void __launch_bounds__(NW * 32) k_intra_i16x2(const __grid_constant__
                     const uint4 bq = (s & 2) ? bc1 : bc0;
                     hin = (s & 1) ? bq.z : bq.x;
                     fin = (s & 1) ? bq.w : bq.y;
-                } else {
-                    hin = NEG_O2;
-                    fin = NEG_O2;
+                } else {                  // H(0,j) = 0, F(1,j) = -o
+                    hin = BNEG_O2;
+                    fin = BNEG_O2;
                 }
             }
             if (act) {
@@ -229,24 +232,23 @@ __global__ void __launch_bounds__(NW * 32) k_intra_i16x2(const __grid_constant__
                     wa[4 * v + 0] = x.x; wa[4 * v + 1] = x.y; wa[4 * v + 2] = x.z; wa[4 * v + 3] = x.w;
                     wb[4 * v + 0] = y.x; wb[4 * v + 1] = y.y; wb[4 * v + 2] = y.z; wb[4 * v + 3] = y.w;
                 }
-                uint32_t f = __viaddmax_s16x2(fin, NEG_E2, hin);
+                uint32_t f = fin;
                 uint32_t d = hd;
-                uint32_t xo_prev = 0;
+                uint32_t yprev = 0;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const uint32_t p = prmt(wa[r / 4], wb[r / 4], pair_sel(r % 4));
-                    const uint32_t e_r = __viaddmax_s16x2(E[r], NEG_E2, Ho[r]);
-                    const uint32_t x = __viaddmax_s16x2_relu(d, p, e_r);
-                    if (r > 0) f = __viaddmax_s16x2(f, NEG_MIN2, xo_prev);
-                    const uint32_t xo = __viaddmax_s16x2(x, NEG_O2, MIN2);
-                    const uint32_t ho = __viaddmax_s16x2(f, NEG_O2, xo);
+                    const uint32_t e_r = __viaddmax_u16x2(E[r], ADD_NEG_E, Ho[r]);
+                    const uint32_t x = __viaddmax_u16x2(d, p, e_r);
+                    const uint32_t y = __vimax3_u16x2(f, x, BZERO2);
+                    const uint32_t ho = y - OO;
+                    f = __viaddmax_u16x2(f, ADD_NEG_E, ho);
                     d = Ho[r];
                     E[r] = e_r;
                     Ho[r] = ho;
-                    xo_prev = xo;
+                    if (r & 1) mx = __vimax3_u16x2(mx, yprev, y);
+                    yprev = y;
                 }
-#pragma unroll
-                for (int r = 0; r < R; r += 2) mx = __vimax3_s16x2(mx, Ho[r], Ho[r + 1]);
                 hd = hin;
                 pub_h = Ho[R - 1];
                 pub_f = f;
@@ -284,15 +286,15 @@ __global__ void __launch_bounds__(NW * 32) k_intra_i16x2(const __grid_constant__
 #pragma unroll
     for (int dd = 16; dd >= 1; dd >>= 1) {
         const uint32_t other = __shfl_xor_sync(0xffffffffu, mx, dd);
-        mx = __vimax3_s16x2(mx, other, other);
+        mx = __vimax3_u16x2(mx, other, other);
     }
     if (k == 0) red[w] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int i = 1; i < NW; ++i) mx = __vimax3_s16x2(mx, red[i], red[i]);
-        const int hA = int(int16_t(mx & 0xffffu)) + o;
-        const int hB = int(int16_t(mx >> 16)) + o;
+        for (int i = 1; i < NW; ++i) mx = __vimax3_u16x2(mx, red[i], red[i]);
+        const int hA = int(mx & 0xffffu) - 32768;
+        const int hB = int(mx >> 16) - 32768;
         const int64_t tA = 2 * pair;
         int mask = 0;
         const int64_t oA = a.db.perm[tA];

@@ -78,6 +78,32 @@ struct IntraArgs {
     int32_t *status;
 };
 
+// Arguments of the batched persistent kernel: query pairs (qp_a[i], qp_b[i];
+// qp_b = -1 for a lone query) against the sorted sequences
+// [seq_begin, seq_end), tiles = chunks of 256/T sequences x query pairs.
+struct BatchArgs {
+    DbView db;
+    int64_t seq_begin, seq_end;
+    int32_t n_chunks;
+    int32_t n_qp;
+    const int32_t *qp_a;
+    const int32_t *qp_b;
+    const int64_t *q_off;       // device, n_q+1
+    const uint8_t *queries;     // device
+    int32_t gap_open, gap_extend;
+    int32_t sat_limit;
+    int8_t prof8[kProfRows][kProfRows];
+    uint2 *scratch;             // per CTA slot, per subwarp boundary rows (null: single pass)
+    int64_t scratch_stride;     // uint2 entries per CTA slot
+    int32_t max_cols;           // uint2 entries per subwarp (>= any chunk's columns)
+    int32_t *scores;            // [n_q][n_seqs]
+    int32_t *ovf_list;          // [n_q][list_stride]
+    int64_t list_stride;
+    int32_t *ovf_count;         // [n_q]
+    int32_t *ovf_seqs;          // [n_q]
+    int32_t *tile_counter;      // zeroed before launch
+};
+
 // Arguments of the int32 kernel.  Work items are pairs with a mask of the
 // halves to score; either an explicit list (ovf_list/ovf_count) or, when
 // list is null, every pair in [pair_begin, pair_end) with mask 3.
@@ -101,6 +127,9 @@ bool inter_config_supported(int lanes, int rows);
 cudaError_t launch_intra_i16x2(const IntraArgs &a, int warps, int rows, cudaStream_t s);
 int intra_rows_per_superpass(int warps, int rows);
 bool intra_config_supported(int warps, int rows);
+cudaError_t launch_batch_i16x2(const BatchArgs &a, int lanes, int rows, int grid, cudaStream_t s);
+bool batch_config_supported(int lanes, int rows);
+int batch_slots(int lanes, int rows, int sms);   // resident CTAs of the persistent grid
 cudaError_t launch_profile32(const uint8_t *query, int32_t m, int32_t m_pad, const int32_t *matrix_host,
                              int32_t A, int32_t gap_open, int32_t *prof32, cudaStream_t s);
 cudaError_t launch_i32(const I32Args &a, int lanes, int rows, int grid, cudaStream_t s);

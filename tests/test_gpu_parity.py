@@ -250,3 +250,46 @@ def test_invalid_arguments_reported(gpu):
         with pytest.raises(gpu.SwError) as e:
             d.search(np.array([3], np.uint8), np.array([0, 1]), S, 10, 1, lanes=5)
         assert e.value.code == 6
+
+
+# --- batched persistent form (query pairs in the int16x2 halves) ------------
+
+BATCH_SHAPES = [(8, 16), (8, 32), (16, 16), (16, 32)]
+
+
+@pytest.mark.parametrize("lanes,rows", BATCH_SHAPES)
+def test_batched_matches_oracle(gpu, lanes, rows):
+    rng = np.random.default_rng(40 + lanes + rows)
+    db = _db(rng, 333, 1, 500)
+    qs = synth.seqset_from_lengths(rng, [0, 1, 17, 130, 131, 256, 257, 700, 64])   # odd count, one empty
+    st = _check(gpu, qs, db, synth.blosum62(), 10, 1, mode=gpu.SW_MODE_BATCHED, lanes=lanes,
+                rows_per_lane=rows)
+    assert st["mode_used"] == gpu.SW_MODE_BATCHED
+    assert st["inter_launches"] == 1
+
+
+def test_batched_long_split_and_saturation(gpu):
+    rng = np.random.default_rng(41)
+    W = synth.ALPHABET.index("W")
+    seqs = [synth.random_residues(rng, int(n)) for n in rng.integers(1, 900, 120)]
+    seqs[3] = np.full(3100, W, dtype=np.uint8)                      # long and saturating
+    seqs[50] = np.concatenate([synth.random_residues(rng, 300), np.full(3000, W, np.uint8)])
+    seqs[51] = np.full(2990, W, dtype=np.uint8)                     # saturates, not long at cutoff 3072
+    db = synth.seqset_from_list(seqs)
+    qs = synth.seqset_from_list([np.full(3050, W, np.uint8), synth.random_residues(rng, 2200),
+                                 synth.random_residues(rng, 40)])
+    for cutoff in (0, 200):
+        st = _check(gpu, qs, db, synth.blosum62(), 10, 1, mode=gpu.SW_MODE_BATCHED, long_cutoff=cutoff)
+        assert st["rescored"] >= 3
+
+
+def test_batched_equals_plain(gpu):
+    rng = np.random.default_rng(42)
+    db = _db(rng, 2000, 2, 1200)
+    qs = synth.seqset_from_lengths(rng, rng.integers(1, 1500, 11))
+    S = synth.blosum62()
+    with gpu.Database(db.residues, db.offsets, 24) as d:
+        sp, hp, _ = d.search(qs.residues, qs.offsets, S, 11, 1, top_k=25, mode=gpu.SW_MODE_PLAIN)
+        sb, hb, _ = d.search(qs.residues, qs.offsets, S, 11, 1, top_k=25, mode=gpu.SW_MODE_BATCHED)
+    np.testing.assert_array_equal(sp, sb)
+    np.testing.assert_array_equal(hp, hb)
