@@ -179,10 +179,11 @@ class ClockSampler:
 def traffic_per_launch(cells_per_launch: float):
     """DRAM bytes per inter-task launch from the committed ncu summary, if it
     was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_inter_i16x2_traffic.json")
+    path = os.path.join(ROOT, "profiles", "k_inter_i16x2_swissprot_like_0.7db.md")
     src = os.path.join(ROOT, "paper_2203_11100_gb300", "csrc", "k_inter16.cu")
     try:
-        rec = json.load(open(path))
+        line = next(l for l in open(path) if l.startswith("traffic:"))
+        rec = dict(kv.split("=", 1) for kv in line.split()[1:])
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
         if rec.get("source_sha256") != sha:
             return None

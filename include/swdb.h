@@ -87,7 +87,15 @@ typedef struct {
     int32_t rows_per_lane;    /* query rows held per lane (16 or 32); 0 = chosen per query */
     void *workspace;          /* caller-owned device scratch, or NULL for the handle's own */
     size_t workspace_bytes;   /* size of workspace */
+    int32_t flags;            /* SW_FLAG_* bits */
 } sw_search_opts;
+
+/* Capture the device work of the search into a CUDA graph on first use and
+ * replay it while the call's signature (buffers, query lengths, matrix,
+ * penalties, options, stream) stays the same.  Query contents may change
+ * between replays.  One graph is cached per handle.  Per-kernel times in
+ * sw_search_stats are not measured for captured work. */
+#define SW_FLAG_GRAPH 1
 
 /* Counters of one search, filled when the caller passes a non-NULL pointer
  * (which makes sw_search wait for the device before returning). */
@@ -107,6 +115,8 @@ typedef struct {
     int32_t inter_launches; /* launches of the inter-task kernel */
     int64_t inter_cells;    /* cells scored by the inter-task kernel launches */
     int64_t long_cells;     /* cells of the long sequences (intra_ms launches) */
+    int32_t graph_replayed; /* 1 if a cached CUDA graph ran the work */
+    int32_t reserved0;
 } sw_search_stats;
 
 /*

@@ -7,6 +7,7 @@ CPU fallback: if the library is missing, every call raises.
 """
 from .binding import (  # noqa: F401
     HIT_DTYPE,
+    SW_FLAG_GRAPH,
     SW_MODE_AUTO,
     SW_MODE_BATCHED,
     SW_MODE_PLAIN,

@@ -18,6 +18,7 @@ from . import build as _build
 SW_OK = 0
 SW_PREC_AUTO, SW_PREC_I16, SW_PREC_I32 = 0, 1, 2
 SW_MODE_AUTO, SW_MODE_PLAIN, SW_MODE_BATCHED = 0, 1, 2
+SW_FLAG_GRAPH = 1
 
 HIT_DTYPE = np.dtype([("score", "<i4"), ("reserved", "<i4"), ("db_index", "<i8")])
 
@@ -34,7 +35,7 @@ class SwError(RuntimeError):
 class SwSearchOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("mode", ctypes.c_int32), ("long_cutoff", ctypes.c_int64),
                 ("lanes", ctypes.c_int32), ("rows_per_lane", ctypes.c_int32),
-                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t), ("flags", ctypes.c_int32)]
 
 
 class SwSearchStats(ctypes.Structure):
@@ -43,7 +44,8 @@ class SwSearchStats(ctypes.Structure):
                 ("lanes_used", ctypes.c_int32), ("rows_per_lane_used", ctypes.c_int32),
                 ("launches", ctypes.c_int32), ("inter_ms", ctypes.c_float), ("rescore_ms", ctypes.c_float),
                 ("intra_ms", ctypes.c_float), ("other_ms", ctypes.c_float), ("inter_launches", ctypes.c_int32),
-                ("inter_cells", ctypes.c_int64), ("long_cells", ctypes.c_int64)]
+                ("inter_cells", ctypes.c_int64), ("long_cells", ctypes.c_int64),
+                ("graph_replayed", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
 class SwDbInfo(ctypes.Structure):
@@ -151,8 +153,9 @@ def sw_db_get_info(handle) -> dict:
     return {f: getattr(info, f) for f, _ in SwDbInfo._fields_}
 
 
-def _opts(precision, mode, long_cutoff, lanes, rows_per_lane, workspace):
+def _opts(precision, mode, long_cutoff, lanes, rows_per_lane, workspace, flags=0):
     o = SwSearchOpts()
+    o.flags = flags
     o.precision = precision
     o.mode = mode
     o.long_cutoff = long_cutoff
@@ -179,7 +182,7 @@ def sw_search_workspace_size(handle, q_offsets, top_k: int, precision=SW_PREC_AU
 
 def sw_search(handle, queries, q_offsets, matrix, gap_open: int, gap_extend: int, top_k: int,
               scores_out=None, hits_out=None, precision=SW_PREC_AUTO, mode=SW_MODE_AUTO, long_cutoff=0,
-              lanes=0, rows_per_lane=0, workspace=None, stats: bool = False, stream=None):
+              lanes=0, rows_per_lane=0, workspace=None, stats: bool = False, stream=None, graph: bool = False):
     """Run sw_search.  Outputs are written into scores_out / hits_out (numpy =
     host, torch CUDA tensor = device).  Returns a stats dict when stats=True."""
     lib = load_library()
@@ -190,7 +193,7 @@ def sw_search(handle, queries, q_offsets, matrix, gap_open: int, gap_extend: int
     if hits_out is not None and isinstance(hits_out, np.ndarray) and hits_out.dtype != HIT_DTYPE:
         raise TypeError("hits_out must have dtype HIT_DTYPE")
     hp, h_cuda = _addr(hits_out, None, "hits_out")
-    o = _opts(precision, mode, long_cutoff, lanes, rows_per_lane, workspace)
+    o = _opts(precision, mode, long_cutoff, lanes, rows_per_lane, workspace, SW_FLAG_GRAPH if graph else 0)
     st = SwSearchStats() if stats else None
     if stream is None and (q_cuda or s_cuda or h_cuda or workspace is not None):
         import torch

@@ -69,6 +69,8 @@ struct sw_db {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    cudaGraphExec_t graph_exec = nullptr;   // last captured search (SW_FLAG_GRAPH)
+    std::string graph_key;
     std::mutex mu;
 
     DbView view() const {
@@ -122,6 +124,8 @@ void free_db_device(sw_db *db) {
     db->d_perm = nullptr;
     db->ws = nullptr;
     db->ws_bytes = 0;
+    if (db->graph_exec) cudaGraphExecDestroy(db->graph_exec);
+    db->graph_exec = nullptr;
     if (db->stream) cudaStreamDestroy(db->stream);
     if (db->side) cudaStreamDestroy(db->side);
     if (db->ev_fork) cudaEventDestroy(db->ev_fork);
@@ -288,6 +292,10 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
     p.n_long = std::min<int64_t>(nlb * kBundleSeqs, db->n_seqs);
     p.long_codes_bytes = nlb < db->n_bundles ? db->h_bundle_off[size_t(nlb)] : db->codes_bytes;
     p.need_long_boundary = nlb > 0 && p.max_m > intra_rows_per_superpass(p.warps_long, p.rows_long);
+    if (nlb > 0 && p.precision == SW_PREC_I16) {
+        const cudaError_t e = prepare_intra_i16x2(p.warps_long, p.rows_long);
+        if (e != cudaSuccess) return fail(SW_ERR_CUDA, std::string("intra-task kernel set-up: ") + cudaGetErrorString(e));
+    }
     p.need_boundary = p.max_m > std::min(p.min_tr, p.lanes32 * p.rows32);
 
     if (p.mode == SW_MODE_BATCHED) {
@@ -654,7 +662,6 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
         SW_CUDA_TRY(cudaMemcpyAsync(buf.queries, queries, size_t(plan.total_m), cudaMemcpyHostToDevice, st));
     int32_t *d_status = buf.counters + 3 * size_t(std::max<int32_t>(n_q, 1));
     int32_t *d_tiles = d_status + 1;
-    SW_CUDA_TRY(cudaMemsetAsync(buf.counters, 0, sizeof(int32_t) * (3 * size_t(std::max<int32_t>(n_q, 1)) + 2), st));
 
     // int8 profile table for the int16x2 kernel: [query code][db code] = S + o.
     InterArgs ia;
@@ -684,12 +691,26 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
     const int64_t n_pairs = db->n_sorted / 2;
 
     const int64_t list_stride = std::max<int64_t>(n_pairs, 1);
+    const bool split = plan.precision == SW_PREC_I16 && plan.long_end_pair > 0 && n_q > 0 && db->n_seqs > 0;
+    const int32_t n_qp = int32_t(plan.qp_a.size());
+
+    // Host-to-device inputs first: they stay outside any captured graph.
+    if ((split || plan.mode == SW_MODE_BATCHED) && n_q > 0)
+        SW_CUDA_TRY(cudaMemcpyAsync(buf.q_off, q_offsets, sizeof(int64_t) * size_t(n_q + 1), cudaMemcpyHostToDevice, st));
+    if (plan.mode == SW_MODE_BATCHED && n_qp > 0) {
+        std::vector<int32_t> qp(plan.qp_a);
+        qp.insert(qp.end(), plan.qp_b.begin(), plan.qp_b.end());
+        SW_CUDA_TRY(cudaMemcpyAsync(buf.qp, qp.data(), sizeof(int32_t) * qp.size(), cudaMemcpyHostToDevice, st));
+    }
+    int last_lanes = plan.lanes, last_rows = plan.rows;
+
+    // All device work of the search, in stream order.  Run directly, or
+    // captured once into a CUDA graph and replayed (SW_FLAG_GRAPH).
+    auto enqueue = [&]() -> int {
+    SW_CUDA_TRY(cudaMemsetAsync(buf.counters, 0, sizeof(int32_t) * (3 * size_t(std::max<int32_t>(n_q, 1)) + 2), st));
 
     // (1) Long sequences of every query: one intra-task launch on the side
     //     stream, concurrent with the per-query launches below.
-    const bool split = plan.precision == SW_PREC_I16 && plan.long_end_pair > 0 && n_q > 0 && db->n_seqs > 0;
-    if ((split || plan.mode == SW_MODE_BATCHED) && n_q > 0)
-        SW_CUDA_TRY(cudaMemcpyAsync(buf.q_off, q_offsets, sizeof(int64_t) * size_t(n_q + 1), cudaMemcpyHostToDevice, st));
     if (split) {
         IntraArgs la;
         memset(&la, 0, sizeof la);
@@ -719,18 +740,13 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
 
     // (2b) Batched form: every query pair against the rest of the database in
     //      one persistent launch.
-    int last_lanes = plan.lanes, last_rows = plan.rows;
     if (plan.mode == SW_MODE_BATCHED && db->n_seqs > 0) {
         for (int32_t qi = 0; qi < n_q; ++qi)
             if (q_offsets[qi + 1] == q_offsets[qi])
                 SW_CUDA_TRY(cudaMemsetAsync(d_scores + size_t(qi) * size_t(db->n_seqs), 0,
                                             sizeof(int32_t) * size_t(db->n_seqs), st));
-        const int32_t n_qp = int32_t(plan.qp_a.size());
         const int spc = kCtaThreads / plan.lanes;
         if (n_qp > 0 && plan.batch_seq_begin < db->n_sorted) {
-            std::vector<int32_t> qp(plan.qp_a);
-            qp.insert(qp.end(), plan.qp_b.begin(), plan.qp_b.end());
-            SW_CUDA_TRY(cudaMemcpyAsync(buf.qp, qp.data(), sizeof(int32_t) * qp.size(), cudaMemcpyHostToDevice, st));
             BatchArgs ba;
             memset(&ba, 0, sizeof ba);
             ba.db = db->view();
@@ -819,6 +835,54 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
     }
     if (top_k > 0 && n_q > 0 && (hits_out != nullptr))
         TIMED(LaunchTimer::OTHER, launch_topk(d_scores, n_q, db->n_seqs, top_k, d_hits, st));
+    return SW_OK;
+    };
+
+    bool graph_replayed = false;
+    if (opts && (opts->flags & SW_FLAG_GRAPH)) {
+        // Everything the captured work depends on, byte for byte.
+        std::string key;
+        auto put = [&key](const void *p, size_t n) { key.append(static_cast<const char *>(p), n); };
+        const void *ptrs[] = {d_queries, d_scores, d_hits, ws, st};
+        put(ptrs, sizeof ptrs);
+        const int32_t ints[] = {n_q, gap_open, gap_extend, top_k, plan.mode, plan.precision, plan.lanes, plan.rows,
+                                hits_out != nullptr};
+        put(ints, sizeof ints);
+        put(&plan.long_end_pair, sizeof plan.long_end_pair);
+        if (n_q > 0) put(q_offsets, sizeof(int64_t) * size_t(n_q + 1));
+        put(matrix, sizeof(int32_t) * size_t(db->A) * size_t(db->A));
+        if (!(db->graph_exec && db->graph_key == key)) {
+            if (db->graph_exec) cudaGraphExecDestroy(db->graph_exec);
+            db->graph_exec = nullptr;
+            db->graph_key.clear();
+            timer.on = false;   // per-launch events cannot outlive this call inside a graph
+            SW_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            const int erc = enqueue();
+            cudaGraph_t graph = nullptr;
+            const cudaError_t cap = cudaStreamEndCapture(st, &graph);
+            if (erc) {
+                if (graph) cudaGraphDestroy(graph);
+                return erc;
+            }
+            if (cap != cudaSuccess) return fail(SW_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(cap));
+            const cudaError_t ie = cudaGraphInstantiate(&db->graph_exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) {
+                db->graph_exec = nullptr;
+                return fail(SW_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+            }
+            db->graph_key = key;
+        } else {
+            graph_replayed = true;
+            // the plan's per-query launch shapes are the same as when captured
+            if (plan.precision == SW_PREC_I16 && plan.mode == SW_MODE_PLAIN && plan.auto_shape && n_q > 0)
+                choose_shape(q_offsets[n_q] - q_offsets[n_q - 1], &last_lanes, &last_rows);
+        }
+        SW_CUDA_TRY(cudaGraphLaunch(db->graph_exec, st));
+    } else {
+        rc = enqueue();
+        if (rc) return rc;
+    }
 
     bool sync = false;
     if (scores_out && !s_dev && n_q > 0 && db->n_seqs > 0) {
@@ -850,6 +914,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
         stats->lanes_used = plan.precision == SW_PREC_I16 ? last_lanes : plan.lanes32;
         stats->rows_per_lane_used = plan.precision == SW_PREC_I16 ? last_rows : plan.rows32;
         stats->launches = timer.launches;
+        stats->graph_replayed = graph_replayed ? 1 : 0;
         stats->inter_ms = timer.total(LaunchTimer::INTER);
         stats->rescore_ms = timer.total(LaunchTimer::RESCORE);
         stats->intra_ms = timer.total(LaunchTimer::INTRA);

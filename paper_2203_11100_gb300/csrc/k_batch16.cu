@@ -259,9 +259,7 @@ size_t batch_smem() {
 
 template <int T, int R>
 cudaError_t launch_tr(const BatchArgs &a, int grid, cudaStream_t s) {
-    const size_t smem = batch_smem<T, R>();
-    cudaError_t e = cudaFuncSetAttribute(k_batch_i16x2<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
+    const size_t smem = batch_smem<T, R>();   // attribute set by batch_slots at planning
     k_batch_i16x2<T, R><<<grid, kCtaThreads, smem, s>>>(a);
     return cudaGetLastError();
 }

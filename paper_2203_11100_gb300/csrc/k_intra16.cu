@@ -327,11 +327,15 @@ cudaError_t launch_rn(const IntraArgs &a, cudaStream_t s) {
     if (pairs <= 0 || a.n_q <= 0) return cudaSuccess;
     const int64_t grid = pairs * a.n_q;
     if (grid >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
-    const size_t smem = intra_smem<R, NW>();
-    cudaError_t e = cudaFuncSetAttribute(k_intra_i16x2<R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
+    const size_t smem = intra_smem<R, NW>();   // attribute set by prepare_intra_i16x2 at planning
     k_intra_i16x2<R, NW><<<unsigned(grid), NW * 32, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int R, int NW>
+cudaError_t prepare_rn() {
+    return cudaFuncSetAttribute(k_intra_i16x2<R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(intra_smem<R, NW>()));
 }
 
 }  // namespace
@@ -341,6 +345,12 @@ bool intra_config_supported(int warps, int rows) {
 }
 
 int intra_rows_per_superpass(int warps, int rows) { return warps * 32 * rows; }
+
+cudaError_t prepare_intra_i16x2(int warps, int rows) {
+    if (rows == 16 && warps == 4) return prepare_rn<16, 4>();
+    if (rows == 16 && warps == 8) return prepare_rn<16, 8>();
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_intra_i16x2(const IntraArgs &a, int warps, int rows, cudaStream_t s) {
     if (rows == 16 && warps == 4) return launch_rn<16, 4>(a, s);

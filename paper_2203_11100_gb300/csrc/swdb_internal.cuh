@@ -126,10 +126,11 @@ cudaError_t launch_inter_i16x2(const InterArgs &a, int lanes, int rows, cudaStre
 bool inter_config_supported(int lanes, int rows);
 cudaError_t launch_intra_i16x2(const IntraArgs &a, int warps, int rows, cudaStream_t s);
 int intra_rows_per_superpass(int warps, int rows);
+cudaError_t prepare_intra_i16x2(int warps, int rows);   // kernel attributes; call before any capture
 bool intra_config_supported(int warps, int rows);
 cudaError_t launch_batch_i16x2(const BatchArgs &a, int lanes, int rows, int grid, cudaStream_t s);
 bool batch_config_supported(int lanes, int rows);
-int batch_slots(int lanes, int rows, int sms);   // resident CTAs of the persistent grid
+int batch_slots(int lanes, int rows, int sms);   // resident CTAs of the persistent grid (sets attributes)
 cudaError_t launch_profile32(const uint8_t *query, int32_t m, int32_t m_pad, const int32_t *matrix_host,
                              int32_t A, int32_t gap_open, int32_t *prof32, cudaStream_t s);
 cudaError_t launch_i32(const I32Args &a, int lanes, int rows, int grid, cudaStream_t s);

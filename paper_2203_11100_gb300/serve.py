@@ -1,0 +1,244 @@
+"""Continuous-batching search server over a database resident in HBM.
+
+Requests (one query each) arrive at any time through ``submit``.  A
+dispatcher thread admits waiting requests into the next batch as long as the
+device bytes they need fit the budget -- the query codes, one int32 score row
+over the whole database, its top-k hits, the int32 profile and the overflow
+list the rescore may use -- and launches the batch on the next free worker
+stream with ``sw_search`` in the batched form, while earlier batches are still
+running on other streams.  A completion thread waits on each batch's CUDA
+event, copies nothing but the top-k hits back, and resolves the requests'
+futures, recording arrival-to-hits latency.
+
+Each worker stream owns a device workspace (torch allocates it; the library
+allocates nothing per call), so batches on different streams overlap on the
+device.  All scoring runs in libswdb's kernels; this module only schedules.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import queue
+import threading
+import time
+from concurrent.futures import Future
+
+import numpy as np
+
+from . import binding
+
+_POISON = object()
+
+
+@dataclasses.dataclass
+class _Request:
+    codes: np.ndarray
+    future: Future
+    t_arrival: float
+    nbytes: int
+
+
+@dataclasses.dataclass
+class _Batch:
+    requests: list
+    stream: object
+    event: object
+    hits_dev: object
+    hits_host: object
+    worker: int
+    nbytes: int
+    t_launch: float
+    cells: int
+
+
+class SearchServer:
+    """Serve top-k searches of single queries against one loaded database.
+
+    db          a binding.Database (resident database)
+    matrix      substitution matrix (A x A int32), gap_open / gap_extend, top_k
+    max_batch   most queries per launch
+    streams     worker streams (batches in flight at once)
+    mem_budget  device bytes that admitted-but-unfinished requests may hold
+    """
+
+    def __init__(self, db, matrix, gap_open: int, gap_extend: int, top_k: int = 10, max_batch: int = 32,
+                 streams: int = 2, mem_budget: int | None = None, max_query_len: int = 8000,
+                 mode: int = binding.SW_MODE_BATCHED):
+        import torch
+        self.torch = torch
+        self.db = db
+        self.matrix = np.ascontiguousarray(matrix, dtype=np.int32)
+        self.gap_open, self.gap_extend, self.top_k = int(gap_open), int(gap_extend), int(top_k)
+        self.max_batch = int(max_batch)
+        self.max_query_len = int(max_query_len)
+        self.mode = mode
+        self.n_seqs = db.n_seqs
+        info = db.info()
+        self.db_residues = info["residues"]
+        self.device = torch.device("cuda", db.device)
+        self.per_query_fixed = self.n_seqs * 4 + self.top_k * 16 + (self.n_seqs // 2 + 16) * 4
+        free, _ = torch.cuda.mem_get_info(self.device)
+        self.mem_budget = int(mem_budget) if mem_budget else int(free * 0.5)
+        # One workspace per worker, sized for a full batch of the longest admissible queries.
+        q_off = np.arange(self.max_batch + 1, dtype=np.int64) * self.max_query_len
+        ws_bytes = binding.sw_search_workspace_size(db.handle, q_off, self.top_k, mode=mode)
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
+        self.workspaces = [torch.empty(ws_bytes, dtype=torch.uint8, device=self.device) for _ in range(streams)]
+        self.free_workers = queue.Queue()
+        for i in range(streams):
+            self.free_workers.put(i)
+        self.pending = collections.deque()
+        self.cv = threading.Condition()
+        self.in_flight_bytes = 0
+        self.inflight = queue.Queue()
+        self.latencies = []
+        self.completed = 0
+        self.cells = 0
+        self.batches = 0
+        self.batch_sizes = []
+        self.t_first = None
+        self.t_last = None
+        self.closed = False
+        self.error = None
+        self.dispatcher = threading.Thread(target=self._dispatch, daemon=True)
+        self.completer = threading.Thread(target=self._complete, daemon=True)
+        self.dispatcher.start()
+        self.completer.start()
+
+    # -- public -------------------------------------------------------------
+    def submit(self, codes) -> Future:
+        """Queue one query (uint8 codes); the future resolves to its top-k hits
+        (HIT_DTYPE array, best first)."""
+        codes = np.ascontiguousarray(codes, dtype=np.uint8)
+        if len(codes) > self.max_query_len:
+            raise ValueError(f"query longer than max_query_len={self.max_query_len}")
+        fut = Future()
+        m = len(codes)
+        nbytes = m + self.per_query_fixed + 32 * 4 * (m + 256)
+        req = _Request(codes, fut, time.perf_counter(), nbytes)
+        with self.cv:
+            if self.closed:
+                raise RuntimeError("server closed")
+            if self.t_first is None:
+                self.t_first = req.t_arrival
+            self.pending.append(req)
+            self.cv.notify_all()
+        return fut
+
+    def close(self):
+        with self.cv:
+            self.closed = True
+            self.cv.notify_all()
+        self.dispatcher.join()
+        self.inflight.put(_POISON)
+        self.completer.join()
+        if self.error:
+            raise self.error
+
+    def stats(self) -> dict:
+        lat = np.array(self.latencies) if self.latencies else np.zeros(1)
+        span = (self.t_last - self.t_first) if (self.t_first and self.t_last) else 0.0
+        return {"completed": self.completed, "batches": self.batches,
+                "mean_batch": float(np.mean(self.batch_sizes)) if self.batch_sizes else 0.0,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mean_ms": float(lat.mean() * 1e3), "gcups": self.cells / span / 1e9 if span > 0 else 0.0,
+                "span_s": span}
+
+    # -- threads ------------------------------------------------------------
+    def _take_batch(self):
+        """Admit waiting requests (FIFO) while the batch and memory budget allow."""
+        batch, nbytes = [], 0
+        while self.pending and len(batch) < self.max_batch:
+            r = self.pending[0]
+            if self.in_flight_bytes + nbytes + r.nbytes > self.mem_budget and (batch or self.in_flight_bytes):
+                break
+            batch.append(self.pending.popleft())
+            nbytes += r.nbytes
+        return batch, nbytes
+
+    def _dispatch(self):
+        torch = self.torch
+        torch.cuda.set_device(self.device)
+        try:
+            while True:
+                worker = self.free_workers.get()
+                with self.cv:
+                    while not self.pending and not self.closed:
+                        self.cv.wait()
+                    if not self.pending and self.closed:
+                        self.free_workers.put(worker)
+                        return
+                    batch, nbytes = self._take_batch()
+                    while not batch:                       # memory budget: wait for completions
+                        self.cv.wait(timeout=0.05)
+                        batch, nbytes = self._take_batch()
+                    self.in_flight_bytes += nbytes
+                self._launch(worker, batch, nbytes)
+        except Exception as e:  # surface errors to close()
+            self.error = e
+            with self.cv:
+                for r in self.pending:
+                    r.future.set_exception(e)
+                self.pending.clear()
+
+    def _launch(self, worker, batch, nbytes):
+        torch = self.torch
+        stream = self.streams[worker]
+        lens = np.array([len(r.codes) for r in batch], dtype=np.int64)
+        q_off = np.zeros(len(batch) + 1, dtype=np.int64)
+        np.cumsum(lens, out=q_off[1:])
+        q_host = torch.from_numpy(np.concatenate([r.codes for r in batch]) if q_off[-1] else
+                                  np.zeros(1, np.uint8)).pin_memory()
+        with torch.cuda.stream(stream):
+            q_dev = q_host.to(self.device, non_blocking=True)
+            hits_dev = torch.empty((len(batch), max(self.top_k, 1), 2), dtype=torch.int64, device=self.device)
+            binding.sw_search(self.db.handle, q_dev[:int(q_off[-1])], q_off, self.matrix, self.gap_open,
+                              self.gap_extend, self.top_k, None, hits_dev, mode=self.mode,
+                              workspace=self.workspaces[worker], stream=stream.cuda_stream)
+            hits_host = torch.empty(hits_dev.shape, dtype=torch.int64).pin_memory()
+            hits_host.copy_(hits_dev, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        self.inflight.put(_Batch(batch, stream, ev, hits_dev, hits_host, worker, nbytes, time.perf_counter(),
+                                 int(lens.sum()) * self.db_residues))
+
+    def _complete(self):
+        """Resolve batches as their events complete (in any order across streams)."""
+        live = []
+        done = False
+        while not done or live:
+            try:
+                while True:
+                    b = self.inflight.get(block=not live and not done, timeout=None)
+                    if b is _POISON:
+                        done = True
+                    else:
+                        live.append(b)
+                    if self.inflight.empty():
+                        break
+            except queue.Empty:
+                pass
+            finished = [b for b in live if b.event.query()]
+            if not finished:
+                time.sleep(50e-6)
+                continue
+            now = time.perf_counter()
+            for b in finished:
+                live.remove(b)
+                h = b.hits_host.numpy()
+                for i, r in enumerate(b.requests):
+                    out = np.empty(self.top_k, dtype=binding.HIT_DTYPE)
+                    out["score"] = (h[i, :, 0] & 0xffffffff).astype(np.int64).astype(np.int32)
+                    out["reserved"] = 0
+                    out["db_index"] = h[i, :, 1]
+                    self.latencies.append(now - r.t_arrival)
+                    r.future.set_result(out)
+                with self.cv:
+                    self.in_flight_bytes -= b.nbytes
+                    self.completed += len(b.requests)
+                    self.cells += b.cells
+                    self.batches += 1
+                    self.batch_sizes.append(len(b.requests))
+                    self.t_last = now
+                    self.cv.notify_all()
+                self.free_workers.put(b.worker)

@@ -1,0 +1,22 @@
+"""Host-side pieces of the autotuner (no GPU): sampling and cache keys."""
+import numpy as np
+
+from paper_2203_11100_gb300 import autotune
+
+
+def test_sample_spreads_over_lengths():
+    lens = np.array([5, 100, 7, 3000, 40, 900, 60, 1500])
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    res = np.arange(off[-1], dtype=np.int64).astype(np.uint8)
+    s_res, s_off = autotune._sample(res, off, 3)
+    got = sorted(np.diff(s_off).tolist())
+    assert got == [5, 100, 3000] or got[0] == 5 and got[-1] == 3000
+    assert len(s_res) == s_off[-1]
+
+
+def test_batch_key_depends_on_shape():
+    info = {"n_seqs": 10, "residues": 1000, "max_length": 300}
+    k1 = autotune._batch_key(info, np.array([100, 200, 300]))
+    k2 = autotune._batch_key(info, np.array([1000, 2000, 3000]))
+    k3 = autotune._batch_key(info, np.array([100, 200, 300]))
+    assert k1 != k2 and k1 == k3

@@ -293,3 +293,54 @@ def test_batched_equals_plain(gpu):
         sb, hb, _ = d.search(qs.residues, qs.offsets, S, 11, 1, top_k=25, mode=gpu.SW_MODE_BATCHED)
     np.testing.assert_array_equal(sp, sb)
     np.testing.assert_array_equal(hp, hb)
+
+
+@pytest.mark.parametrize("mode", ["plain", "batched"])
+def test_graph_capture_and_replay(gpu, mode):
+    """The captured work replays exactly, and reads new query contents."""
+    import torch
+    m = gpu.SW_MODE_PLAIN if mode == "plain" else gpu.SW_MODE_BATCHED
+    rng = np.random.default_rng(60)
+    lens = np.concatenate([rng.integers(1, 700, 200), [3300, 3500]])   # includes long sequences
+    db = synth.seqset_from_lengths(rng, lens)
+    S = synth.blosum62()
+    qlens = [90, 300, 1200]
+    with gpu.Database(db.residues, db.offsets, 24) as d:
+        q_off = np.concatenate([[0], np.cumsum(qlens)]).astype(np.int64)
+        q_dev = torch.empty(int(q_off[-1]), dtype=torch.uint8, device="cuda")
+        scores = torch.empty((len(qlens), db.n), dtype=torch.int32, device="cuda")
+        hits = torch.empty((len(qlens), 5, 2), dtype=torch.int64, device="cuda")
+        for rep in range(3):
+            qs = synth.seqset_from_lengths(rng, qlens)       # new contents, same lengths
+            q_dev.copy_(torch.from_numpy(qs.residues))
+            st = gpu.sw_search(d.handle, q_dev, q_off, S, 10, 1, 5, scores, hits, mode=m, graph=True, stats=True)
+            assert st["graph_replayed"] == (1 if rep > 0 else 0)
+            torch.cuda.synchronize()
+            want = oracle.all_scores(qs, db, S, 10, 1)
+            np.testing.assert_array_equal(scores.cpu().numpy(), want)
+            h = hits.cpu().numpy()
+            for i in range(len(qlens)):
+                ws, wi = oracle.top_k(want[i], 5)
+                np.testing.assert_array_equal((h[i, :, 0] & 0xffffffff).astype(np.int64), ws)
+                np.testing.assert_array_equal(h[i, :, 1], wi)
+        # a different signature (other penalties) captures again
+        st = gpu.sw_search(d.handle, q_dev, q_off, S, 11, 2, 5, scores, hits, mode=m, graph=True, stats=True)
+        assert st["graph_replayed"] == 0
+
+
+def test_autotune_picks_and_caches(gpu, tmp_path):
+    from paper_2203_11100_gb300 import autotune
+    rng = np.random.default_rng(61)
+    db = synth.seqset_from_lengths(rng, synth.lognormal_lengths(rng, 3000, 360.0, 2, 5000))
+    qs = synth.seqset_from_lengths(rng, rng.integers(50, 1500, 12))
+    S = synth.blosum62()
+    cache = tmp_path / "tune.json"
+    with gpu.Database(db.residues, db.offsets, 24) as d:
+        params = autotune.autotune(d, qs.residues, qs.offsets, S, 10, 1, sample_queries=4, cache_path=str(cache),
+                                   cutoffs=(1024, 3072))
+        assert cache.exists()
+        assert set(params) == {"mode", "lanes", "rows_per_lane", "long_cutoff"}
+        again = autotune.autotune(d, qs.residues, qs.offsets, S, 10, 1, cache_path=str(cache))
+        assert again == params
+        scores, _, _ = d.search(qs.residues, qs.offsets, S, 10, 1, top_k=0, **params)
+    np.testing.assert_array_equal(scores, oracle.all_scores(qs, db, S, 10, 1))
