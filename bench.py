@@ -43,6 +43,7 @@ UNIT = "GCUPS"
 # Minimum packed int16x2 DPX operations per cell update of the recurrences:
 # E, F, H (2), H-o, running max per cell pair = 5.5 per 2 cells.
 DPX_OPS_PER_CELL = 2.75
+RESULT_TIMEOUT_S = 300.0   # a served request that takes longer than this is a failure
 
 
 def parse_args(argv=None):
@@ -60,6 +61,13 @@ def parse_args(argv=None):
                    help="plain: one inter-task launch per query (the paper's form); "
                         "batched: all queries in one persistent launch")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--serve", action="store_true",
+                   help="serving benchmark: Poisson request stream against a resident database "
+                        "(continuous batching), reports p50/p99 latency and sustained GCUPS")
+    p.add_argument("--serve-db-scale", type=float, default=0.1,
+                   help="fraction of the 20M-sequence serving database (0.1 = 2M sequences)")
+    p.add_argument("--serve-requests", type=int, default=96)
+    p.add_argument("--serve-max-batch", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-cells", type=float, default=6e10,
                    help="cells of the oracle's bounded sample (about 10-20 s on 16 cores)")
@@ -337,6 +345,98 @@ def run_ours(args, dist: Dist):
     return out
 
 
+def run_serving(args, dist: Dist):
+    """Continuous-batching server under Poisson arrivals (config of the
+    serving workload at a stated database fraction)."""
+    import torch
+    import paper_2203_11100_gb300 as swdb
+    from paper_2203_11100_gb300.serve import SearchServer
+
+    dev = dist.local_rank
+    torch.cuda.set_device(dev)
+    swdb.load_library()
+    dbs = synth.serving_database(db_scale=args.serve_db_scale)
+    n_req = args.serve_requests
+    reqs = synth.serving_requests(4 * n_req, seed=synth.SEED + 7919 * dist.rank)
+    S = synth.blosum62()
+    db = swdb.Database(dbs.residues, dbs.offsets, len(synth.ALPHABET), device=dev)
+    residues = int(dbs.lengths.sum())
+    clocks = ClockSampler(dev)
+
+    def new_server():
+        return SearchServer(db, S, 10, 1, top_k=10, max_batch=args.serve_max_batch, streams=3, max_query_len=8000)
+
+    # warm-up: one batch through a server
+    srv = new_server()
+    for f in [srv.submit(reqs.seq(i)) for i in range(args.serve_max_batch)]:
+        f.result(timeout=RESULT_TIMEOUT_S)
+    srv.close()
+
+    clocks.start()
+    # saturation: every request queued at once (closed system)
+    srv = new_server()
+    t0 = time.perf_counter()
+    futs = [srv.submit(reqs.seq(i)) for i in range(n_req)]
+    for f in futs:
+        f.result(timeout=RESULT_TIMEOUT_S)
+    sat_s = time.perf_counter() - t0
+    sat = srv.stats()
+    srv.close()
+    sat_rate = n_req / sat_s
+    sat_cells = float(reqs.lengths[:n_req].sum()) * residues
+
+    points = []
+    rng = np.random.default_rng(synth.SEED + 11)
+    base = n_req
+    for frac in (0.5, 0.8, 0.95):
+        rate = frac * sat_rate
+        count = max(16, n_req // 2)
+        gaps = rng.exponential(1.0 / rate, count)
+        srv = new_server()
+        t_start = time.perf_counter()
+        arrivals = t_start + np.cumsum(gaps)
+        futs = []
+        for i in range(count):
+            now = time.perf_counter()
+            if arrivals[i] > now:
+                time.sleep(arrivals[i] - now)
+            futs.append(srv.submit(reqs.seq(base + i)))
+        for f in futs:
+            f.result(timeout=RESULT_TIMEOUT_S)
+        st = srv.stats()
+        srv.close()
+        base += count
+        points.append({"offered_rate_per_s": rate, "load": frac, "requests": count, "p50_ms": st["p50_ms"],
+                       "p99_ms": st["p99_ms"], "mean_batch": st["mean_batch"], "gcups": st["gcups"]})
+    clk = clocks.stop()
+
+    # the plain one-query-per-launch form on the same saturation requests
+    q_off = reqs.offsets[:n_req + 1].copy()
+    q_res = reqs.residues[:int(q_off[-1])]
+    q_dev = torch.from_numpy(q_res).to(f"cuda:{dev}")
+    hits = torch.empty((n_req, 10, 2), dtype=torch.int64, device=f"cuda:{dev}")
+    swdb.sw_search(db.handle, q_dev, q_off, S, 10, 1, 10, None, hits, mode=swdb.SW_MODE_PLAIN)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    swdb.sw_search(db.handle, q_dev, q_off, S, 10, 1, 10, None, hits, mode=swdb.SW_MODE_PLAIN, stats=True)
+    plain_s = time.perf_counter() - t0
+    db.close()
+    value = sat_cells / sat_s / 1e9
+    return {"metric": "GCUPS (served: continuous batching, database resident in HBM)", "value": value,
+            "unit": UNIT, "n_gpus": dist.world, "steps": 1, "warmup": 1, "ms_per_step": sat_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i16x2",
+            "data": "synthetic",
+            "config": {"workload": "serving", "db_seqs": dbs.n, "db_residues": residues,
+                       "db_fraction_of_20M": args.serve_db_scale, "requests_saturation": n_req,
+                       "request_lengths": "lognormal mean 400, 30..8000", "matrix": "BLOSUM62",
+                       "gap_open": 10, "gap_extend": 1, "top_k": 10, "max_batch": args.serve_max_batch,
+                       "streams": 3},
+            "serving": {"saturation_rate_per_s": sat_rate, "saturation_p50_ms": sat["p50_ms"],
+                        "saturation_p99_ms": sat["p99_ms"], "points": points,
+                        "plain_one_launch_per_query_gcups": sat_cells / plain_s / 1e9},
+            "clocks": clk}
+
+
 def run_reference(args, dist: Dist):
     """The oracle timed on the host cores, one bounded sample per step."""
     if dist.rank != 0:
@@ -384,6 +484,9 @@ def main(argv=None):
     if args.impl == "reference":
         dist = Dist(init=False)   # rank 0 alone runs the oracle; other ranks exit without work
         out = run_reference(args, dist)
+    elif args.serve:
+        dist = Dist()
+        out = run_serving(args, dist)
     else:
         dist = Dist()
         out = run_ours(args, dist)

@@ -38,6 +38,8 @@
 //   32767 - max(S) no int16 operation overflowed and the score is exact.
 //   Sequences at or above that limit are appended to a list and rescored
 //   in int32 by another kernel.
+#include <type_traits>
+
 #include "swdb_internal.cuh"
 
 namespace swdb {
@@ -71,7 +73,7 @@ __device__ __forceinline__ uint32_t pack2(int v) {
 }
 
 template <int T, int R>
-__global__ void __launch_bounds__(kCtaThreads) k_inter_i16x2(const __grid_constant__ InterArgs a) {
+__global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_inter_i16x2(const __grid_constant__ InterArgs a) {
     static_assert(R % 16 == 0, "rows per lane must be a multiple of 16");
     static_assert(32 % T == 0 && T >= 4, "lanes must divide the warp");
     constexpr int PAIRS_PER_CTA = kCtaThreads / T;
@@ -182,28 +184,34 @@ __global__ void __launch_bounds__(kCtaThreads) k_inter_i16x2(const __grid_consta
             }
         }
 
-        for (int s = 0; s < steps; ++s) {
+        // One column step of the subwarp.  STEADY: every lane of every subwarp
+        // of the warp is inside its sequence (no predicates) and U = s % 4 is a
+        // compile-time constant, so lane 0's code and boundary selects fold away.
+        auto step = [&](const int s, auto steady_c, auto u_c) {
+            constexpr bool STEADY = decltype(steady_c)::value;
+            constexpr int U = decltype(u_c)::value;
             uint32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1, T);
             uint32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1, T);
             uint32_t cin = __shfl_up_sync(0xffffffffu, pub_c, 1, T);
             const int j = s - k;
-            const bool act = (j >= 0) && (j < Lp);
+            const bool act = STEADY || ((j >= 0) && (j < Lp));
             if (k == 0 && act) {
-                if ((s & 3) == 0) {
+                const int s3 = STEADY ? U : (s & 3);
+                if (s3 == 0) {
                     quad = quad_next;
                     if (s + 4 < Lp) quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
                     if (pass > 0) cp_async_wait1();      // group s/4 has landed
                 }
-                const uint32_t w = (s & 2) ? quad.y : quad.x;
-                cin = (s & 1) ? (w >> 16) : (w & 0xffffu);
+                const uint32_t w = (s3 & 2) ? quad.y : quad.x;
+                cin = (s3 & 1) ? (w >> 16) : (w & 0xffffu);
                 if (pass == 0) {          // H(0,j) = 0, F(1,j) = -o
                     hin = BNEG_O2;
                     fin = BNEG_O2;
                 } else {
-                    const uint2 bv = stg[((s >> 2) & 1) * 4 + (s & 3)];
+                    const uint2 bv = stg[((s >> 2) & 1) * 4 + s3];
                     hin = bv.x;
                     fin = bv.y;
-                    if ((s & 3) == 3) {   // buffer of group s/4 is free: fetch group s/4 + 2 into it
+                    if (s3 == 3) {        // buffer of group s/4 is free: fetch group s/4 + 2 into it
                         if (s + 5 < Lp) {
                             const uint4 *g = bnd + size_t((s >> 2) + 2) * (kBundlePairs * 2);
                             cp_async16(stg + ((s >> 2) & 1) * 4, g);
@@ -246,11 +254,28 @@ __global__ void __launch_bounds__(kCtaThreads) k_inter_i16x2(const __grid_consta
                 pub_h = Ho[R - 1];
                 pub_f = f;
                 pub_c = cin;
-                if (k == T - 1 && !last_pass)   // 4 consecutive columns fill one 32-byte sector
-                    reinterpret_cast<uint2 *>(bnd)[size_t(j >> 2) * (kBundlePairs * 4) + (j & 3)] =
+                if (k == T - 1 && !last_pass) {   // 4 consecutive columns fill one 32-byte sector
+                    const int jl = s - (T - 1);
+                    reinterpret_cast<uint2 *>(bnd)[size_t(jl >> 2) * (kBundlePairs * 4) + (jl & 3)] =
                         make_uint2(Ho[R - 1], f);
+                }
             }
+        };
+        using FalseC = std::integral_constant<bool, false>;
+        using TrueC = std::integral_constant<bool, true>;
+        // Steady columns: s >= T-1 (every lane started) and s + 3 < Lmin (no lane
+        // of any subwarp in the warp has finished), in groups of 4 aligned to s % 4 == 0.
+        const int Lmin = __reduce_min_sync(0xffffffffu, Lp);
+        const int s_steady = (T + 2) & ~3;
+        int s = 0;
+        for (; s < s_steady && s < steps; ++s) step(s, FalseC(), std::integral_constant<int, -1>());
+        for (; s + 3 < Lmin; s += 4) {
+            step(s, TrueC(), std::integral_constant<int, 0>());
+            step(s + 1, TrueC(), std::integral_constant<int, 1>());
+            step(s + 2, TrueC(), std::integral_constant<int, 2>());
+            step(s + 3, TrueC(), std::integral_constant<int, 3>());
         }
+        for (; s < steps; ++s) step(s, FalseC(), std::integral_constant<int, -1>());
     }
 
 #pragma unroll

@@ -5,19 +5,24 @@
 // uses it for long sequences; "solveLong" in Section 3.2).  This kernel is
 // this library's own design for sm_103a:
 //
-// * One CTA scores one PAIR of long database sequences (packed int16x2, as
-//   in the inter-task kernel: the database is sorted, so the two sequences
-//   of a pair have similar lengths).
-// * The CTA's NW warps split the query: in each super-pass of NW*32*R rows,
-//   warp w owns rows [w*32*R, (w+1)*32*R) and its 32 lanes own R rows each.
+// * A pipeline of NW warps scores one PAIR of long database sequences
+//   (packed int16x2, as in the inter-task kernel: the database is sorted, so
+//   the two sequences of a pair have similar lengths).  A CTA runs P such
+//   pipelines on P consecutive pairs.
+// * The warps of a pipeline split the query: in each super-pass of NW*32*R
+//   rows, warp w owns rows [w*32*R, (w+1)*32*R) and its 32 lanes own R rows
+//   each.  Warp w of every pipeline reads the same profile slice, so the
+//   CTA's shared memory holds NW slices for P pairs (the profile is 32 bytes
+//   per query row, and shared memory, not registers, bounds occupancy here).
 //   Inside a warp the lanes form the same skewed wavefront as the inter-task
 //   kernel (lane k works on column j one step after lane k-1; H/F/codes move
 //   lane to lane by shuffle).
-// * Between warps the bottom row of warp w (H-o and F per column) goes to
-//   warp w+1 through a shared-memory ring of D chunks of C columns: a
-//   bounded producer/consumer pipeline with acquire/release flags, so the
-//   warps advance as a wavefront of their own.  Between super-passes the
-//   last warp's bottom row goes through global scratch and a CTA barrier.
+// * Between warps of a pipeline the bottom row of warp w (H-o and F per
+//   column) goes to warp w+1 through a shared-memory ring of D chunks of C
+//   columns: a bounded producer/consumer pipeline with acquire/release
+//   flags, so the warps advance as a wavefront of their own.  Between
+//   super-passes the last warp's bottom row goes through global scratch
+//   (staged back with cp.async) and a CTA barrier.
 // * Every wait is bounded: if a flag does not arrive within the spin limit
 //   the kernel records SW_ERR_TIMEOUT in a status word, tells the other
 //   warps to stop waiting, and finishes without hanging.
@@ -48,6 +53,14 @@ __device__ __forceinline__ uint32_t pack2(int v) {
     return h | (h << 16);
 }
 
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gmem_src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 __device__ __forceinline__ int ld_acquire(const int *p) {
     int v;
     asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
@@ -74,26 +87,31 @@ __device__ bool wait_flag(const int *flag, int target, int *abort_flag, int32_t 
     return false;
 }
 
-template <int R, int NW>
-__global__ void __launch_bounds__(NW * 32) k_intra_i16x2(const __grid_constant__ IntraArgs a) {
+template <int R, int NW, int P>
+__global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_constant__ IntraArgs a) {
     constexpr int T = 32;
     constexpr int TR = T * R;
     constexpr int SPR = NW * TR;
     constexpr int C = kChunk;
     constexpr int D = kDepth;
+    constexpr int NT = NW * P * 32;
+    constexpr int SLICE = kProfRows * TR;                                      // bytes per profile slice
     extern __shared__ __align__(16) uint8_t smem[];
     int8_t *prof_all = reinterpret_cast<int8_t *>(smem);                      // [NW][32][TR]
-    uint2 *ring_all = reinterpret_cast<uint2 *>(smem + NW * kProfRows * TR);  // [NW][D*C], link into warp w
-    int8_t *mat = reinterpret_cast<int8_t *>(ring_all + NW * D * C);          // [32*32]
-    int *full = reinterpret_cast<int *>(mat + kProfRows * kProfRows);         // [NW] chunks written into link w
-    int *empty = full + NW;                                                   // [NW] chunks read from link w
-    int *abort_flag = empty + NW;
-    __shared__ uint32_t red[NW];
+    uint2 *ring_all = reinterpret_cast<uint2 *>(smem + NW * SLICE);           // [P][NW][D*C], link into warp w
+    uint2 *stage_all = ring_all + P * NW * D * C;                             // [P][8] boundary staging
+    int8_t *mat = reinterpret_cast<int8_t *>(stage_all + P * 8);              // [32*32]
+    int *full = reinterpret_cast<int *>(mat + kProfRows * kProfRows);         // [P][NW] chunks written into link w
+    int *empty = full + P * NW;                                               // [P][NW] chunks read from link w
+    int *abort_flag = empty + P * NW;
+    __shared__ uint32_t red[P * NW];
 
-    const int w = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5;
+    const int pl = warp / NW;          // pipeline (pair) within the CTA
+    const int w = warp % NW;           // warp within the pipeline
     const int k = threadIdx.x & 31;
-    // Pair-major order: the longest pairs of every query are dispatched first.
-    const int64_t pair = a.pair_begin + blockIdx.x / a.n_q;
+    // Pair-major order: the longest pair groups of every query are dispatched first.
+    const int64_t group = blockIdx.x / a.n_q;
     const int q = int(blockIdx.x % a.n_q);
     const int64_t q0 = a.q_off[q];
     const int m = int(a.q_off[q + 1] - q0);
@@ -102,31 +120,41 @@ __global__ void __launch_bounds__(NW * 32) k_intra_i16x2(const __grid_constant__
     int32_t *scores = a.scores + int64_t(q) * a.db.n_seqs;
     int32_t *ovf_list = a.ovf_list + int64_t(q) * a.list_stride;
 
-    for (int i = threadIdx.x; i < kProfRows * kProfRows; i += NW * 32) mat[i] = (&a.prof8[0][0])[i];
-    if (threadIdx.x < NW) {
+    for (int i = threadIdx.x; i < kProfRows * kProfRows; i += NT) mat[i] = (&a.prof8[0][0])[i];
+    if (threadIdx.x < P * NW) {
         full[threadIdx.x] = 0;
         empty[threadIdx.x] = 0;
     }
     if (threadIdx.x == 0) *abort_flag = 0;
 
-    const int64_t b = pair / kBundlePairs;
-    const int slot = int(pair % kBundlePairs);
-    const int Lp = (a.db.len[2 * pair] + 3) & ~3;
-    const int64_t off = a.db.bundle_off[b];
-    const uint2 *cptr = reinterpret_cast<const uint2 *>(a.db.codes + off) + slot;
-    uint4 *gbnd = a.boundary ? reinterpret_cast<uint4 *>(a.boundary + int64_t(q) * a.boundary_stride + off / 2) + slot * 2
-                             : nullptr;
+    const int64_t pair = a.pair_begin + group * P + pl;
+    const bool valid = pair < a.pair_end;
+    int Lp = 0;
+    const uint2 *cptr = nullptr;
+    uint2 *gbnd2 = nullptr;              // this pair's global boundary, [column/4][slot][column%4]
+    if (valid) {
+        const int64_t b = pair / kBundlePairs;
+        const int slot = int(pair % kBundlePairs);
+        Lp = (a.db.len[2 * pair] + 3) & ~3;
+        const int64_t off = a.db.bundle_off[b];
+        cptr = reinterpret_cast<const uint2 *>(a.db.codes + off) + slot;
+        if (a.boundary) gbnd2 = a.boundary + int64_t(q) * a.boundary_stride + off / 2 + slot * 4;
+    }
 
     const int o = a.gap_open;
-    // Biased constants: B(v) = v + 32768 per half (see k_inter16.cu).
     const uint32_t BNEG_O2 = pack2(32768 - o);
     const uint32_t ADD_NEG_E = pack2(-a.gap_extend);
     const uint32_t OO = uint32_t(o) | (uint32_t(o) << 16);
     const uint32_t BZERO2 = 0x80008000u;
 
-    int8_t *prof = prof_all + w * kProfRows * TR;
-    uint2 *ring_in = ring_all + w * D * C;
-    uint2 *ring_out = ring_all + ((w + 1) % NW) * D * C;
+    const int8_t *prof = prof_all + w * SLICE;
+    uint2 *ring_in = ring_all + (pl * NW + w) * D * C;
+    uint2 *ring_out = ring_all + (pl * NW + (w + 1) % NW) * D * C;
+    int *full_in = &full[pl * NW + w];
+    int *empty_in = &empty[pl * NW + w];
+    int *full_out = &full[pl * NW + (w + 1) % NW];
+    int *empty_out = &empty[pl * NW + (w + 1) % NW];
+    uint2 *stg = stage_all + pl * 8;
 
     const int nsp = (m + SPR - 1) / SPR;
     uint32_t mx = BZERO2;      // running max of B(H)
@@ -134,18 +162,12 @@ __global__ void __launch_bounds__(NW * 32) k_intra_i16x2(const __grid_constant__
 
     for (int sp = 0; sp < nsp; ++sp) {
         __syncthreads();
-        const int row0 = sp * SPR + w * TR;
-        if (row0 >= m || Lp == 0) continue;
-        const bool from_ring = w > 0;
-        const bool to_ring = (w + 1 < NW) && (row0 + TR < m);
-        const bool from_global = (w == 0) && sp > 0;
-        const bool to_global = !to_ring && (sp + 1 < nsp);
-
-        // This warp's profile slice, layout [a][k][r] for rows row0 .. row0+TR-1.
-        for (int wi = k; wi < kProfRows * TR / 4; wi += 32) {
-            const int e0 = wi * 4;
+        // All NW profile slices of this super-pass, layout [slice][a][k][r].
+        for (int wi = threadIdx.x; wi < NW * SLICE / 4; wi += NT) {
+            const int slice = wi / (SLICE / 4);
+            const int e0 = (wi % (SLICE / 4)) * 4;
             const int res = e0 / TR;
-            const int rr = row0 + (e0 % TR);
+            const int rr = sp * SPR + slice * TR + (e0 % TR);
             uint32_t word = 0;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -157,9 +179,15 @@ __global__ void __launch_bounds__(NW * 32) k_intra_i16x2(const __grid_constant__
                 }
                 word |= (uint32_t(uint8_t(int8_t(v)))) << (8 * c);
             }
-            reinterpret_cast<uint32_t *>(prof)[wi] = word;
+            reinterpret_cast<uint32_t *>(prof_all)[wi] = word;
         }
-        __syncwarp();
+        __syncthreads();
+        const int row0 = sp * SPR + w * TR;
+        if (row0 >= m || Lp == 0) continue;
+        const bool from_ring = w > 0;
+        const bool to_ring = (w + 1 < NW) && (row0 + TR < m);
+        const bool from_global = (w == 0) && sp > 0;
+        const bool to_global = !to_ring && (sp + 1 < nsp);
 
         uint32_t E[R], Ho[R];
 #pragma unroll
@@ -168,13 +196,18 @@ __global__ void __launch_bounds__(NW * 32) k_intra_i16x2(const __grid_constant__
         // pub_h: B(Ho) of this lane's bottom row; pub_f: B(F) of the next lane's top row
         uint32_t pub_h = BNEG_O2, pub_f = BNEG_O2, pub_c = 0;
         uint2 quad = make_uint2(0, 0), quad_next = make_uint2(0, 0);
-        uint4 bc0 = make_uint4(0, 0, 0, 0), bc1 = bc0, bn0 = bc0, bn1 = bc0;
-        uint2 sb0 = make_uint2(0, 0), sb1 = sb0, sb2 = sb0, sb3 = sb0;
+        const uint4 *gsrc = reinterpret_cast<const uint4 *>(gbnd2);
         if (k == 0) {
             quad_next = __ldg(cptr);
             if (from_global) {
-                bn0 = gbnd[0];
-                bn1 = gbnd[1];
+                cp_async16(stg + 0, gsrc);
+                cp_async16(stg + 2, gsrc + 1);
+                cp_async_commit();
+                if (4 < Lp) {
+                    cp_async16(stg + 4, gsrc + kBundlePairs * 2);
+                    cp_async16(stg + 6, gsrc + kBundlePairs * 2 + 1);
+                }
+                cp_async_commit();
             }
         }
         const int steps = Lp + T - 1;
@@ -182,9 +215,8 @@ __global__ void __launch_bounds__(NW * 32) k_intra_i16x2(const __grid_constant__
             const int j31 = s - (T - 1);
             // Flow control (warp-uniform): wait for the producer's chunk before
             // lane 0 enters it, and for ring space before lane 31 starts writing one.
-            if (from_ring && s < Lp && (s % C) == 0) wait_flag(&full[w], g_in + 1, abort_flag, a.status);
-            if (to_ring && j31 >= 0 && (j31 % C) == 0)
-                wait_flag(&empty[(w + 1) % NW], g_out - D + 1, abort_flag, a.status);
+            if (from_ring && s < Lp && (s % C) == 0) wait_flag(full_in, g_in + 1, abort_flag, a.status);
+            if (to_ring && j31 >= 0 && (j31 % C) == 0) wait_flag(empty_out, g_out - D + 1, abort_flag, a.status);
 
             uint32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1, T);
             uint32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1, T);
@@ -194,16 +226,8 @@ __global__ void __launch_bounds__(NW * 32) k_intra_i16x2(const __grid_constant__
             if (k == 0 && act) {
                 if ((s & 3) == 0) {
                     quad = quad_next;
-                    bc0 = bn0;
-                    bc1 = bn1;
-                    if (s + 4 < Lp) {
-                        quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
-                        if (from_global) {
-                            const uint4 *g = gbnd + size_t((s >> 2) + 1) * (kBundlePairs * 2);
-                            bn0 = g[0];
-                            bn1 = g[1];
-                        }
-                    }
+                    if (s + 4 < Lp) quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
+                    if (from_global) cp_async_wait1();
                 }
                 const uint32_t wd = (s & 2) ? quad.y : quad.x;
                 cin = (s & 1) ? (wd >> 16) : (wd & 0xffffu);
@@ -212,9 +236,17 @@ __global__ void __launch_bounds__(NW * 32) k_intra_i16x2(const __grid_constant__
                     hin = v.x;
                     fin = v.y;
                 } else if (from_global) {
-                    const uint4 bq = (s & 2) ? bc1 : bc0;
-                    hin = (s & 1) ? bq.z : bq.x;
-                    fin = (s & 1) ? bq.w : bq.y;
+                    const uint2 bv = stg[((s >> 2) & 1) * 4 + (s & 3)];
+                    hin = bv.x;
+                    fin = bv.y;
+                    if ((s & 3) == 3) {
+                        if (s + 5 < Lp) {
+                            const uint4 *g = gsrc + size_t((s >> 2) + 2) * (kBundlePairs * 2);
+                            cp_async16(stg + ((s >> 2) & 1) * 4, g);
+                            cp_async16(stg + ((s >> 2) & 1) * 4 + 2, g + 1);
+                        }
+                        cp_async_commit();
+                    }
                 } else {                  // H(0,j) = 0, F(1,j) = -o
                     hin = BNEG_O2;
                     fin = BNEG_O2;
@@ -237,9 +269,9 @@ __global__ void __launch_bounds__(NW * 32) k_intra_i16x2(const __grid_constant__
                 uint32_t yprev = 0;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const uint32_t p = prmt(wa[r / 4], wb[r / 4], pair_sel(r % 4));
+                    const uint32_t pr = prmt(wa[r / 4], wb[r / 4], pair_sel(r % 4));
                     const uint32_t e_r = __viaddmax_u16x2(E[r], ADD_NEG_E, Ho[r]);
-                    const uint32_t x = __viaddmax_u16x2(d, p, e_r);
+                    const uint32_t x = __viaddmax_u16x2(d, pr, e_r);
                     const uint32_t y = __vimax3_u16x2(f, x, BZERO2);
                     const uint32_t ho = y - OO;
                     f = __viaddmax_u16x2(f, ADD_NEG_E, ho);
@@ -254,30 +286,21 @@ __global__ void __launch_bounds__(NW * 32) k_intra_i16x2(const __grid_constant__
                 pub_f = f;
                 pub_c = cin;
                 if (k == T - 1) {
-                    if (to_ring) {
+                    if (to_ring)
                         ring_out[(g_out % D) * C + (j % C)] = make_uint2(Ho[R - 1], f);
-                    } else if (to_global) {
-                        sb0 = sb1;
-                        sb1 = sb2;
-                        sb2 = sb3;
-                        sb3 = make_uint2(Ho[R - 1], f);
-                        if ((j & 3) == 3) {
-                            uint4 *g = gbnd + size_t(j >> 2) * (kBundlePairs * 2);
-                            g[0] = make_uint4(sb0.x, sb0.y, sb1.x, sb1.y);
-                            g[1] = make_uint4(sb2.x, sb2.y, sb3.x, sb3.y);
-                        }
-                    }
+                    else if (to_global)
+                        gbnd2[size_t(j >> 2) * (kBundlePairs * 4) + (j & 3)] = make_uint2(Ho[R - 1], f);
                 }
             }
             // Release a consumed chunk (lane 0 has used its last column) and
             // publish a produced one (lane 31 wrote its last column).
             if (from_ring && s < Lp && ((s % C) == C - 1 || s == Lp - 1)) {
-                if (k == 0) st_release(&empty[w], g_in + 1);
+                if (k == 0) st_release(empty_in, g_in + 1);
                 ++g_in;
             }
             if (to_ring && j31 >= 0 && j31 < Lp && ((j31 % C) == C - 1 || j31 == Lp - 1)) {
                 __syncwarp();
-                if (k == T - 1) st_release(&full[(w + 1) % NW], g_out + 1);
+                if (k == T - 1) st_release(full_out, g_out + 1);
                 ++g_out;
             }
         }
@@ -288,11 +311,11 @@ __global__ void __launch_bounds__(NW * 32) k_intra_i16x2(const __grid_constant__
         const uint32_t other = __shfl_xor_sync(0xffffffffu, mx, dd);
         mx = __vimax3_u16x2(mx, other, other);
     }
-    if (k == 0) red[w] = mx;
+    if (k == 0) red[warp] = mx;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (valid && w == 0 && k == 0) {
 #pragma unroll
-        for (int i = 1; i < NW; ++i) mx = __vimax3_u16x2(mx, red[i], red[i]);
+        for (int i = 1; i < NW; ++i) mx = __vimax3_u16x2(mx, red[pl * NW + i], red[pl * NW + i]);
         const int hA = int(mx & 0xffffu) - 32768;
         const int hB = int(mx >> 16) - 32768;
         const int64_t tA = 2 * pair;
@@ -315,31 +338,33 @@ __global__ void __launch_bounds__(NW * 32) k_intra_i16x2(const __grid_constant__
     }
 }
 
-template <int R, int NW>
+template <int R, int NW, int P>
 size_t intra_smem() {
-    return size_t(NW) * kProfRows * 32 * R + size_t(NW) * kDepth * kChunk * sizeof(uint2) + kProfRows * kProfRows +
-           sizeof(int) * (2 * NW + 1);
+    return size_t(NW) * kProfRows * 32 * R + size_t(P) * NW * kDepth * kChunk * sizeof(uint2) +
+           size_t(P) * 8 * sizeof(uint2) + kProfRows * kProfRows + sizeof(int) * (2 * P * NW + 1);
 }
 
-template <int R, int NW>
-cudaError_t launch_rn(const IntraArgs &a, cudaStream_t s) {
+template <int R, int NW, int P>
+cudaError_t launch_rnp(const IntraArgs &a, cudaStream_t s) {
     const int64_t pairs = a.pair_end - a.pair_begin;
     if (pairs <= 0 || a.n_q <= 0) return cudaSuccess;
-    const int64_t grid = pairs * a.n_q;
+    const int64_t groups = (pairs + P - 1) / P;
+    const int64_t grid = groups * a.n_q;
     if (grid >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
-    const size_t smem = intra_smem<R, NW>();   // attribute set by prepare_intra_i16x2 at planning
-    k_intra_i16x2<R, NW><<<unsigned(grid), NW * 32, smem, s>>>(a);
+    const size_t smem = intra_smem<R, NW, P>();   // attribute set by prepare_intra_i16x2 at planning
+    k_intra_i16x2<R, NW, P><<<unsigned(grid), NW * P * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int R, int NW>
-cudaError_t prepare_rn() {
-    return cudaFuncSetAttribute(k_intra_i16x2<R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(intra_smem<R, NW>()));
+template <int R, int NW, int P>
+cudaError_t prepare_rnp() {
+    return cudaFuncSetAttribute(k_intra_i16x2<R, NW, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(intra_smem<R, NW, P>()));
 }
 
 }  // namespace
 
+// Shapes: warps per pipeline (NW) and pipelines per CTA (P), 16 rows per lane.
 bool intra_config_supported(int warps, int rows) {
     return (warps == 4 || warps == 8) && rows == 16;
 }
@@ -347,14 +372,14 @@ bool intra_config_supported(int warps, int rows) {
 int intra_rows_per_superpass(int warps, int rows) { return warps * 32 * rows; }
 
 cudaError_t prepare_intra_i16x2(int warps, int rows) {
-    if (rows == 16 && warps == 4) return prepare_rn<16, 4>();
-    if (rows == 16 && warps == 8) return prepare_rn<16, 8>();
+    if (rows == 16 && warps == 4) return prepare_rnp<16, 4, 3>();
+    if (rows == 16 && warps == 8) return prepare_rnp<16, 8, 1>();
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_intra_i16x2(const IntraArgs &a, int warps, int rows, cudaStream_t s) {
-    if (rows == 16 && warps == 4) return launch_rn<16, 4>(a, s);
-    if (rows == 16 && warps == 8) return launch_rn<16, 8>(a, s);
+    if (rows == 16 && warps == 4) return launch_rnp<16, 4, 3>(a, s);
+    if (rows == 16 && warps == 8) return launch_rnp<16, 8, 1>(a, s);
     return cudaErrorInvalidValue;
 }
 

@@ -30,7 +30,7 @@ from . import binding
 _POISON = object()
 
 
-@dataclasses.dataclass
+@dataclasses.dataclass(eq=False)        # identity equality: fields hold arrays
 class _Request:
     codes: np.ndarray
     future: Future
@@ -38,7 +38,7 @@ class _Request:
     nbytes: int
 
 
-@dataclasses.dataclass
+@dataclasses.dataclass(eq=False)
 class _Batch:
     requests: list
     stream: object
@@ -125,15 +125,17 @@ class SearchServer:
             self.cv.notify_all()
         return fut
 
-    def close(self):
+    def close(self, timeout: float = 600.0):
         with self.cv:
             self.closed = True
             self.cv.notify_all()
-        self.dispatcher.join()
+        self.dispatcher.join(timeout)
         self.inflight.put(_POISON)
-        self.completer.join()
+        self.completer.join(timeout)
         if self.error:
             raise self.error
+        if self.dispatcher.is_alive() or self.completer.is_alive():
+            raise TimeoutError("server threads did not finish")
 
     def stats(self) -> dict:
         lat = np.array(self.latencies) if self.latencies else np.zeros(1)
@@ -161,7 +163,16 @@ class SearchServer:
         torch.cuda.set_device(self.device)
         try:
             while True:
-                worker = self.free_workers.get()
+                worker = None
+                while worker is None:           # a failed completer never returns workers
+                    try:
+                        worker = self.free_workers.get(timeout=0.1)
+                    except queue.Empty:
+                        if self.error is not None:
+                            return
+                        with self.cv:
+                            if self.closed and not self.pending:
+                                return
                 with self.cv:
                     while not self.pending and not self.closed:
                         self.cv.wait()
@@ -170,6 +181,8 @@ class SearchServer:
                         return
                     batch, nbytes = self._take_batch()
                     while not batch:                       # memory budget: wait for completions
+                        if self.error is not None:
+                            return
                         self.cv.wait(timeout=0.05)
                         batch, nbytes = self._take_batch()
                     self.in_flight_bytes += nbytes
@@ -203,8 +216,34 @@ class SearchServer:
                                  int(lens.sum()) * self.db_residues))
 
     def _complete(self):
-        """Resolve batches as their events complete (in any order across streams)."""
+        """Resolve batches as their events complete (in any order across streams).
+        If anything fails, every outstanding future gets the exception."""
         live = []
+        try:
+            self._complete_loop(live)
+        except BaseException as e:  # noqa: BLE001 - surfaced through the futures and close()
+            self.error = e
+            for b in live:
+                for r in b.requests:
+                    if not r.future.done():
+                        r.future.set_exception(e)
+            while True:
+                try:
+                    b = self.inflight.get_nowait()
+                except queue.Empty:
+                    break
+                if b is not _POISON:
+                    for r in b.requests:
+                        if not r.future.done():
+                            r.future.set_exception(e)
+            with self.cv:
+                for r in self.pending:
+                    if not r.future.done():
+                        r.future.set_exception(e)
+                self.pending.clear()
+                self.cv.notify_all()
+
+    def _complete_loop(self, live):
         done = False
         while not done or live:
             try:
@@ -224,7 +263,6 @@ class SearchServer:
                 continue
             now = time.perf_counter()
             for b in finished:
-                live.remove(b)
                 h = b.hits_host.numpy()
                 for i, r in enumerate(b.requests):
                     out = np.empty(self.top_k, dtype=binding.HIT_DTYPE)
@@ -241,4 +279,5 @@ class SearchServer:
                     self.batch_sizes.append(len(b.requests))
                     self.t_last = now
                     self.cv.notify_all()
+                live[:] = [x for x in live if x is not b]   # only once its futures are resolved
                 self.free_workers.put(b.worker)
