@@ -178,6 +178,17 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(nm)
         os.unlink(self.path)
+        if not sm:
+            # timed region shorter than one sampling period: read the clocks once now
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.gpu}", "--query-gpu=clocks.sm,clocks.max.sm",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=10).stdout.split(",")
+                return {"sm_mhz": float(out[0]), "sm_max_mhz": float(out[1]), "reasons": sorted(reasons),
+                        "samples": 0, "note": "timed region shorter than the 200 ms sampling period; "
+                                              "clocks read once right after it"}
+            except Exception:
+                pass
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
@@ -298,7 +309,7 @@ def run_ours(args, dist: Dist):
     if dist.rank == 0:
         rate_dpx, sms = swdb.sw_probe_alu_rate(dev, 0)
         rate_cells, _ = swdb.sw_probe_alu_rate(dev, 1)
-        mhz = clk.get("sm_mhz") or torch.cuda.get_device_properties(dev).clock_rate / 1e3
+        mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
         peak = rate_dpx * sms * mhz * 1e6 / DPX_OPS_PER_CELL / 1e9
         ceiling = rate_cells * sms * mhz * 1e6 / 1e9
         inter_cells = float(sum(s["inter_cells"] for s in st_all))

@@ -19,6 +19,8 @@
 // Saturated (query, sequence) results are appended to per-query lists, with
 // the two sequences of a database pair merged into one entry (pair*4 + mask)
 // because the int32 rescore uses the pair's boundary region for both.
+#include <type_traits>
+
 #include "swdb_internal.cuh"
 
 namespace swdb {
@@ -148,28 +150,33 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_batch_i16x2(
                 }
             }
             const int steps = Lw + T - 1;
-            for (int s = 0; s < steps; ++s) {
+            // One column step; STEADY: all lanes of the warp inside their sequences,
+            // U = s % 4 known at compile time (see k_inter16.cu).
+            auto step = [&](const int s, auto steady_c, auto u_c) {
+                constexpr bool STEADY = decltype(steady_c)::value;
+                constexpr int U = decltype(u_c)::value;
                 uint32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1, T);
                 uint32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1, T);
                 uint32_t cin = __shfl_up_sync(0xffffffffu, pub_c, 1, T);
                 const int j = s - k;
-                const bool act = (j >= 0) && (j < Lp);
+                const bool act = STEADY || ((j >= 0) && (j < Lp));
                 if (k == 0 && act) {
-                    if ((s & 3) == 0) {
+                    const int s3 = STEADY ? U : (s & 3);
+                    if (s3 == 0) {
                         quad = quad_next;
                         if (s + 4 < Lp) quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
                         if (pass > 0) cp_async_wait1();
                     }
-                    const uint32_t wd = (s & 2) ? quad.y : quad.x;
-                    cin = (wd >> (16 * (s & 1) + 8 * h)) & 0xffu;
+                    const uint32_t wd = (s3 & 2) ? quad.y : quad.x;
+                    cin = (wd >> (16 * (s3 & 1) + 8 * h)) & 0xffu;
                     if (pass == 0) {
                         hin = BNEG_O2;
                         fin = BNEG_O2;
                     } else {
-                        const uint2 bv = stg[((s >> 2) & 1) * 4 + (s & 3)];
+                        const uint2 bv = stg[((s >> 2) & 1) * 4 + s3];
                         hin = bv.x;
                         fin = bv.y;
-                        if ((s & 3) == 3) {
+                        if (s3 == 3) {
                             if (s + 5 < Lp) {
                                 const uint4 *g = gsrc + size_t((s >> 2) + 2) * 2;
                                 cp_async16(stg + ((s >> 2) & 1) * 4, g);
@@ -207,9 +214,22 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_batch_i16x2(
                     pub_h = Ho[R - 1];
                     pub_f = f;
                     pub_c = cin;
-                    if (k == T - 1 && !last_pass) slot_scratch[j] = make_uint2(Ho[R - 1], f);
+                    if (k == T - 1 && !last_pass) slot_scratch[s - (T - 1)] = make_uint2(Ho[R - 1], f);
                 }
+            };
+            using FalseC = std::integral_constant<bool, false>;
+            using TrueC = std::integral_constant<bool, true>;
+            const int Lmin = __reduce_min_sync(0xffffffffu, Lp);
+            const int s_steady = (T + 2) & ~3;
+            int s = 0;
+            for (; s < s_steady && s < steps; ++s) step(s, FalseC(), std::integral_constant<int, -1>());
+            for (; s + 3 < Lmin; s += 4) {
+                step(s, TrueC(), std::integral_constant<int, 0>());
+                step(s + 1, TrueC(), std::integral_constant<int, 1>());
+                step(s + 2, TrueC(), std::integral_constant<int, 2>());
+                step(s + 3, TrueC(), std::integral_constant<int, 3>());
             }
+            for (; s < steps; ++s) step(s, FalseC(), std::integral_constant<int, -1>());
         }
 
 #pragma unroll

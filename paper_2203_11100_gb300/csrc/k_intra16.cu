@@ -29,6 +29,8 @@
 // Per cell pair the arithmetic is the same biased-domain sequence as the
 // inter-task kernel (four DPX operations, one 32-bit subtraction, one byte
 // permute and half a running max; see k_inter16.cu for the derivation).
+#include <type_traits>
+
 #include "swdb_internal.cuh"
 
 namespace swdb {
@@ -211,7 +213,11 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
             }
         }
         const int steps = Lp + T - 1;
-        for (int s = 0; s < steps; ++s) {
+        // One column step; STEADY: every lane inside the sequence (s >= 31 and
+        // s + 3 < Lp), U = s % 4 at compile time (see k_inter16.cu).
+        auto step = [&](const int s, auto steady_c, auto u_c) {
+            constexpr bool STEADY = decltype(steady_c)::value;
+            constexpr int U = decltype(u_c)::value;
             const int j31 = s - (T - 1);
             // Flow control (warp-uniform): wait for the producer's chunk before
             // lane 0 enters it, and for ring space before lane 31 starts writing one.
@@ -222,24 +228,25 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
             uint32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1, T);
             uint32_t cin = __shfl_up_sync(0xffffffffu, pub_c, 1, T);
             const int j = s - k;
-            const bool act = (j >= 0) && (j < Lp);
+            const bool act = STEADY || ((j >= 0) && (j < Lp));
             if (k == 0 && act) {
-                if ((s & 3) == 0) {
+                const int s3 = STEADY ? U : (s & 3);
+                if (s3 == 0) {
                     quad = quad_next;
                     if (s + 4 < Lp) quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
                     if (from_global) cp_async_wait1();
                 }
-                const uint32_t wd = (s & 2) ? quad.y : quad.x;
-                cin = (s & 1) ? (wd >> 16) : (wd & 0xffffu);
+                const uint32_t wd = (s3 & 2) ? quad.y : quad.x;
+                cin = (s3 & 1) ? (wd >> 16) : (wd & 0xffffu);
                 if (from_ring) {
                     const uint2 v = ring_in[(g_in % D) * C + (s % C)];
                     hin = v.x;
                     fin = v.y;
                 } else if (from_global) {
-                    const uint2 bv = stg[((s >> 2) & 1) * 4 + (s & 3)];
+                    const uint2 bv = stg[((s >> 2) & 1) * 4 + s3];
                     hin = bv.x;
                     fin = bv.y;
-                    if ((s & 3) == 3) {
+                    if (s3 == 3) {
                         if (s + 5 < Lp) {
                             const uint4 *g = gsrc + size_t((s >> 2) + 2) * (kBundlePairs * 2);
                             cp_async16(stg + ((s >> 2) & 1) * 4, g);
@@ -287,9 +294,9 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
                 pub_c = cin;
                 if (k == T - 1) {
                     if (to_ring)
-                        ring_out[(g_out % D) * C + (j % C)] = make_uint2(Ho[R - 1], f);
+                        ring_out[(g_out % D) * C + (j31 % C)] = make_uint2(Ho[R - 1], f);
                     else if (to_global)
-                        gbnd2[size_t(j >> 2) * (kBundlePairs * 4) + (j & 3)] = make_uint2(Ho[R - 1], f);
+                        gbnd2[size_t(j31 >> 2) * (kBundlePairs * 4) + (j31 & 3)] = make_uint2(Ho[R - 1], f);
                 }
             }
             // Release a consumed chunk (lane 0 has used its last column) and
@@ -303,7 +310,18 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
                 if (k == T - 1) st_release(full_out, g_out + 1);
                 ++g_out;
             }
+        };
+        using FalseC = std::integral_constant<bool, false>;
+        using TrueC = std::integral_constant<bool, true>;
+        int s = 0;
+        for (; s < 32 && s < steps; ++s) step(s, FalseC(), std::integral_constant<int, -1>());
+        for (; s + 3 < Lp; s += 4) {
+            step(s, TrueC(), std::integral_constant<int, 0>());
+            step(s + 1, TrueC(), std::integral_constant<int, 1>());
+            step(s + 2, TrueC(), std::integral_constant<int, 2>());
+            step(s + 3, TrueC(), std::integral_constant<int, 3>());
         }
+        for (; s < steps; ++s) step(s, FalseC(), std::integral_constant<int, -1>());
     }
 
 #pragma unroll
