@@ -88,6 +88,8 @@ typedef struct {
     void *workspace;          /* caller-owned device scratch, or NULL for the handle's own */
     size_t workspace_bytes;   /* size of workspace */
     int32_t flags;            /* SW_FLAG_* bits */
+    int32_t long_rows_per_lane; /* query rows per lane of the intra-task kernel: 16 (4-warp
+                                   pipelines) or 32 (2-warp pipelines); 0 = library choice */
 } sw_search_opts;
 
 /* Capture the device work of the search into a CUDA graph on first use and

@@ -35,7 +35,8 @@ class SwError(RuntimeError):
 class SwSearchOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("mode", ctypes.c_int32), ("long_cutoff", ctypes.c_int64),
                 ("lanes", ctypes.c_int32), ("rows_per_lane", ctypes.c_int32),
-                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t), ("flags", ctypes.c_int32)]
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t), ("flags", ctypes.c_int32),
+                ("long_rows_per_lane", ctypes.c_int32)]
 
 
 class SwSearchStats(ctypes.Structure):
@@ -153,9 +154,10 @@ def sw_db_get_info(handle) -> dict:
     return {f: getattr(info, f) for f, _ in SwDbInfo._fields_}
 
 
-def _opts(precision, mode, long_cutoff, lanes, rows_per_lane, workspace, flags=0):
+def _opts(precision, mode, long_cutoff, lanes, rows_per_lane, workspace, flags=0, long_rows_per_lane=0):
     o = SwSearchOpts()
     o.flags = flags
+    o.long_rows_per_lane = long_rows_per_lane
     o.precision = precision
     o.mode = mode
     o.long_cutoff = long_cutoff
@@ -171,9 +173,9 @@ def _opts(precision, mode, long_cutoff, lanes, rows_per_lane, workspace, flags=0
 
 
 def sw_search_workspace_size(handle, q_offsets, top_k: int, precision=SW_PREC_AUTO, mode=SW_MODE_AUTO,
-                             long_cutoff=0, lanes=0, rows_per_lane=0) -> int:
+                             long_cutoff=0, lanes=0, rows_per_lane=0, long_rows_per_lane=0) -> int:
     q_offsets = np.ascontiguousarray(q_offsets, dtype=np.int64)
-    o = _opts(precision, mode, long_cutoff, lanes, rows_per_lane, None)
+    o = _opts(precision, mode, long_cutoff, lanes, rows_per_lane, None, 0, long_rows_per_lane)
     n = ctypes.c_size_t()
     _check(load_library().sw_search_workspace_size(handle, q_offsets.ctypes.data, len(q_offsets) - 1, top_k,
                                                    ctypes.byref(o), ctypes.byref(n)))
@@ -182,7 +184,8 @@ def sw_search_workspace_size(handle, q_offsets, top_k: int, precision=SW_PREC_AU
 
 def sw_search(handle, queries, q_offsets, matrix, gap_open: int, gap_extend: int, top_k: int,
               scores_out=None, hits_out=None, precision=SW_PREC_AUTO, mode=SW_MODE_AUTO, long_cutoff=0,
-              lanes=0, rows_per_lane=0, workspace=None, stats: bool = False, stream=None, graph: bool = False):
+              lanes=0, rows_per_lane=0, workspace=None, stats: bool = False, stream=None, graph: bool = False,
+              long_rows_per_lane=0):
     """Run sw_search.  Outputs are written into scores_out / hits_out (numpy =
     host, torch CUDA tensor = device).  Returns a stats dict when stats=True."""
     lib = load_library()
@@ -193,7 +196,8 @@ def sw_search(handle, queries, q_offsets, matrix, gap_open: int, gap_extend: int
     if hits_out is not None and isinstance(hits_out, np.ndarray) and hits_out.dtype != HIT_DTYPE:
         raise TypeError("hits_out must have dtype HIT_DTYPE")
     hp, h_cuda = _addr(hits_out, None, "hits_out")
-    o = _opts(precision, mode, long_cutoff, lanes, rows_per_lane, workspace, SW_FLAG_GRAPH if graph else 0)
+    o = _opts(precision, mode, long_cutoff, lanes, rows_per_lane, workspace, SW_FLAG_GRAPH if graph else 0,
+              long_rows_per_lane)
     st = SwSearchStats() if stats else None
     if stream is None and (q_cuda or s_cuda or h_cuda or workspace is not None):
         import torch

@@ -185,8 +185,8 @@ struct Plan {
     int64_t long_end_pair = 0;       // pairs [0, long_end_pair) hold the long sequences
     int64_t n_long = 0;              // real sequences among them
     int64_t long_residues = 0;
-    int lanes_long = 32, rows_long = 16;   // per warp of the intra-task kernel
-    int warps_long = 4;
+    int lanes_long = 32, rows_long = 32;   // per warp of the intra-task kernel
+    int warps_long = 2;
     int64_t long_codes_bytes = 0;          // layout bytes of the long bundles (a prefix)
     bool need_long_boundary = false;
     // batched mode: query pairs (a = longer, b = next, -1 if none), persistent grid
@@ -284,6 +284,11 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
     // with wide subwarps on a second stream, concurrently with the rest, so a
     // handful of very long sequences do not set the length of the main launch.
     const int64_t cutoff = opts && opts->long_cutoff ? opts->long_cutoff : 3072;
+    if (opts && opts->long_rows_per_lane) {
+        if (opts->long_rows_per_lane == 16) { p.rows_long = 16; p.warps_long = 4; }
+        else if (opts->long_rows_per_lane == 32) { p.rows_long = 32; p.warps_long = 2; }
+        else return fail(SW_ERR_UNSUPPORTED, "long_rows_per_lane must be 16 or 32");
+    }
     int64_t nlb = 0;
     if (cutoff > 0 && p.precision == SW_PREC_I16)
         while (nlb < db->n_bundles && db->h_bundle_len[size_t(nlb)] > cutoff) ++nlb;

@@ -164,12 +164,17 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
 
     for (int sp = 0; sp < nsp; ++sp) {
         __syncthreads();
-        // All NW profile slices of this super-pass, layout [slice][a][k][r].
+        // All NW profile slices of this super-pass.  Within a slice the layout is
+        // [residue a][16-row half h][lane k][16 rows]: lane k's rows 16h..16h+15 sit
+        // at a*TR + h*32*16 + k*16 (quarter-warp lanes read consecutive 16-byte slots).
         for (int wi = threadIdx.x; wi < NW * SLICE / 4; wi += NT) {
             const int slice = wi / (SLICE / 4);
             const int e0 = (wi % (SLICE / 4)) * 4;
             const int res = e0 / TR;
-            const int rr = sp * SPR + slice * TR + (e0 % TR);
+            const int within = e0 % TR;                 // kk * R + r
+            const int kk = within / R, rl = within % R;
+            const int phys = slice * SLICE + res * TR + (rl >> 4) * (T * 16) + kk * 16 + (rl & 15);
+            const int rr = sp * SPR + slice * TR + within;
             uint32_t word = 0;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -181,7 +186,7 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
                 }
                 word |= (uint32_t(uint8_t(int8_t(v)))) << (8 * c);
             }
-            reinterpret_cast<uint32_t *>(prof_all)[wi] = word;
+            reinterpret_cast<uint32_t *>(prof_all)[phys / 4] = word;
         }
         __syncthreads();
         const int row0 = sp * SPR + w * TR;
@@ -261,13 +266,13 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
             }
             if (act) {
                 const int ta = int(cin & 0xffu), tb = int((cin >> 8) & 0xffu);
-                const uint4 *pa = reinterpret_cast<const uint4 *>(prof + ta * TR + k * R);
-                const uint4 *pb = reinterpret_cast<const uint4 *>(prof + tb * TR + k * R);
+                const uint4 *pa = reinterpret_cast<const uint4 *>(prof + ta * TR + k * 16);
+                const uint4 *pb = reinterpret_cast<const uint4 *>(prof + tb * TR + k * 16);
                 uint32_t wa[R / 4], wb[R / 4];
 #pragma unroll
                 for (int v = 0; v < R / 16; ++v) {
-                    const uint4 x = pa[v];
-                    const uint4 y = pb[v];
+                    const uint4 x = pa[v * T];
+                    const uint4 y = pb[v * T];
                     wa[4 * v + 0] = x.x; wa[4 * v + 1] = x.y; wa[4 * v + 2] = x.z; wa[4 * v + 3] = x.w;
                     wb[4 * v + 0] = y.x; wb[4 * v + 1] = y.y; wb[4 * v + 2] = y.z; wb[4 * v + 3] = y.w;
                 }
@@ -382,22 +387,23 @@ cudaError_t prepare_rnp() {
 
 }  // namespace
 
-// Shapes: warps per pipeline (NW) and pipelines per CTA (P), 16 rows per lane.
+// Shapes: warps per pipeline (NW) and rows per lane (R); pipelines per CTA (P)
+// follow: (4 warps, 16 rows) x 3 pipelines, (2 warps, 32 rows) x 4 pipelines.
 bool intra_config_supported(int warps, int rows) {
-    return (warps == 4 || warps == 8) && rows == 16;
+    return (warps == 4 && rows == 16) || (warps == 2 && rows == 32);
 }
 
 int intra_rows_per_superpass(int warps, int rows) { return warps * 32 * rows; }
 
 cudaError_t prepare_intra_i16x2(int warps, int rows) {
     if (rows == 16 && warps == 4) return prepare_rnp<16, 4, 3>();
-    if (rows == 16 && warps == 8) return prepare_rnp<16, 8, 1>();
+    if (rows == 32 && warps == 2) return prepare_rnp<32, 2, 4>();
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_intra_i16x2(const IntraArgs &a, int warps, int rows, cudaStream_t s) {
     if (rows == 16 && warps == 4) return launch_rnp<16, 4, 3>(a, s);
-    if (rows == 16 && warps == 8) return launch_rnp<16, 8, 1>(a, s);
+    if (rows == 32 && warps == 2) return launch_rnp<32, 2, 4>(a, s);
     return cudaErrorInvalidValue;
 }
 

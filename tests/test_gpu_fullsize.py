@@ -1,0 +1,109 @@
+"""Parity at the benchmark's full sizes, in the launch configuration it times.
+
+The oracle cannot score whole workloads of 10^12-10^14 cells, so each
+full-size search is checked (a) against the oracle one pair at a time on a
+deterministic sample -- every top-k hit, the longest database sequences and
+random pairs -- and (b) by properties that hold at any size: every score is
+>= 0, the top-k hits are exactly the best entries of the returned score table
+in (score desc, index asc) order, and the batched form returns the same full
+score table as the plain form.  Scores are integers: tolerance 0.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _hits_consistent(scores_row, hits_row, k):
+    s, i = oracle.top_k(scores_row, k)
+    np.testing.assert_array_equal(hits_row["score"], s)
+    np.testing.assert_array_equal(hits_row["db_index"], i)
+
+
+def _sample_pairs(w, scores, hits, rng, n_random, n_longest):
+    qi, ti = [], []
+    for q in range(w.queries.n):                         # every top-k hit
+        for t in hits[q]["db_index"]:
+            if t >= 0:
+                qi.append(q)
+                ti.append(int(t))
+    longest = np.argsort(w.db.lengths)[::-1][:n_longest]  # the longest database sequences
+    for q in range(w.queries.n):
+        for t in longest:
+            qi.append(q)
+            ti.append(int(t))
+    qi += list(rng.integers(0, w.queries.n, n_random))   # random pairs
+    ti += list(rng.integers(0, w.db.n, n_random))
+    qi = np.array(qi, dtype=np.int64)
+    ti = np.array(ti, dtype=np.int64)
+    want = oracle.score_pairs(w.queries, w.db, qi, ti, w.matrix, w.gap_open, w.gap_extend)
+    np.testing.assert_array_equal(scores[qi, ti].astype(np.int64), want)
+    return len(qi)
+
+
+def test_swissprot_like_full_size_plain_and_batched(gpu):
+    w = synth.make_workload("swissprot_like_20q")       # the default benchmark workload
+    rng = np.random.default_rng(70)
+    with gpu.Database(w.db.residues, w.db.offsets, len(synth.ALPHABET)) as d:
+        sp, hp, st = d.search(w.queries.residues, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend,
+                              top_k=w.top_k, stats=True)  # bench's launch configuration (plain, library shapes)
+        sb, hb, _ = d.search(w.queries.residues, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend,
+                             top_k=w.top_k, mode=gpu.SW_MODE_BATCHED)
+    assert st["long_sequences"] > 0                      # the long-sequence path took part
+    assert (sp >= 0).all()
+    np.testing.assert_array_equal(sp, sb)
+    np.testing.assert_array_equal(hp, hb)
+    for q in range(w.queries.n):
+        _hits_consistent(sp[q], hp[q], w.top_k)
+    n = _sample_pairs(w, sp, hp, rng, n_random=600, n_longest=3)
+    assert n >= 600 + 200
+
+
+def test_long_queries_full_size(gpu):
+    w = synth.make_workload("long_4q_50k")
+    rng = np.random.default_rng(71)
+    with gpu.Database(w.db.residues, w.db.offsets, len(synth.ALPHABET)) as d:
+        s, h, st = d.search(w.queries.residues, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend,
+                            top_k=w.top_k, stats=True)
+    assert st["long_sequences"] >= 4000
+    assert (s >= 0).all()
+    for q in range(w.queries.n):
+        _hits_consistent(s[q], h[q], w.top_k)
+    # long x long pairs cost up to 1.2e9 cells each: sample the hits, two long and
+    # a few medium sequences, and random pairs
+    qi, ti = [], []
+    for q in range(w.queries.n):
+        for t in h[q]["db_index"][:3]:
+            qi.append(q)
+            ti.append(int(t))
+    order = np.argsort(w.db.lengths)
+    picks = [order[-1], order[int(len(order) * 0.95)], order[len(order) // 2], order[0]]
+    for q in range(w.queries.n):
+        for t in picks:
+            qi.append(q)
+            ti.append(int(t))
+    qi += list(rng.integers(0, w.queries.n, 40))
+    ti += list(rng.integers(0, w.db.n, 40))
+    qi = np.array(qi, np.int64)
+    ti = np.array(ti, np.int64)
+    want = oracle.score_pairs(w.queries, w.db, qi, ti, w.matrix, w.gap_open, w.gap_extend)
+    np.testing.assert_array_equal(s[qi, ti].astype(np.int64), want)
+
+
+def test_batched_512_queries_sampled(gpu):
+    w = synth.make_workload("batched_512q", db_scale=0.1)
+    rng = np.random.default_rng(72)
+    with gpu.Database(w.db.residues, w.db.offsets, len(synth.ALPHABET)) as d:
+        s, h, st = d.search(w.queries.residues, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend,
+                            top_k=w.top_k, mode=gpu.SW_MODE_BATCHED, stats=True)
+    assert st["mode_used"] == gpu.SW_MODE_BATCHED
+    assert (s >= 0).all()
+    for q in range(0, w.queries.n, 7):
+        _hits_consistent(s[q], h[q], w.top_k)
+    qi = rng.integers(0, w.queries.n, 800).astype(np.int64)
+    ti = rng.integers(0, w.db.n, 800).astype(np.int64)
+    want = oracle.score_pairs(w.queries, w.db, qi, ti, w.matrix, w.gap_open, w.gap_extend)
+    np.testing.assert_array_equal(s[qi, ti].astype(np.int64), want)

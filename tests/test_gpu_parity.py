@@ -139,14 +139,15 @@ def test_long_sequence_split(gpu, cutoff):
         assert st["long_sequences"] == 0
 
 
-def test_intra_task_multi_superpass(gpu):
-    """Queries longer than one super-pass of the intra-task kernel (4 warps x
-    512 rows), against long sequences of ragged lengths."""
+@pytest.mark.parametrize("long_rows", [16, 32])
+def test_intra_task_multi_superpass(gpu, long_rows):
+    """Queries longer than one super-pass of the intra-task kernel (2048
+    rows in both shapes), against long sequences of ragged lengths."""
     rng = np.random.default_rng(23)
     lens = np.concatenate([rng.integers(65, 900, 40), rng.integers(1, 64, 30), [1, 2, 3, 4, 5]])
     db = synth.seqset_from_lengths(rng, lens)
-    qs = synth.seqset_from_lengths(rng, [2047, 2048, 2049, 4200])
-    st = _check(gpu, qs, db, synth.blosum62(), 10, 1, long_cutoff=64)
+    qs = synth.seqset_from_lengths(rng, [2047, 2048, 2049, 4200, 33])
+    st = _check(gpu, qs, db, synth.blosum62(), 10, 1, long_cutoff=64, long_rows_per_lane=long_rows)
     assert st["long_sequences"] >= 40
 
 
