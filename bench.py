@@ -58,6 +58,8 @@ def parse_args(argv=None):
     p.add_argument("--rows", type=int, default=0)
     p.add_argument("--precision", type=int, default=0)
     p.add_argument("--long-rows", type=int, default=0, help="rows per lane of the intra-task kernel (16 or 32)")
+    p.add_argument("--long-cutoff", type=int, default=0,
+                   help="database sequences longer than this go to the intra-task kernel (0 = library default)")
     p.add_argument("--mode", choices=["plain", "batched"], default="plain",
                    help="plain: one inter-task launch per query (the paper's form); "
                         "batched: all queries in one persistent launch")
@@ -260,6 +262,7 @@ def run_ours(args, dist: Dist):
     scores = torch.empty((nq, n), dtype=torch.int32, device=f"cuda:{dev}")
     hits = torch.empty((nq, w.top_k, 2), dtype=torch.int64, device=f"cuda:{dev}")
     kw = dict(lanes=args.lanes, rows_per_lane=args.rows, precision=args.precision, long_rows_per_lane=args.long_rows,
+              long_cutoff=args.long_cutoff,
               mode=swdb.SW_MODE_BATCHED if args.mode == "batched" else swdb.SW_MODE_PLAIN)
 
     def step(stats=True):

@@ -175,6 +175,24 @@ void choose_shape(int64_t m, int *lanes, int *rows) {
     }
 }
 
+// Batched-kernel shapes (lanes, rows) with measured rates (GCUPS, GB300);
+// each query pair takes the one with the least predicted time.
+constexpr ShapeRate kBatchShapes[] = {{8, 16, 5000.0}, {8, 24, 5850.0}, {8, 32, 5850.0}};
+
+int choose_batch_shape(int64_t m) {
+    double best = 1e300;
+    int arg = 0;
+    for (int i = 0; i < int(sizeof(kBatchShapes) / sizeof(kBatchShapes[0])); ++i) {
+        const int64_t tr = int64_t(kBatchShapes[i].lanes) * kBatchShapes[i].rows;
+        const double t = double((m + tr - 1) / tr * tr) / kBatchShapes[i].gcups;
+        if (t < best) {
+            best = t;
+            arg = i;
+        }
+    }
+    return arg;
+}
+
 struct Plan {
     int precision = SW_PREC_I16;
     int mode = SW_MODE_PLAIN;
@@ -191,6 +209,12 @@ struct Plan {
     bool need_long_boundary = false;
     // batched mode: query pairs (a = longer, b = next, -1 if none), persistent grid
     std::vector<int32_t> qp_a, qp_b;
+    struct BatchGroup {
+        int lanes, rows;          // launch shape of this group
+        int32_t begin, count;     // range in qp_a / qp_b
+        int32_t grid;             // persistent CTAs
+    };
+    std::vector<BatchGroup> groups;   // one persistent launch per group
     int32_t batch_grid = 0;
     int64_t batch_seq_begin = 0;
     int32_t batch_max_cols = 0;
@@ -248,13 +272,18 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
     int lanes = opts && opts->lanes ? opts->lanes : 8;
     int rows = opts && opts->rows_per_lane ? opts->rows_per_lane : 16;
     if (p.mode == SW_MODE_BATCHED) {
-        if (!(opts && (opts->lanes || opts->rows_per_lane))) rows = 32;
-        if (!batch_config_supported(lanes, rows))
-            return fail(SW_ERR_UNSUPPORTED, "lanes/rows_per_lane combination not built for the batched kernel");
-        p.auto_shape = false;
-        p.lanes = lanes;
-        p.rows = rows;
-        p.min_tr = lanes * rows;
+        p.auto_shape = !(opts && (opts->lanes || opts->rows_per_lane));
+        if (!p.auto_shape) {
+            if (!batch_config_supported(lanes, rows))
+                return fail(SW_ERR_UNSUPPORTED, "lanes/rows_per_lane combination not built for the batched kernel");
+            p.lanes = lanes;
+            p.rows = rows;
+            p.min_tr = lanes * rows;
+        } else {
+            p.lanes = 8;
+            p.rows = 32;
+            p.min_tr = 128;
+        }
     } else if (p.precision == SW_PREC_I16) {
         p.auto_shape = !(opts && (opts->lanes || opts->rows_per_lane));
         if (!p.auto_shape) {
@@ -312,18 +341,46 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
         std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) {
             return q_offsets[x + 1] - q_offsets[x] > q_offsets[y + 1] - q_offsets[y];
         });
+        std::vector<int32_t> pa, pb;
         for (size_t i = 0; i < idx.size(); i += 2) {
-            p.qp_a.push_back(idx[i]);
-            p.qp_b.push_back(i + 1 < idx.size() ? idx[i + 1] : -1);
+            pa.push_back(idx[i]);
+            pb.push_back(i + 1 < idx.size() ? idx[i + 1] : -1);
         }
+        // Group the pairs by launch shape (each group keeps longest-first order).
+        const int n_shapes = p.auto_shape ? int(sizeof(kBatchShapes) / sizeof(kBatchShapes[0])) : 1;
         p.batch_max_m = idx.empty() ? 0 : int32_t(q_offsets[idx[0] + 1] - q_offsets[idx[0]]);
-        p.batch_grid = batch_slots(p.lanes, p.rows, std::max(1, db->sm_count));
-        if (p.batch_grid <= 0) return fail(SW_ERR_CUDA, "could not size the persistent grid");
+        p.batch_scratch = p.batch_max_m > 128;   // any multi-pass pair, in any shape
+        for (int sh = 0; sh < n_shapes; ++sh) {
+            const int gl = p.auto_shape ? kBatchShapes[sh].lanes : p.lanes;
+            const int gr = p.auto_shape ? kBatchShapes[sh].rows : p.rows;
+            Plan::BatchGroup g{gl, gr, int32_t(p.qp_a.size()), 0, 0};
+            int64_t gmax = 0;
+            for (size_t i = 0; i < pa.size(); ++i) {
+                const int64_t m = q_offsets[pa[i] + 1] - q_offsets[pa[i]];
+                if (p.auto_shape && choose_batch_shape(m) != sh) continue;
+                p.qp_a.push_back(pa[i]);
+                p.qp_b.push_back(pb[i]);
+                gmax = std::max(gmax, m);
+            }
+            g.count = int32_t(p.qp_a.size()) - g.begin;
+            if (g.count == 0) continue;
+            g.grid = batch_slots(gl, gr, std::max(1, db->sm_count));
+            if (g.grid <= 0) return fail(SW_ERR_CUDA, "could not size the persistent grid");
+            p.batch_grid = std::max(p.batch_grid, g.grid);
+            if (gmax > int64_t(gl) * gr) p.batch_scratch = true;
+            p.groups.push_back(g);
+            (void)gmax;
+        }
+        // Size the per-slot scratch for the widest grid any shape could use, so a
+        // workspace sized for one batch fits every batch of the same length bound.
+        if (p.auto_shape)
+            for (const ShapeRate &c : kBatchShapes)
+                p.batch_grid = std::max(p.batch_grid, batch_slots(c.lanes, c.rows, std::max(1, db->sm_count)));
         p.batch_seq_begin = p.long_end_pair * 2;
         p.batch_max_cols = p.batch_seq_begin < db->n_sorted
                                ? int32_t(round_up(db->h_len[size_t(p.batch_seq_begin)], 4))
                                : 0;
-        p.batch_scratch = p.batch_max_m > p.lanes * p.rows && p.batch_max_cols > 0;
+        if (p.batch_max_cols == 0) p.batch_scratch = false;
     }
     *plan = p;
     return SW_OK;
@@ -363,12 +420,12 @@ size_t carve(const sw_db *db, const Plan &p, int32_t n_q, int32_t top_k, bool q_
                                                size_t(std::max<int64_t>(db->n_sorted / 2, 1))));
     if (p.mode == SW_MODE_BATCHED) {
         x.qp = static_cast<int32_t *>(c.take(sizeof(int32_t) * 2 * std::max<size_t>(p.qp_a.size(), 1)));
-        if (p.batch_scratch)
+        if (p.batch_scratch)   // sized for the widest group (all shapes have at most 32 subwarps per CTA)
             x.batch_scratch = static_cast<uint2 *>(c.take(sizeof(uint2) * size_t(p.batch_grid) *
-                                                          size_t(kCtaThreads / p.lanes) * size_t(p.batch_max_cols)));
+                                                          size_t(kCtaThreads / 8) * size_t(p.batch_max_cols)));
     }
-    // [n_q] list lengths, [n_q] work counters, [n_q] flagged, status, tile counter
-    x.counters = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(3 * std::max<int32_t>(n_q, 1) + 2)));
+    // [n_q] list lengths, [n_q] work counters, [n_q] flagged, status, 4 tile counters
+    x.counters = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(3 * std::max<int32_t>(n_q, 1) + 5)));
     *b = x;
     return c.used + 256;
 }
@@ -712,7 +769,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
     // All device work of the search, in stream order.  Run directly, or
     // captured once into a CUDA graph and replayed (SW_FLAG_GRAPH).
     auto enqueue = [&]() -> int {
-    SW_CUDA_TRY(cudaMemsetAsync(buf.counters, 0, sizeof(int32_t) * (3 * size_t(std::max<int32_t>(n_q, 1)) + 2), st));
+    SW_CUDA_TRY(cudaMemsetAsync(buf.counters, 0, sizeof(int32_t) * (3 * size_t(std::max<int32_t>(n_q, 1)) + 5), st));
 
     // (1) Long sequences of every query: one intra-task launch on the side
     //     stream, concurrent with the per-query launches below.
@@ -750,17 +807,18 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
             if (q_offsets[qi + 1] == q_offsets[qi])
                 SW_CUDA_TRY(cudaMemsetAsync(d_scores + size_t(qi) * size_t(db->n_seqs), 0,
                                             sizeof(int32_t) * size_t(db->n_seqs), st));
-        const int spc = kCtaThreads / plan.lanes;
-        if (n_qp > 0 && plan.batch_seq_begin < db->n_sorted) {
+        for (size_t gi = 0; gi < plan.groups.size() && plan.batch_seq_begin < db->n_sorted; ++gi) {
+            const Plan::BatchGroup &g = plan.groups[gi];
+            const int spc = kCtaThreads / g.lanes;
             BatchArgs ba;
             memset(&ba, 0, sizeof ba);
             ba.db = db->view();
             ba.seq_begin = plan.batch_seq_begin;
             ba.seq_end = db->n_sorted;
             ba.n_chunks = int32_t((db->n_sorted - plan.batch_seq_begin + spc - 1) / spc);
-            ba.n_qp = n_qp;
-            ba.qp_a = buf.qp;
-            ba.qp_b = buf.qp + n_qp;
+            ba.n_qp = g.count;
+            ba.qp_a = buf.qp + g.begin;
+            ba.qp_b = buf.qp + n_qp + g.begin;
             ba.q_off = buf.q_off;
             ba.queries = d_queries;
             ba.gap_open = gap_open;
@@ -775,8 +833,10 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
             ba.list_stride = list_stride;
             ba.ovf_count = buf.counters;
             ba.ovf_seqs = buf.counters + 2 * n_q;
-            ba.tile_counter = d_tiles;
-            TIMED(LaunchTimer::INTER, launch_batch_i16x2(ba, plan.lanes, plan.rows, plan.batch_grid, st));
+            ba.tile_counter = d_tiles + (gi & 3);
+            last_lanes = g.lanes;
+            last_rows = g.rows;
+            TIMED(LaunchTimer::INTER, launch_batch_i16x2(ba, g.lanes, g.rows, g.grid, st));
         }
     }
 

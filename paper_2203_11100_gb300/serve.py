@@ -186,7 +186,16 @@ class SearchServer:
                         self.cv.wait(timeout=0.05)
                         batch, nbytes = self._take_batch()
                     self.in_flight_bytes += nbytes
-                self._launch(worker, batch, nbytes)
+                try:
+                    self._launch(worker, batch, nbytes)
+                except Exception as e:   # this batch fails; the server keeps serving
+                    for r in batch:
+                        if not r.future.done():
+                            r.future.set_exception(e)
+                    with self.cv:
+                        self.in_flight_bytes -= nbytes
+                        self.cv.notify_all()
+                    self.free_workers.put(worker)
         except Exception as e:  # surface errors to close()
             self.error = e
             with self.cv:

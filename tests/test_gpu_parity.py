@@ -345,3 +345,23 @@ def test_autotune_picks_and_caches(gpu, tmp_path):
         assert again == params
         scores, _, _ = d.search(qs.residues, qs.offsets, S, 10, 1, top_k=0, **params)
     np.testing.assert_array_equal(scores, oracle.all_scores(qs, db, S, 10, 1))
+
+
+@pytest.mark.parametrize("mode", ["plain", "batched"])
+def test_workspace_bound_covers_mixed_batches(gpu, mode):
+    """A workspace sized for n queries of the maximum length fits every batch
+    of at most n queries no longer than that (how the server sizes its own)."""
+    import torch
+    m = gpu.SW_MODE_PLAIN if mode == "plain" else gpu.SW_MODE_BATCHED
+    rng = np.random.default_rng(80)
+    db = synth.seqset_from_lengths(rng, np.concatenate([rng.integers(1, 900, 400), [3500, 4100]]))
+    S = synth.blosum62()
+    n, maxlen = 8, 3000
+    with gpu.Database(db.residues, db.offsets, 24) as d:
+        bound = gpu.sw_search_workspace_size(d.handle, np.arange(n + 1, dtype=np.int64) * maxlen, 10, mode=m)
+        ws = torch.empty(bound, dtype=torch.uint8, device="cuda")
+        for lens in ([3000, 40, 100, 129, 250, 700, 2999, 1], [5, 6], [3000] * 8, [64] * 7):
+            qs = synth.seqset_from_lengths(rng, lens)
+            scores = np.empty((qs.n, db.n), np.int32)
+            gpu.sw_search(d.handle, qs.residues, qs.offsets, S, 10, 1, 0, scores_out=scores, workspace=ws, mode=m)
+            np.testing.assert_array_equal(scores, oracle.all_scores(qs, db, S, 10, 1))

@@ -91,3 +91,48 @@ def test_failure_reaches_every_future():
         assert r.future.done()
     t.join(timeout=5)
     assert s.error is not None
+
+
+def test_failed_launch_resolves_its_requests():
+    """A batch whose launch raises gets the exception on its own futures and
+    the server goes on with the next batch."""
+    s = _server_shell()
+    s.max_batch = 4
+    s.mem_budget = 1 << 40
+    s.closed = False
+    s.error = None
+    calls = []
+
+    def launch(worker, batch, nbytes):
+        calls.append(len(batch))
+        if len(calls) == 1:
+            raise RuntimeError("workspace too small")
+        for r in batch:
+            r.future.set_result("ok")
+        with s.cv:
+            s.in_flight_bytes -= nbytes
+        s.free_workers.put(worker)
+
+    s._launch = launch
+    s.free_workers.put(0)
+    reqs = [serve._Request(np.zeros(5, np.uint8), Future(), 0.0, 10) for _ in range(6)]
+    s.pending.extend(reqs[:4])
+    t = threading.Thread(target=s._dispatch)
+    s.torch = type("T", (), {"cuda": type("C", (), {"set_device": staticmethod(lambda d: None)})})
+    s.device = None
+    t.start()
+    for r in reqs[:4]:
+        try:
+            r.future.result(timeout=5)
+        except RuntimeError:
+            pass
+    assert all(isinstance(r.future.exception(timeout=1), RuntimeError) for r in reqs[:4])
+    with s.cv:
+        s.pending.extend(reqs[4:])
+        s.cv.notify_all()
+    assert [r.future.result(timeout=5) for r in reqs[4:]] == ["ok", "ok"]
+    with s.cv:
+        s.closed = True
+        s.cv.notify_all()
+    t.join(timeout=5)
+    assert not t.is_alive()
