@@ -222,8 +222,13 @@ struct Plan {
     bool batch_scratch = false;
     int32_t max_m = 0;
     int64_t total_m = 0;
-    bool need_boundary = false;
+    bool need_boundary = false;      // per-pair boundary (int32 rescore)
     int32_t sat_limit = 0;
+    // plain form: persistent inter-task grid with per-slot boundary scratch
+    int32_t inter_grid_max = 0;      // largest resident grid among the shapes used
+    int32_t inter_min_lanes = 8;     // sets the most pairs per CTA
+    int32_t inter_max_cols = 0;      // columns of the longest non-long pair
+    bool inter_scratch = false;
 };
 
 // Choose arithmetic and launch shapes for this call.
@@ -332,6 +337,27 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
     }
     p.need_boundary = p.max_m > std::min(p.min_tr, p.lanes32 * p.rows32);
 
+    if (p.mode == SW_MODE_PLAIN && p.precision == SW_PREC_I16 && n_q > 0) {
+        // Sized over every shape this call may launch (all of the table when the
+        // shape is chosen per query), so that a workspace sized for queries of
+        // the maximum length also fits any batch of shorter ones.
+        const int sms = std::max(1, db->sm_count);
+        const int n_shapes = p.auto_shape ? int(sizeof(kShapes) / sizeof(kShapes[0])) : 1;
+        int min_tr = 1 << 30;
+        p.inter_min_lanes = 32;
+        for (int sh = 0; sh < n_shapes; ++sh) {
+            const int l = p.auto_shape ? kShapes[sh].lanes : p.lanes;
+            const int r = p.auto_shape ? kShapes[sh].rows : p.rows;
+            p.inter_min_lanes = std::min(p.inter_min_lanes, l);
+            p.inter_grid_max = std::max(p.inter_grid_max, inter_slots(l, r, sms));
+            min_tr = std::min(min_tr, l * r);
+        }
+        p.inter_scratch = p.max_m > min_tr;
+        const int64_t first = p.long_end_pair * 2;
+        p.inter_max_cols = first < db->n_sorted ? int32_t(round_up(db->h_len[size_t(first)], 4)) : 0;
+        if (p.inter_max_cols == 0) p.inter_scratch = false;
+        if (p.inter_grid_max <= 0) return fail(SW_ERR_CUDA, "could not size the persistent grid");
+    }
     if (p.mode == SW_MODE_BATCHED) {
         // Pair queries of similar length: sort the non-empty ones longest first
         // and pair neighbours, so the shorter of a pair pads few rows.
@@ -396,6 +422,7 @@ struct Buffers {
     int32_t *prof32 = nullptr;
     int32_t *qp = nullptr;            // batched mode: qp_a then qp_b
     uint2 *batch_scratch = nullptr;   // batched mode: per CTA slot boundary rows
+    uint2 *inter_scratch = nullptr;   // plain mode: per CTA slot boundary rows
     int32_t *ovf_list = nullptr;
     int32_t *counters = nullptr;   // [n_q] list lengths, [n_q] work counters, [n_q] flagged sequences,
                                    // then one status word
@@ -424,8 +451,13 @@ size_t carve(const sw_db *db, const Plan &p, int32_t n_q, int32_t top_k, bool q_
             x.batch_scratch = static_cast<uint2 *>(c.take(sizeof(uint2) * size_t(p.batch_grid) *
                                                           size_t(kCtaThreads / 8) * size_t(p.batch_max_cols)));
     }
-    // [n_q] list lengths, [n_q] work counters, [n_q] flagged, status, 4 tile counters
-    x.counters = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(3 * std::max<int32_t>(n_q, 1) + 5)));
+    if (p.inter_scratch)
+        x.inter_scratch = static_cast<uint2 *>(c.take(sizeof(uint2) * size_t(p.inter_grid_max) *
+                                                      size_t(kCtaThreads / p.inter_min_lanes) *
+                                                      size_t(p.inter_max_cols)));
+    // [n_q] list lengths, [n_q] work counters, [n_q] flagged, [n_q] chunk counters,
+    // status, 4 tile counters
+    x.counters = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(4 * std::max<int32_t>(n_q, 1) + 5)));
     *b = x;
     return c.used + 256;
 }
@@ -722,7 +754,8 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
     sw_hit *d_hits = h_dev ? hits_out : buf.hits;
     if (!q_dev && plan.total_m > 0)
         SW_CUDA_TRY(cudaMemcpyAsync(buf.queries, queries, size_t(plan.total_m), cudaMemcpyHostToDevice, st));
-    int32_t *d_status = buf.counters + 3 * size_t(std::max<int32_t>(n_q, 1));
+    int32_t *d_chunks = buf.counters + 3 * size_t(std::max<int32_t>(n_q, 1));
+    int32_t *d_status = buf.counters + 4 * size_t(std::max<int32_t>(n_q, 1));
     int32_t *d_tiles = d_status + 1;
 
     // int8 profile table for the int16x2 kernel: [query code][db code] = S + o.
@@ -769,7 +802,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
     // All device work of the search, in stream order.  Run directly, or
     // captured once into a CUDA graph and replayed (SW_FLAG_GRAPH).
     auto enqueue = [&]() -> int {
-    SW_CUDA_TRY(cudaMemsetAsync(buf.counters, 0, sizeof(int32_t) * (3 * size_t(std::max<int32_t>(n_q, 1)) + 5), st));
+    SW_CUDA_TRY(cudaMemsetAsync(buf.counters, 0, sizeof(int32_t) * (4 * size_t(std::max<int32_t>(n_q, 1)) + 5), st));
 
     // (1) Long sequences of every query: one intra-task launch on the side
     //     stream, concurrent with the per-query launches below.
@@ -862,7 +895,13 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
             if (plan.auto_shape) choose_shape(m, &lanes, &rows);
             last_lanes = lanes;
             last_rows = rows;
-            TIMED(LaunchTimer::INTER, launch_inter_i16x2(ia, lanes, rows, st));
+            // persistent grid, per-slot boundary scratch (stays in L2)
+            ia.boundary = buf.inter_scratch;
+            ia.max_cols = plan.inter_max_cols;
+            ia.slot_stride = int64_t(kCtaThreads / lanes) * plan.inter_max_cols;
+            ia.chunk_counter = d_chunks + qi;
+            const int slots = inter_slots(lanes, rows, std::max(1, db->sm_count));
+            TIMED(LaunchTimer::INTER, launch_inter_i16x2(ia, lanes, rows, st, slots));
         } else {
             const int tr32 = plan.lanes32 * plan.rows32;
             const int32_t m_pad = int32_t(round_up(m, tr32));

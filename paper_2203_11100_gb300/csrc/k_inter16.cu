@@ -33,11 +33,16 @@
 //                F_below = max(F - e, Ho)            (viaddmax)
 //   which is the recurrence H = max(0, Hdiag + S, E, F) with Hdiag + S =
 //   Ho_diag + (S + o).  The running maximum takes two rows per vimax3.
+// * The grid is either one CTA per chunk of 256/T pairs, or persistent: the
+//   resident CTAs pull chunks (longest first) from an atomic counter and each
+//   keeps its strip-boundary rows in its own scratch slot, reused chunk after
+//   chunk, so those rows stay in L2 instead of being written back to HBM.
 // * Saturation: every value stays below the running maximum of H plus the
 //   largest matrix entry, so if that maximum stays below
 //   32767 - max(S) no int16 operation overflowed and the score is exact.
 //   Sequences at or above that limit are appended to a list and rescored
 //   in int32 by another kernel.
+#include <algorithm>
 #include <type_traits>
 
 #include "swdb_internal.cuh"
@@ -72,7 +77,10 @@ __device__ __forceinline__ uint32_t pack2(int v) {
     return h | (h << 16);
 }
 
-template <int T, int R>
+// SLOTS = true: persistent grid, chunks pulled from *a.chunk_counter, strip
+// boundary in per-slot scratch.  SLOTS = false: one CTA per chunk, per-pair
+// boundary in the database layout's shape.
+template <int T, int R, bool SLOTS>
 __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_inter_i16x2(const __grid_constant__ InterArgs a) {
     static_assert(R % 16 == 0, "rows per lane must be a multiple of 16");
     static_assert(32 % T == 0 && T >= 4, "lanes must divide the warp");
@@ -86,21 +94,35 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_inter_i16x2(
     // (B(Ho), B(F) per column), filled by lane 0 with cp.async one group ahead.
     __shared__ __align__(16) uint2 bstage[PAIRS_PER_CTA][8];
 
+    __shared__ int sh_chunk;
+
     const int tid = threadIdx.x;
     const int k = tid % T;               // lane within the subwarp
     const int sub = tid / T;             // subwarp within the CTA
-    const int64_t pair = a.pair_begin + int64_t(blockIdx.x) * PAIRS_PER_CTA + sub;
-    const bool valid = pair < a.pair_end;
-
     for (int i = tid; i < kProfRows * kProfRows; i += kCtaThreads) mat[i] = (&a.prof8[0][0])[i];
+    const int n_chunks = int((a.pair_end - a.pair_begin + PAIRS_PER_CTA - 1) / PAIRS_PER_CTA);
+
+  for (;;) {
+    int chunk = int(blockIdx.x);
+    if (SLOTS) {
+        __syncthreads();                 // the previous chunk is done with shared state
+        if (tid == 0) sh_chunk = atomicAdd(a.chunk_counter, 1);
+        __syncthreads();
+        chunk = sh_chunk;
+    }
+    if (chunk >= n_chunks) break;
+    // The pair index is not kept across the passes (registers are tight at
+    // R = 32); the epilogue derives it again from the chunk.
+    const int64_t pair0 = a.pair_begin + int64_t(chunk) * PAIRS_PER_CTA + sub;
+    const bool valid = pair0 < a.pair_end;
 
     int64_t b = 0;
     int slot = 0;
     int Lp = 0;
     if (valid) {
-        b = pair / kBundlePairs;
-        slot = int(pair % kBundlePairs);
-        Lp = (a.db.len[2 * pair] + 3) & ~3;   // longest of the pair (sorted, longest first)
+        b = pair0 / kBundlePairs;
+        slot = int(pair0 % kBundlePairs);
+        Lp = (a.db.len[2 * pair0] + 3) & ~3;   // longest of the pair (sorted, longest first)
     }
     const int Lw = __reduce_max_sync(0xffffffffu, Lp);   // warp-uniform column count
 
@@ -111,15 +133,23 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_inter_i16x2(
     const uint32_t OO = uint32_t(o) | (uint32_t(o) << 16);
     const uint32_t BZERO2 = 0x80008000u;              // B(0)
 
-    // Boundary scratch of this bundle: 8*Lb uint2 entries starting at
-    // uint2 index off/2, grouped as [column/4][slot][column%4] so lane 0 of a
-    // pair reads 4 columns with two 16-byte loads.
+    // Boundary scratch of this pair, grouped by 4 columns so lane 0 reads a
+    // group with two 16-byte loads: either the bundle's region (8*Lb uint2
+    // entries at uint2 index off/2, [column/4][slot][column%4]) or this CTA
+    // slot's region (max_cols entries per subwarp, [column]).
     const uint2 *cptr = nullptr;
     uint4 *bnd = nullptr;
+    constexpr int gstride = SLOTS ? 2 : kBundlePairs * 2;   // uint4 per 4-column group
     if (valid) {
         const int64_t off = a.db.bundle_off[b];
         cptr = reinterpret_cast<const uint2 *>(a.db.codes + off) + slot;
-        bnd = reinterpret_cast<uint4 *>(a.boundary + off / 2) + slot * 2;
+        if (a.boundary) {
+            if (SLOTS)
+                bnd = reinterpret_cast<uint4 *>(a.boundary + int64_t(blockIdx.x) * a.slot_stride +
+                                                int64_t(sub) * a.max_cols);
+            else
+                bnd = reinterpret_cast<uint4 *>(a.boundary + off / 2) + slot * 2;
+        }
     }
 
     const int npass = (a.m + TR - 1) / TR;
@@ -177,8 +207,8 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_inter_i16x2(
                 cp_async16(stg + 2, bnd + 1);
                 cp_async_commit();
                 if (4 < Lp) {
-                    cp_async16(stg + 4, bnd + kBundlePairs * 2);
-                    cp_async16(stg + 6, bnd + kBundlePairs * 2 + 1);
+                    cp_async16(stg + 4, bnd + gstride);
+                    cp_async16(stg + 6, bnd + gstride + 1);
                 }
                 cp_async_commit();
             }
@@ -213,7 +243,7 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_inter_i16x2(
                     fin = bv.y;
                     if (s3 == 3) {        // buffer of group s/4 is free: fetch group s/4 + 2 into it
                         if (s + 5 < Lp) {
-                            const uint4 *g = bnd + size_t((s >> 2) + 2) * (kBundlePairs * 2);
+                            const uint4 *g = bnd + size_t((s >> 2) + 2) * gstride;
                             cp_async16(stg + ((s >> 2) & 1) * 4, g);
                             cp_async16(stg + ((s >> 2) & 1) * 4 + 2, g + 1);
                         }
@@ -256,7 +286,7 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_inter_i16x2(
                 pub_c = cin;
                 if (k == T - 1 && !last_pass) {   // 4 consecutive columns fill one 32-byte sector
                     const int jl = s - (T - 1);
-                    reinterpret_cast<uint2 *>(bnd)[size_t(jl >> 2) * (kBundlePairs * 4) + (jl & 3)] =
+                    reinterpret_cast<uint2 *>(bnd)[size_t(jl >> 2) * (gstride * 2) + (jl & 3)] =
                         make_uint2(Ho[R - 1], f);
                 }
             }
@@ -283,7 +313,9 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_inter_i16x2(
         const uint32_t other = __shfl_xor_sync(0xffffffffu, mx, dd, T);
         mx = __vimax3_u16x2(mx, other, other);
     }
-    if (valid && k == 0) {
+    const int chunk_end = SLOTS ? *reinterpret_cast<volatile int *>(&sh_chunk) : int(blockIdx.x);
+    const int64_t pair = a.pair_begin + int64_t(chunk_end) * PAIRS_PER_CTA + sub;
+    if (pair < a.pair_end && k == 0) {
         const int hA = int(mx & 0xffffu) - 32768;
         const int hB = int(mx >> 16) - 32768;
         const int64_t tA = 2 * pair;
@@ -304,16 +336,32 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_inter_i16x2(
             atomicAdd(a.ovf_seqs, __popc(mask));
         }
     }
+    if (!SLOTS) break;
+  }
 }
 
 template <int T, int R>
-cudaError_t launch_tr(const InterArgs &a, cudaStream_t s) {
+cudaError_t launch_tr(const InterArgs &a, cudaStream_t s, int grid_slots) {
     constexpr int PAIRS_PER_CTA = kCtaThreads / T;
     const int64_t pairs = a.pair_end - a.pair_begin;
     if (pairs <= 0) return cudaSuccess;
-    const int64_t grid = (pairs + PAIRS_PER_CTA - 1) / PAIRS_PER_CTA;
-    k_inter_i16x2<T, R><<<unsigned(grid), kCtaThreads, 0, s>>>(a);
+    const int64_t chunks = (pairs + PAIRS_PER_CTA - 1) / PAIRS_PER_CTA;
+    if (grid_slots > 0) {
+        if (!a.chunk_counter) return cudaErrorInvalidValue;
+        k_inter_i16x2<T, R, true><<<unsigned(std::min<int64_t>(grid_slots, chunks)), kCtaThreads, 0, s>>>(a);
+    } else {
+        k_inter_i16x2<T, R, false><<<unsigned(chunks), kCtaThreads, 0, s>>>(a);
+    }
     return cudaGetLastError();
+}
+
+template <int T, int R>
+int slots_tr(int sms) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inter_i16x2<T, R, true>, kCtaThreads, 0) !=
+        cudaSuccess)
+        return 0;
+    return per_sm * sms;
 }
 
 }  // namespace
@@ -325,16 +373,29 @@ bool inter_config_supported(int lanes, int rows) {
     }
 }
 
-cudaError_t launch_inter_i16x2(const InterArgs &a, int lanes, int rows, cudaStream_t s) {
+cudaError_t launch_inter_i16x2(const InterArgs &a, int lanes, int rows, cudaStream_t s, int grid_slots) {
     switch (lanes * 100 + rows) {
-        case 416: return launch_tr<4, 16>(a, s);
-        case 816: return launch_tr<8, 16>(a, s);
-        case 1616: return launch_tr<16, 16>(a, s);
-        case 3216: return launch_tr<32, 16>(a, s);
-        case 832: return launch_tr<8, 32>(a, s);
-        case 1632: return launch_tr<16, 32>(a, s);
-        case 3232: return launch_tr<32, 32>(a, s);
+        case 416: return launch_tr<4, 16>(a, s, grid_slots);
+        case 816: return launch_tr<8, 16>(a, s, grid_slots);
+        case 1616: return launch_tr<16, 16>(a, s, grid_slots);
+        case 3216: return launch_tr<32, 16>(a, s, grid_slots);
+        case 832: return launch_tr<8, 32>(a, s, grid_slots);
+        case 1632: return launch_tr<16, 32>(a, s, grid_slots);
+        case 3232: return launch_tr<32, 32>(a, s, grid_slots);
         default: return cudaErrorInvalidValue;
+    }
+}
+
+int inter_slots(int lanes, int rows, int sms) {
+    switch (lanes * 100 + rows) {
+        case 416: return slots_tr<4, 16>(sms);
+        case 816: return slots_tr<8, 16>(sms);
+        case 1616: return slots_tr<16, 16>(sms);
+        case 3216: return slots_tr<32, 16>(sms);
+        case 832: return slots_tr<8, 32>(sms);
+        case 1632: return slots_tr<16, 32>(sms);
+        case 3232: return slots_tr<32, 32>(sms);
+        default: return 0;
     }
 }
 

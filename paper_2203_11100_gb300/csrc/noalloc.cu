@@ -166,7 +166,9 @@ extern "C" int sw_search_no_alloc(const sw_db *db, const uint8_t *query, int32_t
         ia.gap_open = gap_open;
         ia.gap_extend = gap_extend;
         ia.sat_limit = 32767 - (smax > 0 ? smax : 0);
-        ia.boundary = boundary;
+        ia.boundary = boundary;        // per-pair layout, one CTA per chunk
+        ia.slot_stride = 0;
+        ia.chunk_counter = nullptr;
         ia.scores = scores;
         ia.ovf_list = list;
         ia.ovf_count = counters;

@@ -49,7 +49,16 @@ struct InterArgs {
     int32_t gap_open, gap_extend;
     int32_t sat_limit;          // flag a sequence when its int16 maximum H >= sat_limit
     int8_t prof8[kProfRows][kProfRows];  // [query code][db code] = S + o, pads = -128
-    uint2 *boundary;            // scratch, 4 bytes per database layout byte
+    // Strip-boundary scratch for multi-pass queries, one of two layouts:
+    //  slot_stride == 0: per database pair, 4 bytes per layout byte (grid: one
+    //                    CTA per chunk of pairs);
+    //  slot_stride  > 0: per resident CTA slot, slot_stride uint2 entries each,
+    //                    max_cols per subwarp (persistent grid pulling chunks
+    //                    from *chunk_counter; the scratch is reused and stays in L2).
+    uint2 *boundary;
+    int64_t slot_stride;
+    int32_t max_cols;
+    int32_t *chunk_counter;     // persistent grid only; zeroed before launch
     int32_t *scores;            // row of this query, original database order
     int32_t *ovf_list;          // entries pair*4 + mask of saturated halves
     int32_t *ovf_count;
@@ -122,8 +131,11 @@ struct I32Args {
 };
 
 // Launchers (return cudaGetLastError() after the launch).
-cudaError_t launch_inter_i16x2(const InterArgs &a, int lanes, int rows, cudaStream_t s);
+// grid_slots > 0 launches a persistent grid of that many CTAs (slot-layout
+// scratch); 0 launches one CTA per chunk of pairs (per-pair scratch).
+cudaError_t launch_inter_i16x2(const InterArgs &a, int lanes, int rows, cudaStream_t s, int grid_slots = 0);
 bool inter_config_supported(int lanes, int rows);
+int inter_slots(int lanes, int rows, int sms);   // resident CTAs of a persistent grid
 cudaError_t launch_intra_i16x2(const IntraArgs &a, int warps, int rows, cudaStream_t s);
 int intra_rows_per_superpass(int warps, int rows);
 cudaError_t prepare_intra_i16x2(int warps, int rows);   // kernel attributes; call before any capture

@@ -48,6 +48,18 @@ def test_int16x2_blosum62_shapes(gpu, lanes, rows):
     assert st["cells"] == int(qs.lengths.sum()) * int(db.lengths.sum())
 
 
+@pytest.mark.parametrize("lanes,rows", [(4, 16), (8, 16), (32, 32)])
+def test_int16x2_persistent_slots_reused(gpu, lanes, rows):
+    """Far more sequence chunks than resident blocks: each block slot takes many
+    chunks in turn and reuses its strip-boundary scratch for every pass of every
+    chunk (multi-pass queries, ragged last chunk, short and empty sequences)."""
+    rng = np.random.default_rng(900 + lanes * 100 + rows)
+    db = _db(rng, 120001, 0, 30)
+    qs = synth.seqset_from_lengths(rng, [129, 300, 1100])
+    _check(gpu, qs, db, synth.blosum62(), 10, 1, precision=gpu.SW_PREC_I16, mode=gpu.SW_MODE_PLAIN,
+           lanes=lanes, rows_per_lane=rows)
+
+
 @pytest.mark.parametrize("lanes,rows", I32_SHAPES)
 def test_int32_blosum62_shapes(gpu, lanes, rows):
     rng = np.random.default_rng(7 + lanes * 100 + rows)
