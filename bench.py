@@ -22,6 +22,7 @@ the data path ("weak" scaling); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import glob
 import hashlib
 import json
 import os
@@ -198,20 +199,30 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------
 
-def traffic_per_launch(cells_per_launch: float):
-    """DRAM bytes per inter-task launch from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_inter_i16x2_swissprot_like_0.7db.md")
+def launch_key(args) -> str:
+    """The launch configuration a DRAM-traffic record was measured under."""
+    return (f"{args.workload}/scale{args.db_scale:g}/{args.mode}/lanes{args.lanes}/rows{args.rows}"
+            f"/prec{args.precision}/longrows{args.long_rows}/cutoff{args.long_cutoff}")
+
+
+def traffic_per_launch(args):
+    """Average DRAM bytes (read + written) per inter-task launch, from the
+    committed ncu record of every launch of one step of this same launch
+    configuration, if it was taken on the current kernel source (else None)."""
     src = os.path.join(ROOT, "paper_2203_11100_gb300", "csrc", "k_inter16.cu")
     try:
-        line = next(l for l in open(path) if l.startswith("traffic:"))
-        rec = dict(kv.split("=", 1) for kv in line.split()[1:])
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if rec.get("source_sha256") != sha:
-            return None
-        return float(rec["dram_bytes_per_cell"]) * cells_per_launch
+        key = launch_key(args)
+        for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+            for line in open(path):
+                if not line.startswith("traffic:"):
+                    continue
+                rec = dict(kv.split("=", 1) for kv in line.split()[1:])
+                if rec.get("launch") == key and rec.get("source_sha256") == sha:
+                    return float(rec["dram_bytes_per_launch"])
     except Exception:
         return None
+    return None
 
 
 def cpu_baseline(w, gpu_scores, seed: int, target_cells: float):
@@ -318,8 +329,7 @@ def run_ours(args, dist: Dist):
         ceiling = rate_cells * sms * mhz * 1e6 / 1e9
         inter_cells = float(sum(s["inter_cells"] for s in st_all))
         achieved = inter_cells / (inter_ms * 1e-3) / 1e9 if inter_ms > 0 else 0.0
-        cells_per_launch = inter_cells / max(inter_launches, 1)
-        traffic = traffic_per_launch(cells_per_launch)
+        traffic = traffic_per_launch(args)
         cb = None
         if not args.no_cpu_baseline:
             cb = cpu_baseline(w, scores.cpu().numpy(), seed + 1, args.cpu_sample_cells)
