@@ -11,10 +11,15 @@ of the ``synth`` module.
 - ``top_k``: the k best database entries of a score row, ordered by score
   descending and then database index ascending (the paper is silent on ties;
   this order is the reading this build takes).
+- ``align`` / ``align_pairs``: one optimal local alignment per pair, read
+  off the same matrices by the traceback rules stated in ``traceback.c``
+  (end cell first in row-major order; diagonal before E before F; a gap
+  opens as soon as it can), plain C, int64.
 
-Parity of every function here is pinned by tests/test_oracle_pins.py
-(brute-force enumeration, textbook reductions, hand-worked examples,
-invariants).
+Parity of every function here is pinned by tests/test_oracle_pins.py and
+tests/test_oracle_align_pins.py (brute-force enumeration, textbook
+reductions, hand-worked examples, invariants, rescoring of the returned
+alignments).
 """
 from __future__ import annotations
 
@@ -26,7 +31,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "gotoh.c")
+_SRCS = [os.path.join(_HERE, "gotoh.c"), os.path.join(_HERE, "traceback.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libgotoh.so")
 _lock = threading.Lock()
@@ -34,12 +39,13 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile gotoh.c with gcc into oracle/_build/libgotoh.so."""
+    """Compile gotoh.c and traceback.c with gcc into oracle/_build/libgotoh.so."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(x) for x in _SRCS)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
-                               _SRC, "-o", tmp])
+                               *_SRCS, "-o", tmp])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -56,6 +62,8 @@ def _load():
             lib.swo_score_pairs.restype = ctypes.c_int
             lib.swo_score_pairs.argtypes = [p, p, p, p, p, p, i64, p, ctypes.c_int32, i64, i64,
                                             ctypes.c_int, p]
+            lib.swo_align.restype = i64
+            lib.swo_align.argtypes = [p, i64, p, i64, p, ctypes.c_int32, i64, i64, p, p, p]
             _lib = lib
     return _lib
 
@@ -144,3 +152,46 @@ def top_k(scores_row, k: int):
     s[:len(order)] = row[order]
     i[:len(order)] = order
     return s, i
+
+
+def align(q, t, S, gap_open: int, gap_extend: int) -> dict:
+    """One optimal local alignment of query q against target t (uint8 codes).
+
+    Returns {"score", "q_begin", "q_end", "t_begin", "t_end", "ops"}: the
+    alignment covers q[q_begin:q_end] and t[t_begin:t_end]; ops (uint8) run
+    from its start to its end, 0 = M, 1 = I (query residue opposite a gap),
+    2 = D (target residue opposite a gap).
+    """
+    lib = _load()
+    q = np.ascontiguousarray(q, dtype=np.uint8)
+    t = np.ascontiguousarray(t, dtype=np.uint8)
+    S = _matrix(S)
+    A = S.shape[0]
+    if len(q) and int(q.max()) >= A or len(t) and int(t.max()) >= A:
+        raise ValueError("residue code outside the matrix")
+    coords = np.zeros(4, dtype=np.int64)
+    ops = np.zeros(max(len(q) + len(t), 1), dtype=np.uint8)
+    n_ops = np.zeros(1, dtype=np.int64)
+    qq = q if len(q) else np.zeros(1, np.uint8)
+    tt = t if len(t) else np.zeros(1, np.uint8)
+    r = lib.swo_align(_ptr(qq), len(q), _ptr(tt), len(t), _ptr(S), A, int(gap_open), int(gap_extend),
+                      _ptr(coords), _ptr(ops), _ptr(n_ops))
+    if r < 0:
+        raise MemoryError("oracle scratch allocation failed")
+    return {"score": int(r), "q_begin": int(coords[0]), "q_end": int(coords[1]),
+            "t_begin": int(coords[2]), "t_end": int(coords[3]), "ops": ops[:int(n_ops[0])].copy()}
+
+
+def align_pairs(queries, db, q_idx, t_idx, S, gap_open: int, gap_extend: int,
+                threads: int | None = None) -> list:
+    """``align`` of the pairs (queries.seq(q_idx[k]), db.seq(t_idx[k])), spread
+    over threads (the C call releases the interpreter lock)."""
+    from concurrent.futures import ThreadPoolExecutor
+    q_idx = [int(x) for x in q_idx]
+    t_idx = [int(x) for x in t_idx]
+
+    def one(k):
+        return align(queries.seq(q_idx[k]), db.seq(t_idx[k]), S, gap_open, gap_extend)
+
+    with ThreadPoolExecutor(max_workers=threads or default_threads()) as ex:
+        return list(ex.map(one, range(len(q_idx))))

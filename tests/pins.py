@@ -12,6 +12,9 @@ must equal in a special case:
   (the score when mismatches and gaps are prohibitively expensive).
 - ``best_diagonal_kadane``: Kadane's maximum subarray along every diagonal
   (the score when gaps are prohibitively expensive).
+- ``enumerate_alignments``: every local alignment as an explicit list of
+  columns, each gap column marked as opening its gap or extending it (the
+  raw material of the traceback pins).
 """
 from __future__ import annotations
 
@@ -95,3 +98,56 @@ def best_diagonal_kadane(q, t, S) -> int:
                 run = max(0, run + int(S[q[i]][t[j]]))
                 best = max(best, run)
     return best
+
+
+def enumerate_alignments(q, t, S, gap_open: int, gap_extend: int):
+    """Every non-empty local alignment of every pair of substrings.
+
+    Yields (i0, j0, cols, score): the alignment starts after q[:i0] and
+    t[:j0]; cols is a tuple of (op, opens) with op "M", "I" (q residue
+    opposite a gap) or "D" (t residue opposite a gap), and opens True when a
+    gap column starts a new gap (priced open) rather than extending the gap
+    of the previous column (priced extend; only possible right after a gap
+    column of the same kind).  Both pricings of a continuing column are
+    enumerated, so the maximum over alignments is the recurrences' score
+    whether open >= extend or not.
+    """
+    q = [int(x) for x in q]
+    t = [int(x) for x in t]
+    m, n = len(q), len(t)
+    out = []
+
+    def dfs(i0, j0, i, j, cols, score):
+        if cols:
+            out.append((i0, j0, tuple(cols), score))
+        last = cols[-1][0] if cols else None
+        if i < m and j < n:
+            cols.append(("M", False))
+            dfs(i0, j0, i + 1, j + 1, cols, score + int(S[q[i]][t[j]]))
+            cols.pop()
+        for op, di, dj in (("I", 1, 0), ("D", 0, 1)):
+            if i + di > m or j + dj > n:
+                continue
+            cols.append((op, True))
+            dfs(i0, j0, i + di, j + dj, cols, score - gap_open)
+            cols.pop()
+            if last == op:
+                cols.append((op, False))
+                dfs(i0, j0, i + di, j + dj, cols, score - gap_extend)
+                cols.pop()
+
+    for i0 in range(m + 1):
+        for j0 in range(n + 1):
+            dfs(i0, j0, i0, j0, [], 0)
+    return out
+
+
+def alignment_end(i0, j0, cols):
+    """(i, j) after the last column of an alignment starting at (i0, j0)."""
+    i, j = i0, j0
+    for op, _ in cols:
+        if op in "MI":
+            i += 1
+        if op in "MD":
+            j += 1
+    return i, j
