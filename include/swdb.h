@@ -212,6 +212,78 @@ int sw_top_k(const int32_t *scores, int64_t n_rows, int64_t n_cols, int32_t top_
 int sw_probe_alu_rate(int device, int32_t mode, double *per_sm_cycle, int32_t *sm_count);
 
 /*
+ * Alignments (traceback) of chosen (query, database sequence) pairs, for
+ * instance the hits of sw_search.  Section 2.2 defines the optimal local
+ * alignment score by the Smith-Waterman recurrences (here in the affine-gap
+ * form of Gotoh with the penalties of Section 4.1, as in sw_search); an
+ * alignment reaching that score is read back from the same matrices.  SW#,
+ * the tool the paper measures (Section 2.3), reports such alignments; the
+ * paper itself times only the scores.  Several alignments can reach the
+ * optimum; sw_align returns the one fixed by these rules:
+ *   - it ends at the first cell (i, j) in row-major order (smallest query
+ *     position i, then smallest target position j) whose H is the maximum;
+ *   - walking back from there, a diagonal step is taken before ending a gap
+ *     along the target (E), and that before ending a gap along the query
+ *     (F); inside a gap, the step at which the gap can open is taken before
+ *     extending it; the walk stops at the first cell whose H is 0.
+ * A pair scoring 0 has the empty alignment (all coordinates 0, no ops).
+ */
+#define SW_OP_M 0   /* query residue aligned with target residue */
+#define SW_OP_I 1   /* query residue opposite a gap */
+#define SW_OP_D 2   /* target residue opposite a gap */
+
+typedef struct {
+    int32_t score;
+    int32_t reserved;
+    int64_t q_begin, q_end;   /* query residues [q_begin, q_end), 0-based */
+    int64_t t_begin, t_end;   /* target residues [t_begin, t_end) */
+    int64_t ops_offset;       /* index of the first op in ops_out */
+    int64_t ops_len;          /* number of ops, from the start of the alignment */
+} sw_alignment;               /* 56 bytes */
+
+typedef struct {
+    int64_t forward_cells;    /* cells of the forward pass (sum of m * n) */
+    int64_t traceback_cells;  /* cells recomputed by the traceback pass */
+    float forward_ms;         /* device time of the forward pass */
+    float traceback_ms;       /* device time of the traceback pass */
+    int32_t launches;
+    int32_t reserved;
+} sw_align_stats;             /* 32 bytes */
+
+/*
+ * Ops capacity sw_align needs for these pairs, in bytes: the sum over pairs
+ * of (query length + target length).  Arguments as for sw_align.
+ */
+int sw_align_ops_capacity(const sw_db *db, const int64_t *q_offsets, int32_t n_q,
+                          const int32_t *pair_query, const int64_t *pair_target, int64_t n_pairs,
+                          int64_t *bytes);
+
+/*
+ * Align n_pairs pairs: query pair_query[k] (index into q_offsets) against
+ * database sequence pair_target[k] (caller's original order).
+ *   queries, q_offsets, n_q   as for sw_search (queries host or device)
+ *   pair_query, pair_target   host arrays of n_pairs entries
+ *   matrix, gap_open, gap_extend   as for sw_search (int32 arithmetic)
+ *   alignments_out  host array of n_pairs sw_alignment
+ *   ops_out         host buffer of ops_capacity bytes (sw_align_ops_capacity);
+ *                   pair k's ops are ops_out[ops_offset .. ops_offset + ops_len),
+ *                   each SW_OP_M, SW_OP_I or SW_OP_D
+ *   stats           NULL or counters
+ *   stream          cudaStream_t, or NULL for the handle's stream
+ * The call is synchronous.  Device scratch comes from the handle's own
+ * workspace (grown as needed): for each pair about 8 * ceil(m/256) * (n+1)
+ * bytes of strip checkpoints plus 256 * n bytes of traceback flags.
+ * Errors: SW_ERR_INVALID_ARG (NULL or out-of-range argument, ops_capacity too
+ * small), SW_ERR_OVERFLOW (as sw_search's int32 limits), SW_ERR_OOM,
+ * SW_ERR_CUDA.
+ */
+int sw_align(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_t n_q,
+             const int32_t *pair_query, const int64_t *pair_target, int64_t n_pairs,
+             const int32_t *matrix, int32_t gap_open, int32_t gap_extend,
+             sw_alignment *alignments_out, uint8_t *ops_out, int64_t ops_capacity,
+             sw_align_stats *stats, void *stream);
+
+/*
  * Score one query against a loaded database without allocating any device
  * memory during the call.  (The paper has no counterpart: this entry point
  * exists for callers of this library that cannot allocate at search time.)

@@ -21,6 +21,9 @@ SW_MODE_AUTO, SW_MODE_PLAIN, SW_MODE_BATCHED = 0, 1, 2
 SW_FLAG_GRAPH = 1
 
 HIT_DTYPE = np.dtype([("score", "<i4"), ("reserved", "<i4"), ("db_index", "<i8")])
+SW_OP_M, SW_OP_I, SW_OP_D = 0, 1, 2
+ALIGNMENT_DTYPE = np.dtype([("score", "<i4"), ("reserved", "<i4"), ("q_begin", "<i8"), ("q_end", "<i8"),
+                            ("t_begin", "<i8"), ("t_end", "<i8"), ("ops_offset", "<i8"), ("ops_len", "<i8")])
 
 _STATUS = {0: "SW_OK", 1: "SW_ERR_INVALID_ARG", 2: "SW_ERR_OOM", 3: "SW_ERR_CUDA", 4: "SW_ERR_TIMEOUT",
            5: "SW_ERR_OVERFLOW", 6: "SW_ERR_UNSUPPORTED"}
@@ -47,6 +50,12 @@ class SwSearchStats(ctypes.Structure):
                 ("intra_ms", ctypes.c_float), ("other_ms", ctypes.c_float), ("inter_launches", ctypes.c_int32),
                 ("inter_cells", ctypes.c_int64), ("long_cells", ctypes.c_int64),
                 ("graph_replayed", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+
+
+class SwAlignStats(ctypes.Structure):
+    _fields_ = [("forward_cells", ctypes.c_int64), ("traceback_cells", ctypes.c_int64),
+                ("forward_ms", ctypes.c_float), ("traceback_ms", ctypes.c_float), ("launches", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class SwDbInfo(ctypes.Structure):
@@ -81,6 +90,9 @@ def load_library():
     lib.sw_top_k.argtypes = [vp, i64, i64, i32, vp, vp]
     lib.sw_probe_alu_rate.argtypes = [ctypes.c_int, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
     lib.sw_search_no_alloc.argtypes = [vp, vp, i32, vp, i32, i32, vp, vp]
+    lib.sw_align_ops_capacity.argtypes = [vp, vp, i32, vp, vp, i64, ctypes.POINTER(i64)]
+    lib.sw_align.argtypes = [vp, vp, vp, i32, vp, vp, i64, vp, i32, i32, vp, vp, i64,
+                             ctypes.POINTER(SwAlignStats), vp]
     for name in ("sw_db_load", "sw_db_free", "sw_db_get_info", "sw_search_workspace_size", "sw_search",
                  "sw_top_k", "sw_probe_alu_rate", "sw_search_no_alloc"):
         getattr(lib, name).restype = ctypes.c_int
@@ -251,6 +263,46 @@ def sw_search_no_alloc(handle, query, matrix, gap_open: int, gap_extend: int, sc
                                              sp, stream))
 
 
+def _pairs(pair_query, pair_target):
+    pq = np.ascontiguousarray(pair_query, dtype=np.int32)
+    pt = np.ascontiguousarray(pair_target, dtype=np.int64)
+    if pq.shape != pt.shape or pq.ndim != 1:
+        raise ValueError("pair_query and pair_target must be 1-D arrays of the same length")
+    return pq, pt
+
+
+def sw_align_ops_capacity(handle, q_offsets, pair_query, pair_target) -> int:
+    q_offsets = np.ascontiguousarray(q_offsets, dtype=np.int64)
+    pq, pt = _pairs(pair_query, pair_target)
+    out = ctypes.c_int64(0)
+    _check(load_library().sw_align_ops_capacity(handle, q_offsets.ctypes.data, len(q_offsets) - 1,
+                                                pq.ctypes.data if len(pq) else None,
+                                                pt.ctypes.data if len(pt) else None, len(pq), ctypes.byref(out)))
+    return out.value
+
+
+def sw_align(handle, queries, q_offsets, pair_query, pair_target, matrix, gap_open: int, gap_extend: int,
+             stats: bool = False, stream=None):
+    """Alignments of the pairs (query pair_query[k], database sequence
+    pair_target[k]).  Returns (alignments ALIGNMENT_DTYPE [n_pairs], ops uint8,
+    stats dict or None); pair k's ops are ops[ops_offset : ops_offset + ops_len]."""
+    q_offsets = np.ascontiguousarray(q_offsets, dtype=np.int64)
+    pq, pt = _pairs(pair_query, pair_target)
+    qp, _ = _addr(queries, np.uint8, "queries")
+    matrix = np.ascontiguousarray(matrix, dtype=np.int32)
+    cap = sw_align_ops_capacity(handle, q_offsets, pq, pt)
+    aln = np.zeros(len(pq), dtype=ALIGNMENT_DTYPE)
+    ops = np.zeros(max(cap, 1), dtype=np.uint8)
+    st = SwAlignStats()
+    _check(load_library().sw_align(handle, qp, q_offsets.ctypes.data, len(q_offsets) - 1,
+                                   pq.ctypes.data if len(pq) else None, pt.ctypes.data if len(pt) else None,
+                                   len(pq), matrix.ctypes.data, int(gap_open), int(gap_extend),
+                                   aln.ctypes.data if len(pq) else None, ops.ctypes.data, cap,
+                                   ctypes.byref(st) if stats else None, stream))
+    sd = {f: getattr(st, f) for f, _ in SwAlignStats._fields_} if stats else None
+    return aln, ops[:cap], sd
+
+
 class Database:
     """A resident database (wraps sw_db_load / sw_search / sw_db_free)."""
 
@@ -277,6 +329,12 @@ class Database:
             hits = np.empty((nq, max(top_k, 0)), dtype=HIT_DTYPE) if top_k > 0 else None
         stats = sw_search(self.handle, queries, q_offsets, matrix, gap_open, gap_extend, top_k, scores, hits, **kw)
         return scores, hits, stats
+
+    def align(self, queries, q_offsets, pair_query, pair_target, matrix, gap_open: int, gap_extend: int,
+              stats: bool = False):
+        """Alignments of chosen (query, database sequence) pairs: see sw_align."""
+        return sw_align(self.handle, queries, q_offsets, pair_query, pair_target, matrix, gap_open, gap_extend,
+                        stats=stats)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -55,6 +55,7 @@ struct sw_db {
     std::vector<int64_t> h_bundle_off;
     std::vector<int32_t> h_bundle_len;
     std::vector<int32_t> h_len;    // sorted lengths
+    std::vector<int64_t> h_sorted_pos;   // original index -> sorted position
 
     uint8_t *d_codes = nullptr;
     int64_t *d_bundle_off = nullptr;
@@ -593,6 +594,8 @@ int sw_db_load(const uint8_t *residues, const int64_t *offsets, int64_t n_seqs, 
         perm[size_t(s)] = order[size_t(s)];
         db->h_len[size_t(s)] = int32_t(offsets[order[s] + 1] - offsets[order[s]]);
     }
+    db->h_sorted_pos.assign(size_t(n_seqs), 0);
+    for (int64_t s = 0; s < n_seqs; ++s) db->h_sorted_pos[size_t(order[size_t(s)])] = s;
     db->h_bundle_off.resize(size_t(db->n_bundles));
     db->h_bundle_len.resize(size_t(db->n_bundles));
     int64_t off = 0;
@@ -1085,6 +1088,243 @@ int sw_probe_alu_rate(int device, int32_t mode, double *per_sm_cycle, int32_t *s
     if (err != cudaSuccess) return fail(SW_ERR_CUDA, cudaGetErrorString(err));
     *per_sm_cycle = best;
     *sm_count = sms;
+    return SW_OK;
+}
+
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// alignments (traceback) of chosen pairs
+
+namespace {
+
+int check_align_pairs(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int32_t *pair_query,
+                      const int64_t *pair_target, int64_t n_pairs) {
+    if (!db) return fail(SW_ERR_INVALID_ARG, "db is NULL");
+    if (n_q < 0 || n_pairs < 0) return fail(SW_ERR_INVALID_ARG, "negative count");
+    if (n_pairs == 0) return SW_OK;
+    if (!pair_query || !pair_target) return fail(SW_ERR_INVALID_ARG, "pair arrays are NULL");
+    if (n_q == 0 || !q_offsets) return fail(SW_ERR_INVALID_ARG, "no queries");
+    if (q_offsets[0] != 0) return fail(SW_ERR_INVALID_ARG, "q_offsets[0] must be 0");
+    for (int32_t i = 0; i < n_q; ++i) {
+        const int64_t m = q_offsets[i + 1] - q_offsets[i];
+        if (m < 0) return fail(SW_ERR_INVALID_ARG, "q_offsets must be non-decreasing");
+        if (m > (int64_t(1) << 30)) return fail(SW_ERR_INVALID_ARG, "query longer than 2^30");
+    }
+    for (int64_t k = 0; k < n_pairs; ++k) {
+        if (pair_query[k] < 0 || pair_query[k] >= n_q) return fail(SW_ERR_INVALID_ARG, "pair_query out of range");
+        if (pair_target[k] < 0 || pair_target[k] >= db->n_seqs)
+            return fail(SW_ERR_INVALID_ARG, "pair_target out of range");
+    }
+    return SW_OK;
+}
+
+int64_t pair_len_q(const int64_t *q_offsets, int32_t qi) { return q_offsets[qi + 1] - q_offsets[qi]; }
+int64_t pair_len_t(const sw_db *db, int64_t ti) { return db->h_len[size_t(db->h_sorted_pos[size_t(ti)])]; }
+
+// Device bytes of one pair's traceback scratch (checkpoints, flags, reversed
+// and ordered ops), each part rounded to 256 bytes.
+int64_t align_pair_bytes(int64_t m, int64_t n) {
+    const int64_t ck = align_checkpoint_rows(int32_t(m)) * (n + 1) * int64_t(sizeof(int2));
+    const int64_t fl = int64_t(align_strip_rows()) * n;
+    auto r256 = [](int64_t x) { return (x + 255) & ~int64_t(255); };
+    return r256(ck) + r256(fl) + 2 * r256(m + n);
+}
+
+constexpr int64_t kAlignChunkBytes = int64_t(1) << 30;
+
+}  // namespace
+
+extern "C" {
+
+int sw_align_ops_capacity(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int32_t *pair_query,
+                          const int64_t *pair_target, int64_t n_pairs, int64_t *bytes) {
+    g_last_error.clear();
+    if (!bytes) return fail(SW_ERR_INVALID_ARG, "bytes is NULL");
+    const int rc = check_align_pairs(db, q_offsets, n_q, pair_query, pair_target, n_pairs);
+    if (rc) return rc;
+    int64_t total = 0;
+    for (int64_t k = 0; k < n_pairs; ++k)
+        total += pair_len_q(q_offsets, pair_query[k]) + pair_len_t(db, pair_target[k]);
+    *bytes = total;
+    return SW_OK;
+}
+
+int sw_align(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_t n_q, const int32_t *pair_query,
+             const int64_t *pair_target, int64_t n_pairs, const int32_t *matrix, int32_t gap_open,
+             int32_t gap_extend, sw_alignment *alignments_out, uint8_t *ops_out, int64_t ops_capacity,
+             sw_align_stats *stats, void *stream) {
+    g_last_error.clear();
+    int rc = check_align_pairs(db, q_offsets, n_q, pair_query, pair_target, n_pairs);
+    if (rc) return rc;
+    if (!matrix) return fail(SW_ERR_INVALID_ARG, "matrix is NULL");
+    if (gap_open < 0 || gap_extend < 0) return fail(SW_ERR_INVALID_ARG, "gap penalties must be >= 0");
+    if (stats) memset(stats, 0, sizeof *stats);
+    if (n_pairs == 0) return SW_OK;
+    if (!alignments_out) return fail(SW_ERR_INVALID_ARG, "alignments_out is NULL");
+    int64_t ops_need = 0, max_min_len = 0;
+    for (int64_t k = 0; k < n_pairs; ++k) {
+        const int64_t m = pair_len_q(q_offsets, pair_query[k]), n = pair_len_t(db, pair_target[k]);
+        ops_need += m + n;
+        max_min_len = std::max(max_min_len, std::min(m, n));
+    }
+    if (ops_need > 0 && (!ops_out || ops_capacity < ops_need))
+        return fail(SW_ERR_INVALID_ARG, "ops_capacity too small (see sw_align_ops_capacity)");
+    // int32 arithmetic: the limits of sw_search's int32 path.
+    const int A = db->A;
+    int smax = matrix[0], smin = matrix[0];
+    for (int i = 0; i < A * A; ++i) {
+        smax = std::max(smax, matrix[i]);
+        smin = std::min(smin, matrix[i]);
+    }
+    const int64_t absmax = std::max<int64_t>(smax, -int64_t(smin));
+    if (absmax > (1 << 20) || int64_t(gap_open) + gap_extend > (int64_t(1) << 28) ||
+        max_min_len * std::max(smax, 0) + gap_open + gap_extend + absmax > (int64_t(1) << 28))
+        return fail(SW_ERR_OVERFLOW, "matrix entries, penalties or lengths too large for exact int32 scores");
+
+    std::lock_guard<std::mutex> lock(db->mu);
+    DeviceGuard guard(db->device);
+    const int64_t total_q = q_offsets[n_q];
+    if (total_q > 0 && !queries) return fail(SW_ERR_INVALID_ARG, "queries is NULL");
+    const bool q_dev = total_q == 0 || is_device_ptr(queries);
+    if (!q_dev)
+        for (int64_t i = 0; i < total_q; ++i)
+            if (queries[i] >= A) return fail(SW_ERR_INVALID_ARG, "query residue code >= alphabet_size");
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : db->stream;
+
+    // Chunks of pairs whose scratch stays under kAlignChunkBytes (a single
+    // larger pair forms a chunk of its own).
+    std::vector<int64_t> chunk_begin{0};
+    int64_t acc = 0, max_chunk_scratch = 0;
+    for (int64_t k = 0; k < n_pairs; ++k) {
+        const int64_t b = align_pair_bytes(pair_len_q(q_offsets, pair_query[k]), pair_len_t(db, pair_target[k]));
+        if (acc > 0 && acc + b > kAlignChunkBytes) {
+            chunk_begin.push_back(k);
+            max_chunk_scratch = std::max(max_chunk_scratch, acc);
+            acc = 0;
+        }
+        acc += b;
+    }
+    max_chunk_scratch = std::max(max_chunk_scratch, acc);
+    chunk_begin.push_back(n_pairs);
+    int64_t max_chunk_pairs = 0;
+    for (size_t c = 0; c + 1 < chunk_begin.size(); ++c)
+        max_chunk_pairs = std::max(max_chunk_pairs, chunk_begin[c + 1] - chunk_begin[c]);
+
+    auto r256 = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t q_bytes = q_dev ? 0 : r256(size_t(total_q));
+    const size_t mat_bytes = r256(sizeof(int32_t) * kProfRows * kProfRows);
+    const size_t pairs_bytes = r256(sizeof(AlignPairDev) * size_t(max_chunk_pairs));
+    const size_t res_bytes = r256(sizeof(AlignResultDev) * size_t(max_chunk_pairs));
+    const size_t need = q_bytes + mat_bytes + pairs_bytes + res_bytes + size_t(max_chunk_scratch) + 256;
+    if (db->ws_bytes < need) {
+        SW_CUDA_TRY(cudaDeviceSynchronize());
+        cudaFree(db->ws);
+        db->ws = nullptr;
+        db->ws_bytes = 0;
+        SW_CUDA_TRY(cudaMalloc(&db->ws, need));
+        db->ws_bytes = need;
+    }
+    uint8_t *w = static_cast<uint8_t *>(db->ws);
+    uint8_t *d_q = q_dev ? const_cast<uint8_t *>(queries) : w;
+    int32_t *d_mat = reinterpret_cast<int32_t *>(w + q_bytes);
+    AlignPairDev *d_pairs = reinterpret_cast<AlignPairDev *>(w + q_bytes + mat_bytes);
+    AlignResultDev *d_res = reinterpret_cast<AlignResultDev *>(w + q_bytes + mat_bytes + pairs_bytes);
+    uint8_t *d_scratch = w + q_bytes + mat_bytes + pairs_bytes + res_bytes;
+
+    std::vector<int32_t> mat(kProfRows * kProfRows, 0);
+    for (int x = 0; x < A; ++x)
+        for (int y = 0; y < A; ++y) mat[size_t(x * kProfRows + y)] = matrix[x * A + y];
+    if (!q_dev && total_q > 0) SW_CUDA_TRY(cudaMemcpyAsync(d_q, queries, size_t(total_q), cudaMemcpyHostToDevice, st));
+    SW_CUDA_TRY(cudaMemcpyAsync(d_mat, mat.data(), sizeof(int32_t) * mat.size(), cudaMemcpyHostToDevice, st));
+
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    if (stats)
+        for (auto &x : ev) SW_CUDA_TRY(cudaEventCreate(&x));
+    struct EvFree {
+        cudaEvent_t *e;
+        ~EvFree() {
+            for (int i = 0; i < 3; ++i)
+                if (e[i]) cudaEventDestroy(e[i]);
+        }
+    } ev_free{ev};
+
+    int64_t ops_base = 0;
+    std::vector<AlignPairDev> hp;
+    std::vector<AlignResultDev> hr;
+    for (size_t c = 0; c + 1 < chunk_begin.size(); ++c) {
+        const int64_t k0 = chunk_begin[c], k1 = chunk_begin[c + 1], np = k1 - k0;
+        hp.assign(size_t(np), AlignPairDev{});
+        // scratch layout of the chunk: ckpt | flags | rev | ops, each pair's part 256-byte aligned
+        int64_t ck = 0, fl = 0, rv = 0, op = 0;
+        for (int64_t k = k0; k < k1; ++k) {
+            AlignPairDev &d = hp[size_t(k - k0)];
+            const int64_t m = pair_len_q(q_offsets, pair_query[k]), n = pair_len_t(db, pair_target[k]);
+            d.q_off = q_offsets[pair_query[k]];
+            d.t_sorted = db->h_sorted_pos[size_t(pair_target[k])];
+            d.m = int32_t(m);
+            d.n = int32_t(n);
+            d.ckpt_off = ck / int64_t(sizeof(int2));
+            ck += r256(size_t(align_checkpoint_rows(int32_t(m)) * (n + 1) * int64_t(sizeof(int2))));
+            d.flags_off = fl;
+            fl += r256(size_t(int64_t(align_strip_rows()) * n));
+            d.rev_off = rv;
+            rv += r256(size_t(m + n));
+            d.ops_off = op;
+            op += m + n;
+        }
+        AlignArgs a;
+        memset(&a, 0, sizeof a);
+        a.db = db->view();
+        a.queries = d_q;
+        a.pairs = d_pairs;
+        a.n_pairs = np;
+        a.results = d_res;
+        a.mat = d_mat;
+        a.ckpt = reinterpret_cast<int2 *>(d_scratch);
+        a.flags = d_scratch + ck;
+        a.rev = d_scratch + ck + fl;
+        a.ops = d_scratch + ck + fl + rv;
+        a.gap_open = gap_open;
+        a.gap_extend = gap_extend;
+        SW_CUDA_TRY(cudaMemcpyAsync(d_pairs, hp.data(), sizeof(AlignPairDev) * size_t(np), cudaMemcpyHostToDevice, st));
+        if (stats) SW_CUDA_TRY(cudaEventRecord(ev[0], st));
+        SW_CUDA_TRY(launch_align(a, 0, st));
+        if (stats) SW_CUDA_TRY(cudaEventRecord(ev[1], st));
+        SW_CUDA_TRY(launch_align(a, 1, st));
+        if (stats) SW_CUDA_TRY(cudaEventRecord(ev[2], st));
+        hr.assign(size_t(np), AlignResultDev{});
+        SW_CUDA_TRY(cudaMemcpyAsync(hr.data(), d_res, sizeof(AlignResultDev) * size_t(np), cudaMemcpyDeviceToHost, st));
+        if (op > 0) SW_CUDA_TRY(cudaMemcpyAsync(ops_out + ops_base, a.ops, size_t(op), cudaMemcpyDeviceToHost, st));
+        SW_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int64_t k = k0; k < k1; ++k) {
+            const AlignResultDev &r = hr[size_t(k - k0)];
+            if (r.status != 0) return fail(SW_ERR_CUDA, "traceback walk met an inconsistent cell");
+            sw_alignment &o = alignments_out[k];
+            o.score = r.score;
+            o.reserved = 0;
+            o.q_begin = r.i_begin;
+            o.q_end = r.i_end;
+            o.t_begin = r.j_begin;
+            o.t_end = r.j_end;
+            o.ops_offset = ops_base + hp[size_t(k - k0)].ops_off;
+            o.ops_len = r.n_ops;
+            if (stats) {
+                stats->forward_cells += int64_t(hp[size_t(k - k0)].m) * hp[size_t(k - k0)].n;
+                stats->traceback_cells += r.cells;
+            }
+        }
+        if (stats) {
+            float t0 = 0.f, t1 = 0.f;
+            SW_CUDA_TRY(cudaEventElapsedTime(&t0, ev[0], ev[1]));
+            SW_CUDA_TRY(cudaEventElapsedTime(&t1, ev[1], ev[2]));
+            stats->forward_ms += t0;
+            stats->traceback_ms += t1;
+            stats->launches += 2;
+        }
+        ops_base += op;
+    }
     return SW_OK;
 }
 

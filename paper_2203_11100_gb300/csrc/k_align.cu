@@ -1,0 +1,302 @@
+// Traceback of optimal local alignments for chosen (query, database
+// sequence) pairs: the alignment behind a score of Section 2.2, read back
+// from the Gotoh matrices (affine gaps as in Section 4.1) with the tie rules
+// stated in swdb.h.
+//
+// One warp per pair, int32 arithmetic.  Lane k holds query rows
+// 8k+1 .. 8k+8 of a 256-row strip and runs one column behind lane k-1 (a
+// skewed wavefront: H and F of a lane's bottom row reach the next lane by
+// shuffle).  The int32 profile of the strip, [target code][row], sits in
+// shared memory, so a lane reads its 8 rows with two 16-byte loads.
+//
+// Forward pass (k_align_fwd): every strip in turn over all n columns; the
+// last lane writes its bottom row's H and F for every column (the strip's
+// checkpoint row, the top boundary of the next strip).  The maximum and the
+// first cell in row-major order that holds it are kept per lane and reduced
+// over the warp at the end.
+//
+// Traceback pass (k_align_bwd): starting from the end cell's strip, the
+// warp recomputes that strip's rows up to the current row and columns up to
+// the current column from the checkpoint row above it, storing one flag byte
+// per cell (which of the candidates H equals, whether E and F open at the
+// cell); lane 0 then walks the path through the strip.  When the path
+// leaves the strip at the top, the strip above is recomputed the same way.
+// Every strip is recomputed at most once, so the traceback costs at most
+// one more forward pass, and memory is ceil(m/256) checkpoint rows plus one
+// strip of flags instead of m x n.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/swdb.h"
+#include "swdb_internal.cuh"
+
+namespace swdb {
+namespace {
+
+constexpr int kAR = 8;                   // query rows per lane
+constexpr int kStrip = 32 * kAR;         // rows per strip
+constexpr int32_t kNegInf = -(1 << 29);  // -infinity of the recurrences
+
+// flag bits of one cell (i, j)
+constexpr uint8_t F_ZERO = 1;    // H(i,j) = 0
+constexpr uint8_t F_DIAG = 2;    // H(i,j) = H(i-1,j-1) + S(q_i, t_j)
+constexpr uint8_t F_HE = 4;      // H(i,j) = E(i,j)
+constexpr uint8_t F_HF = 8;      // H(i,j) = F(i,j)
+constexpr uint8_t F_EOPEN = 16;  // E(i,j) = H(i,j-1) - o
+constexpr uint8_t F_FOPEN = 32;  // F(i,j) = H(i-1,j) - o
+
+// Address of column 0 of sorted database sequence s in the bundle layout;
+// column j0 is at base[(j0/4)*64 + (j0%4)*2].
+__device__ __forceinline__ const uint8_t *target_base(const DbView &db, int64_t s) {
+    const int64_t b = s / kBundleSeqs;
+    const int slot = int((s % kBundleSeqs) >> 1);
+    const int h = int(s & 1);
+    return db.codes + db.bundle_off[b] + slot * kQuadBytes + h;
+}
+
+__device__ __forceinline__ int target_code(const uint8_t *base, int j0) {
+    return base[int64_t(j0 >> 2) * kBundleRowBytes + (j0 & 3) * 2];
+}
+
+// Profile of rows r0 .. r0+255: prof[c][r] = S(q_{r0+r}, c), -inf past m or
+// for codes outside the matrix.
+__device__ __forceinline__ void load_profile(int32_t (*prof)[kStrip], const int32_t *mat, const uint8_t *q,
+                                             int m, int r0, int lane) {
+    for (int idx = lane; idx < kProfRows * kStrip; idx += 32) {
+        const int c = idx / kStrip, r = idx % kStrip;
+        int32_t v = kNegInf;
+        if (r0 + r < m) {
+            const int qc = q[r0 + r];
+            if (qc < kProfRows) v = mat[qc * kProfRows + c];
+        }
+        prof[c][r] = v;
+    }
+}
+
+__device__ __forceinline__ int32_t max3(int32_t a, int32_t b, int32_t c) { return __vimax3_s32(a, b, c); }
+
+__global__ void __launch_bounds__(32) k_align_fwd(const AlignArgs a) {
+    __shared__ __align__(16) int32_t prof[kProfRows][kStrip];
+    __shared__ int32_t mat[kProfRows * kProfRows];
+    const int lane = threadIdx.x;
+    const AlignPairDev P = a.pairs[blockIdx.x];
+    AlignResultDev *R = a.results + blockIdx.x;
+    for (int i = lane; i < kProfRows * kProfRows; i += 32) mat[i] = a.mat[i];
+    const int m = P.m, n = P.n;
+    if (m <= 0 || n <= 0) {
+        if (lane == 0) *R = AlignResultDev{};
+        return;
+    }
+    const uint8_t *q = a.queries + P.q_off;
+    const uint8_t *tb = target_base(a.db, P.t_sorted);
+    const int32_t o = a.gap_open, e = a.gap_extend;
+
+    int32_t best = 0;
+    int64_t bkey = INT64_MAX;              // (i << 32) | j of the first maximum in row-major order
+    for (int r0 = 0; r0 < m; r0 += kStrip) {
+        const int strip = r0 / kStrip;
+        __syncwarp();
+        load_profile(prof, mat, q, m, r0, lane);
+        __syncwarp();
+        int32_t H[kAR], E[kAR];
+#pragma unroll
+        for (int r = 0; r < kAR; ++r) { H[r] = 0; E[r] = kNegInf; }
+        int32_t hd = 0, pub_h = 0, pub_f = kNegInf;
+        const int2 *ck_in = strip > 0 ? a.ckpt + P.ckpt_off + int64_t(strip - 1) * (n + 1) : nullptr;
+        int2 *ck_out = a.ckpt + P.ckpt_off + int64_t(strip) * (n + 1);
+        const bool write_ck = r0 + kStrip < m;
+        const int row0 = r0 + lane * kAR + 1;          // 1-based first row of this lane
+        for (int s = 0; s < n + 31; ++s) {
+            int32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1);
+            int32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1);
+            const int j = s - lane + 1;                 // 1-based column
+            if (j >= 1 && j <= n) {
+                if (lane == 0) {
+                    if (strip == 0) { hin = 0; fin = kNegInf; }
+                    else { const int2 v = ck_in[j]; hin = v.x; fin = v.y; }
+                }
+                const int c = target_code(tb, j - 1);
+                const int4 p0 = *reinterpret_cast<const int4 *>(&prof[c][lane * kAR]);
+                const int4 p1 = *reinterpret_cast<const int4 *>(&prof[c][lane * kAR + 4]);
+                const int32_t sc[kAR] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+                int32_t f = fin, up = hin, d = hd;
+#pragma unroll
+                for (int r = 0; r < kAR; ++r) {
+                    const int32_t e_r = __viaddmax_s32(E[r], -e, H[r] - o);     // E(i,j)
+                    f = __viaddmax_s32(f, -e, up - o);                           // F(i,j)
+                    const int32_t h = max3(d + sc[r], e_r, max(f, 0));           // H(i,j)
+                    d = H[r];
+                    E[r] = e_r;
+                    H[r] = h;
+                    up = h;
+                    const int i = row0 + r;
+                    if (h >= best && h > 0 && i <= m) {
+                        const int64_t key = (int64_t(i) << 32) | uint32_t(j);
+                        if (h > best || key < bkey) { best = h; bkey = key; }
+                    }
+                }
+                hd = hin;
+                pub_h = H[kAR - 1];
+                pub_f = f;
+                if (write_ck && lane == 31) ck_out[j] = make_int2(H[kAR - 1], f);
+            }
+        }
+        if (write_ck && lane == 31) ck_out[0] = make_int2(0, kNegInf);
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const int32_t ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int64_t ok = __shfl_xor_sync(0xffffffffu, bkey, off);
+        if (ob > best || (ob == best && ok < bkey)) { best = ob; bkey = ok; }
+    }
+    if (lane == 0) {
+        AlignResultDev res{};
+        res.score = best;
+        if (best > 0) {
+            res.i_end = int32_t(bkey >> 32);
+            res.j_end = int32_t(bkey & 0xffffffff);
+        }
+        *R = res;
+    }
+}
+
+__global__ void __launch_bounds__(32) k_align_bwd(const AlignArgs a) {
+    __shared__ __align__(16) int32_t prof[kProfRows][kStrip];
+    __shared__ int32_t mat[kProfRows * kProfRows];
+    const int lane = threadIdx.x;
+    const AlignPairDev P = a.pairs[blockIdx.x];
+    AlignResultDev *R = a.results + blockIdx.x;
+    for (int i = lane; i < kProfRows * kProfRows; i += 32) mat[i] = a.mat[i];
+    const int m = P.m, n = P.n;
+    if (R->score <= 0 || m <= 0 || n <= 0) return;   // empty alignment, written by the forward pass
+    const uint8_t *q = a.queries + P.q_off;
+    const uint8_t *tb = target_base(a.db, P.t_sorted);
+    const int32_t o = a.gap_open, e = a.gap_extend;
+    uint8_t *flags = a.flags + P.flags_off;          // [column j-1][row within the strip]
+    uint8_t *rev = a.rev + P.rev_off;
+    const int64_t max_ops = int64_t(m) + n;
+
+    int i = R->i_end, j = R->j_end, state = 0;        // state 0 = H, 1 = E, 2 = F
+    int64_t k = 0;
+    int done = 0, status = 0;
+    int64_t cells = 0;
+    while (!done) {
+        if (i < 1) { status = 4; break; }             // not reached: a gap opens at row 1
+        const int strip = (i - 1) / kStrip;
+        const int r0 = strip * kStrip;
+        const int cols = j;
+        __syncwarp();
+        load_profile(prof, mat, q, m, r0, lane);
+        __syncwarp();
+        int32_t H[kAR], E[kAR];
+#pragma unroll
+        for (int r = 0; r < kAR; ++r) { H[r] = 0; E[r] = kNegInf; }
+        int32_t hd = 0, pub_h = 0, pub_f = kNegInf;
+        const int2 *ck_in = strip > 0 ? a.ckpt + P.ckpt_off + int64_t(strip - 1) * (n + 1) : nullptr;
+        const int row0 = r0 + lane * kAR + 1;
+        const bool lane_used = row0 <= i;             // rows below the path's row are never read
+        for (int s = 0; s < cols + 31; ++s) {
+            int32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1);
+            int32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1);
+            const int jj = s - lane + 1;
+            if (jj >= 1 && jj <= cols && lane_used) {
+                if (lane == 0) {
+                    if (strip == 0) { hin = 0; fin = kNegInf; }
+                    else { const int2 v = ck_in[jj]; hin = v.x; fin = v.y; }
+                }
+                const int c = target_code(tb, jj - 1);
+                const int4 p0 = *reinterpret_cast<const int4 *>(&prof[c][lane * kAR]);
+                const int4 p1 = *reinterpret_cast<const int4 *>(&prof[c][lane * kAR + 4]);
+                const int32_t sc[kAR] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+                int32_t f = fin, up = hin, d = hd;
+                uint32_t fl[2] = {0u, 0u};
+#pragma unroll
+                for (int r = 0; r < kAR; ++r) {
+                    const int32_t hleft_o = H[r] - o;
+                    const int32_t e_r = __viaddmax_s32(E[r], -e, hleft_o);
+                    const int32_t up_o = up - o;
+                    f = __viaddmax_s32(f, -e, up_o);
+                    const int32_t diag = d + sc[r];
+                    const int32_t h = max3(diag, e_r, max(f, 0));
+                    uint32_t b = 0;
+                    if (h == 0) b |= F_ZERO;
+                    if (h == diag) b |= F_DIAG;
+                    if (h == e_r) b |= F_HE;
+                    if (h == f) b |= F_HF;
+                    if (e_r == hleft_o) b |= F_EOPEN;
+                    if (f == up_o) b |= F_FOPEN;
+                    fl[r >> 2] |= b << (8 * (r & 3));
+                    d = H[r];
+                    E[r] = e_r;
+                    H[r] = h;
+                    up = h;
+                }
+                *reinterpret_cast<uint2 *>(flags + int64_t(jj - 1) * kStrip + lane * kAR) = make_uint2(fl[0], fl[1]);
+                hd = hin;
+                pub_h = H[kAR - 1];
+                pub_f = f;
+            }
+        }
+        cells += int64_t(min(i, m) - r0) * cols;
+        __syncwarp();
+        if (lane == 0) {
+            // Walk the path through rows r0+1 .. i of this strip.
+            for (;;) {
+                if (k >= max_ops) { status = 1; done = 1; break; }
+                if (state == 0) {
+                    if (i == 0 || j == 0) { done = 1; break; }
+                    if (i <= r0) break;                // continue in the strip above
+                    const uint8_t b = flags[int64_t(j - 1) * kStrip + (i - r0 - 1)];
+                    if (b & F_ZERO) { done = 1; break; }
+                    if (b & F_DIAG) { rev[k++] = SW_OP_M; --i; --j; }
+                    else if (b & F_HE) state = 1;
+                    else if (b & F_HF) state = 2;
+                    else { status = 2; done = 1; break; }
+                } else if (state == 1) {
+                    if (j == 0) { status = 3; done = 1; break; }
+                    const uint8_t b = flags[int64_t(j - 1) * kStrip + (i - r0 - 1)];
+                    rev[k++] = SW_OP_D;
+                    if (b & F_EOPEN) state = 0;
+                    --j;
+                } else {
+                    if (i <= r0) break;                // continue in the strip above
+                    const uint8_t b = flags[int64_t(j - 1) * kStrip + (i - r0 - 1)];
+                    rev[k++] = SW_OP_I;
+                    if (b & F_FOPEN) state = 0;
+                    --i;
+                }
+            }
+        }
+        i = __shfl_sync(0xffffffffu, i, 0);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        state = __shfl_sync(0xffffffffu, state, 0);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        done = __shfl_sync(0xffffffffu, done, 0);
+        status = __shfl_sync(0xffffffffu, status, 0);
+    }
+    __syncwarp();
+    uint8_t *ops = a.ops + P.ops_off;
+    for (int64_t x = lane; x < k; x += 32) ops[x] = rev[k - 1 - x];
+    if (lane == 0) {
+        R->i_begin = i;
+        R->j_begin = j;
+        R->n_ops = int32_t(k);
+        R->status = status;
+        R->cells = cells;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_align(const AlignArgs &a, int which, cudaStream_t s) {
+    if (a.n_pairs <= 0) return cudaSuccess;
+    if (a.n_pairs > 0x7fffffff) return cudaErrorInvalidValue;
+    if (which == 0) k_align_fwd<<<unsigned(a.n_pairs), 32, 0, s>>>(a);
+    else k_align_bwd<<<unsigned(a.n_pairs), 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int64_t align_checkpoint_rows(int32_t m) { return m <= 0 ? 0 : (int64_t(m) + kStrip - 1) / kStrip; }
+int32_t align_strip_rows() { return kStrip; }
+
+}  // namespace swdb

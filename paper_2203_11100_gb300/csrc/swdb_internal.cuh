@@ -130,6 +130,40 @@ struct I32Args {
     int32_t *status;            // set to nonzero on an internal error
 };
 
+// Traceback of chosen pairs (k_align.cu).  One descriptor per pair; every
+// offset is into the buffer named beside it.
+struct AlignPairDev {
+    int64_t q_off;        // queries: first residue of the query
+    int64_t t_sorted;     // sorted database position of the target
+    int64_t ckpt_off;     // ckpt (int2 units): ceil(m/256) rows of n+1 (H, F)
+    int64_t flags_off;    // flags (bytes): one strip, 256 x n
+    int64_t rev_off;      // rev (bytes): m + n reversed ops
+    int64_t ops_off;      // ops (bytes): m + n ops in order
+    int32_t m, n;
+};
+struct AlignResultDev {
+    int32_t score;
+    int32_t i_end, j_end;      // 1-based end cell (0 when the score is 0)
+    int32_t i_begin, j_begin;  // rows / columns before the alignment's first column
+    int32_t n_ops;
+    int32_t status;            // 0, or where the walk found an inconsistent flag
+    int32_t pad;
+    int64_t cells;             // cells recomputed by the traceback pass
+};
+struct AlignArgs {
+    DbView db;
+    const uint8_t *queries;
+    const AlignPairDev *pairs;
+    int64_t n_pairs;
+    AlignResultDev *results;
+    const int32_t *mat;        // [32][32] int32, entries outside the alphabet unused
+    int2 *ckpt;
+    uint8_t *flags;
+    uint8_t *rev;
+    uint8_t *ops;
+    int32_t gap_open, gap_extend;
+};
+
 // Launchers (return cudaGetLastError() after the launch).
 // grid_slots > 0 launches a persistent grid of that many CTAs (slot-layout
 // scratch); 0 launches one CTA per chunk of pairs (per-pair scratch).
@@ -150,6 +184,9 @@ bool i32_config_supported(int lanes, int rows);
 cudaError_t launch_probe(int mode, int grid, int iters, unsigned long long *cycles, uint32_t *sink,
                          cudaStream_t s);
 int probe_blocks_per_sm(int mode);
+cudaError_t launch_align(const AlignArgs &a, int which, cudaStream_t s);   // 0 forward, 1 traceback
+int64_t align_checkpoint_rows(int32_t m);
+int32_t align_strip_rows();
 cudaError_t launch_topk(const int32_t *scores, int64_t n_rows, int64_t n_cols, int32_t k,
                         void *hits, cudaStream_t s);
 

@@ -78,3 +78,24 @@ def test_top_k_rejects_bad_sizes(lib):
     assert lib.sw_top_k(None, 1, 10, 5000, None, None) == 1
     assert lib.sw_top_k(None, -1, 10, 5, None, None) == 1
     assert lib.sw_top_k(None, 0, 10, 5, None, None) == 0
+
+
+def test_align_rejects_bad_arguments_on_host(lib):
+    from paper_2203_11100_gb300 import binding
+    pq = np.zeros(1, np.int32)
+    pt = np.zeros(1, np.int64)
+    off = np.array([0, 3], dtype=np.int64)
+    out = ctypes.c_int64(0)
+    rc = lib.sw_align_ops_capacity(None, off.ctypes.data, 1, pq.ctypes.data, pt.ctypes.data, 1, ctypes.byref(out))
+    assert rc == 1 and "db is NULL" in binding.sw_last_error()
+    rc = lib.sw_align_ops_capacity(None, off.ctypes.data, 1, pq.ctypes.data, pt.ctypes.data, 1, None)
+    assert rc == 1 and "bytes is NULL" in binding.sw_last_error()
+    rc = lib.sw_align(None, None, off.ctypes.data, 1, pq.ctypes.data, pt.ctypes.data, 1, None, 10, 1,
+                      None, None, 0, None, None)
+    assert rc == 1 and "db is NULL" in binding.sw_last_error()
+
+
+def test_alignment_struct_sizes():
+    from paper_2203_11100_gb300 import binding
+    assert binding.ALIGNMENT_DTYPE.itemsize == 56
+    assert ctypes.sizeof(binding.SwAlignStats) == 32
