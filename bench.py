@@ -72,6 +72,11 @@ def parse_args(argv=None):
                    help="fraction of the 20M-sequence serving database (0.1 = 2M sequences)")
     p.add_argument("--serve-requests", type=int, default=96)
     p.add_argument("--serve-max-batch", type=int, default=16)
+    p.add_argument("--sweep", action="store_true",
+                   help="GCUPS against query length: each query of the workload searched alone, at the "
+                        "workload's gap penalties and at 10/2")
+    p.add_argument("--align", action="store_true",
+                   help="traceback benchmark: align the top-k hits of the workload's search")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-cells", type=float, default=6e10,
                    help="cells of the oracle's bounded sample (about 10-20 s on 16 cores)")
@@ -462,6 +467,153 @@ def run_serving(args, dist: Dist):
             "clocks": clk}
 
 
+def run_sweep(args, dist: Dist):
+    """GCUPS against query length, as in the paper's query-length figure
+    (Section 4.2): every query of the workload searched alone against the
+    whole database (one plain search per query), K timed steps after W
+    warm-up steps each, at the workload's penalties and at the paper's 10/2
+    (Section 4.1)."""
+    import torch
+    import paper_2203_11100_gb300 as swdb
+
+    dev = dist.local_rank
+    torch.cuda.set_device(dev)
+    swdb.load_library()
+    w = synth.make_workload(args.workload, seed=synth.SEED, db_scale=args.db_scale)
+    db = swdb.Database(w.db.residues, w.db.offsets, len(synth.ALPHABET), device=dev)
+    residues = int(w.db.lengths.sum())
+    # A stream of its own: the legacy default stream's handle is NULL, which
+    # the library reads as "the handle's own stream".
+    stream = torch.cuda.Stream(device=dev)
+    scores = torch.empty((1, w.db.n), dtype=torch.int32, device=f"cuda:{dev}")
+    hits = torch.empty((1, w.top_k, 2), dtype=torch.int64, device=f"cuda:{dev}")
+    clocks = ClockSampler(dev)
+    clocks.start()
+    rows = []
+    totals = {}
+    for o, e in ((w.gap_open, w.gap_extend), (10, 2)):
+        cells_sum = ms_sum = 0.0
+        for qi in range(w.queries.n):
+            q = w.queries.seq(qi)
+            q_dev = torch.from_numpy(np.ascontiguousarray(q)).to(f"cuda:{dev}")
+            q_off = np.array([0, len(q)], dtype=np.int64)
+
+            def step():
+                swdb.sw_search(db.handle, q_dev, q_off, w.matrix, o, e, w.top_k, scores, hits,
+                               stream=stream.cuda_stream, mode=swdb.SW_MODE_PLAIN)
+
+            for _ in range(args.warmup):
+                step()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(args.steps):
+                step()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            cells = float(len(q)) * residues * args.steps
+            rows.append({"m": len(q), "gap": f"{o}/{e}", "gcups": cells / ms / 1e6, "ms_per_search": ms / args.steps})
+            cells_sum += cells
+            ms_sum += ms
+        totals[f"{o}/{e}"] = cells_sum / ms_sum / 1e6
+    clk = clocks.stop()
+    db.close()
+    key = f"{w.gap_open}/{w.gap_extend}"
+    return {"metric": "GCUPS by query length (device-timed, one query per search)", "value": totals[key],
+            "unit": UNIT, "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "i16x2", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: each query alone", "db_seqs": w.db.n, "db_residues": residues,
+                       "query_lengths": [int(x) for x in w.queries.lengths], "matrix": "BLOSUM62",
+                       "penalties": list(totals)},
+            "aggregate_gcups": totals, "sweep": rows, "clocks": clk}
+
+
+def run_align(args, dist: Dist):
+    """Traceback of the top-k hits: search the workload once, then align every
+    (query, hit) pair with sw_align; W warm-up and K timed calls."""
+    import torch
+    import paper_2203_11100_gb300 as swdb
+
+    dev = dist.local_rank
+    torch.cuda.set_device(dev)
+    swdb.load_library()
+    w = synth.make_workload(args.workload, seed=synth.SEED, db_scale=args.db_scale)
+    db = swdb.Database(w.db.residues, w.db.offsets, len(synth.ALPHABET), device=dev)
+    _, hits, _ = db.search(w.queries.residues, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend,
+                           top_k=w.top_k, want_scores=False)
+    pq = np.repeat(np.arange(w.queries.n, dtype=np.int32), w.top_k)
+    pt = hits["db_index"].reshape(-1).astype(np.int64)
+    keep = pt >= 0
+    pq, pt = pq[keep], pt[keep]
+    for _ in range(args.warmup):
+        db.align(w.queries.residues, w.queries.offsets, pq, pt, w.matrix, w.gap_open, w.gap_extend)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    fwd_ms = tb_ms = 0.0
+    wall = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        aln, ops, st = db.align(w.queries.residues, w.queries.offsets, pq, pt, w.matrix, w.gap_open,
+                                w.gap_extend, stats=True)
+        wall.append(time.perf_counter() - t0)
+        fwd_ms += st["forward_ms"]
+        tb_ms += st["traceback_ms"]
+    clk = clocks.stop()
+    db.close()
+    if not np.array_equal(aln["score"], hits["score"].reshape(-1)[keep]):
+        raise RuntimeError("alignment scores differ from the search scores")
+    n = len(pq)
+    fwd_cells, tb_cells = st["forward_cells"], st["traceback_cells"]
+    lens_q, lens_t = w.queries.lengths[pq], w.db.lengths[pt]
+    cb = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        order = np.argsort(lens_q * lens_t, kind="stable")
+        pick, cells = [], 0
+        for k in order:                                # smallest pairs first, up to ~1e10 cells
+            c = int(lens_q[k]) * int(lens_t[k])
+            if cells + c > 1e10:
+                break
+            pick.append(int(k))
+            cells += c
+        t0 = time.perf_counter()
+        want = oracle.align_pairs(w.queries, w.db, pq[pick], pt[pick], w.matrix, w.gap_open, w.gap_extend)
+        dt = time.perf_counter() - t0
+        exact = True
+        for k, wa in zip(pick, want):
+            o0 = int(aln["ops_offset"][k])
+            got = ops[o0:o0 + int(aln["ops_len"][k])]
+            exact &= (int(aln["score"][k]), int(aln["q_begin"][k]), int(aln["q_end"][k]), int(aln["t_begin"][k]),
+                      int(aln["t_end"][k])) == (wa["score"], wa["q_begin"], wa["q_end"], wa["t_begin"], wa["t_end"])
+            exact &= bool(np.array_equal(got, wa["ops"]))
+        cb = {"value": len(pick) / dt, "unit": "alignments/s", "cores": oracle.default_threads(), "kind": "oracle",
+              "gcups": cells / dt / 1e9,
+              "sample": f"the {len(pick)} smallest of the {n} pairs ({cells:.3g} cells, {dt:.1f} s)",
+              "sample_bit_exact_vs_gpu": exact}
+    dev_s = (fwd_ms + tb_ms) / 1e3
+    e2e_s = float(np.sum(wall))
+    return {"metric": "alignments of the top-k hits per second (device-timed, bit-exact vs oracle)",
+            "value": n * args.steps / dev_s, "unit": "alignments/s", "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": (fwd_ms + tb_ms) / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+            "config": {"workload": f"{args.workload} top-{w.top_k} hits", "pairs": n,
+                       "query_lengths": [int(lens_q.min()), int(lens_q.max())],
+                       "target_lengths": [int(lens_t.min()), int(lens_t.max())],
+                       "forward_cells_per_step": fwd_cells, "traceback_cells_per_step": tb_cells,
+                       "matrix": "BLOSUM62", "gap_open": w.gap_open, "gap_extend": w.gap_extend},
+            "kernel_ms": {"forward": fwd_ms / args.steps, "traceback": tb_ms / args.steps},
+            "gcups": {"forward": fwd_cells / (fwd_ms / args.steps) / 1e6,
+                      "traceback": tb_cells / (tb_ms / args.steps) / 1e6},
+            "longest_pair_cells": int((lens_q * lens_t).max()),
+            "e2e": {"value": n * args.steps / e2e_s, "unit": "alignments/s",
+                    "h2d_bytes_per_step": int(w.queries.offsets[-1]) + n * 12,
+                    "d2h_bytes_per_step": n * 40 + int(ops.nbytes), "ms_per_step": e2e_s * 1e3 / args.steps},
+            "cpu_baseline": cb, "gpu_launches": 2 * args.steps, "clocks": clk}
+
+
 def run_reference(args, dist: Dist):
     """The oracle timed on the host cores, one bounded sample per step."""
     if dist.rank != 0:
@@ -512,6 +664,12 @@ def main(argv=None):
     elif args.serve:
         dist = Dist()
         out = run_serving(args, dist)
+    elif args.align:
+        dist = Dist()
+        out = run_align(args, dist)
+    elif args.sweep:
+        dist = Dist()
+        out = run_sweep(args, dist)
     else:
         dist = Dist()
         out = run_ours(args, dist)

@@ -331,6 +331,21 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
     for (int64_t b = 0; b < nlb; ++b) p.long_residues += db->h_bundle_res[size_t(b)];
     p.n_long = std::min<int64_t>(nlb * kBundleSeqs, db->n_seqs);
     p.long_codes_bytes = nlb < db->n_bundles ? db->h_bundle_off[size_t(nlb)] : db->codes_bytes;
+    if (!(opts && opts->long_rows_per_lane)) {
+        // Few (long pair, query) tasks: the launch is bound by the serial
+        // column chain of the longest sequences, which shares its SMs with the
+        // concurrent inter-task launch, so 16 rows per lane (a shorter step)
+        // wins; many tasks: it is throughput-bound and 32 rows per lane (less
+        // overhead per cell) wins (measured on GB300: a lone 144-residue query
+        // against the 565,000-sequence database 17.5 vs 22.8 ms; the 50,000-
+        // sequence database with 10% long sequences 4,311 vs 3,789 GCUPS at
+        // m = 35,000 for 32 rows).
+        int32_t nonempty = 0;
+        for (int32_t i = 0; i < n_q; ++i) nonempty += q_offsets[i + 1] > q_offsets[i];
+        const bool few = p.long_end_pair * int64_t(nonempty) <= 4 * int64_t(std::max(1, db->sm_count));
+        p.rows_long = few ? 16 : 32;
+        p.warps_long = few ? 4 : 2;
+    }
     p.need_long_boundary = nlb > 0 && p.max_m > intra_rows_per_superpass(p.warps_long, p.rows_long);
     if (nlb > 0 && p.precision == SW_PREC_I16) {
         const cudaError_t e = prepare_intra_i16x2(p.warps_long, p.rows_long);
@@ -953,7 +968,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
         const void *ptrs[] = {d_queries, d_scores, d_hits, ws, st};
         put(ptrs, sizeof ptrs);
         const int32_t ints[] = {n_q, gap_open, gap_extend, top_k, plan.mode, plan.precision, plan.lanes, plan.rows,
-                                hits_out != nullptr};
+                                hits_out != nullptr, plan.rows_long, plan.warps_long};
         put(ints, sizeof ints);
         put(&plan.long_end_pair, sizeof plan.long_end_pair);
         if (n_q > 0) put(q_offsets, sizeof(int64_t) * size_t(n_q + 1));
