@@ -6,7 +6,11 @@ with the same entry-point names; it only marshals arguments.  There is no
 CPU fallback: if the library is missing, every call raises.
 """
 from .binding import (  # noqa: F401
+    ALIGNMENT_DTYPE,
     HIT_DTYPE,
+    SW_OP_D,
+    SW_OP_I,
+    SW_OP_M,
     SW_FLAG_GRAPH,
     SW_MODE_AUTO,
     SW_MODE_BATCHED,
@@ -18,6 +22,8 @@ from .binding import (  # noqa: F401
     Database,
     load_library,
     library_path,
+    sw_align,
+    sw_align_ops_capacity,
     sw_db_free,
     sw_db_get_info,
     sw_db_load,
