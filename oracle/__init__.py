@@ -11,6 +11,10 @@ of the ``synth`` module.
 - ``top_k``: the k best database entries of a score row, ordered by score
   descending and then database index ascending (the paper is silent on ties;
   this order is the reading this build takes).
+- ``score``/``score_pairs``/``all_scores`` with ``mode`` = "global",
+  "semiglobal" or "overlap": the textbook variants of the same recurrences
+  (first row and column, no zero floor, where the score is read) written
+  out in ``modes.c``.
 - ``align`` / ``align_pairs``: one optimal local alignment per pair, read
   off the same matrices by the traceback rules stated in ``traceback.c``
   (end cell first in row-major order; diagonal before E before F; a gap
@@ -31,7 +35,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "gotoh.c"), os.path.join(_HERE, "traceback.c")]
+_SRCS = [os.path.join(_HERE, "gotoh.c"), os.path.join(_HERE, "traceback.c"), os.path.join(_HERE, "modes.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libgotoh.so")
 _lock = threading.Lock()
@@ -39,7 +43,7 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile gotoh.c and traceback.c with gcc into oracle/_build/libgotoh.so."""
+    """Compile the oracle's C files with gcc into oracle/_build/libgotoh.so."""
     os.makedirs(_BUILD, exist_ok=True)
     newest = max(os.path.getmtime(x) for x in _SRCS)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
@@ -62,6 +66,11 @@ def _load():
             lib.swo_score_pairs.restype = ctypes.c_int
             lib.swo_score_pairs.argtypes = [p, p, p, p, p, p, i64, p, ctypes.c_int32, i64, i64,
                                             ctypes.c_int, p]
+            lib.swo_score_mode.restype = i64
+            lib.swo_score_mode.argtypes = [p, i64, p, i64, p, ctypes.c_int32, i64, i64, ctypes.c_int32]
+            lib.swo_score_pairs_mode.restype = ctypes.c_int
+            lib.swo_score_pairs_mode.argtypes = [p, p, p, p, p, p, i64, p, ctypes.c_int32, i64, i64, ctypes.c_int32,
+                                                 ctypes.c_int, p]
             lib.swo_align.restype = i64
             lib.swo_align.argtypes = [p, i64, p, i64, p, ctypes.c_int32, i64, i64, p, p, p]
             _lib = lib
@@ -78,8 +87,19 @@ def _matrix(S) -> np.ndarray:
     return S
 
 
-def score(q, t, S, gap_open: int, gap_extend: int) -> int:
-    """Local alignment score of query q against target t (uint8 codes)."""
+MODES = {"local": 0, "global": 1, "semiglobal": 2, "overlap": 3}
+
+
+def _mode(mode) -> int:
+    m = MODES.get(mode, mode) if isinstance(mode, str) else int(mode)
+    if m not in MODES.values():
+        raise ValueError(f"unknown alignment mode {mode!r}")
+    return m
+
+
+def score(q, t, S, gap_open: int, gap_extend: int, mode="local") -> int:
+    """Alignment score of query q against target t (uint8 codes); local
+    (Smith-Waterman) unless mode says otherwise."""
     lib = _load()
     q = np.ascontiguousarray(q, dtype=np.uint8)
     t = np.ascontiguousarray(t, dtype=np.uint8)
@@ -87,9 +107,17 @@ def score(q, t, S, gap_open: int, gap_extend: int) -> int:
     A = S.shape[0]
     if len(q) and int(q.max()) >= A or len(t) and int(t.max()) >= A:
         raise ValueError("residue code outside the matrix")
-    r = lib.swo_score(_ptr(q), len(q), _ptr(t), len(t), _ptr(S), A, int(gap_open), int(gap_extend))
-    if r < 0:
-        raise MemoryError("oracle scratch allocation failed")
+    md = _mode(mode)
+    qq = q if len(q) else np.zeros(1, np.uint8)
+    tt = t if len(t) else np.zeros(1, np.uint8)
+    if md == 0:
+        r = lib.swo_score(_ptr(qq), len(q), _ptr(tt), len(t), _ptr(S), A, int(gap_open), int(gap_extend))
+        if r < 0:
+            raise MemoryError("oracle scratch allocation failed")
+    else:
+        r = lib.swo_score_mode(_ptr(qq), len(q), _ptr(tt), len(t), _ptr(S), A, int(gap_open), int(gap_extend), md)
+        if r == np.iinfo(np.int64).min:
+            raise MemoryError("oracle scratch allocation failed")
     return int(r)
 
 
@@ -98,7 +126,7 @@ def default_threads() -> int:
 
 
 def score_pairs(queries, db, q_idx, t_idx, S, gap_open: int, gap_extend: int,
-                threads: int | None = None) -> np.ndarray:
+                threads: int | None = None, mode="local") -> np.ndarray:
     """Scores of the pairs (queries.seq(q_idx[k]), db.seq(t_idx[k])) as int64."""
     lib = _load()
     S = _matrix(S)
@@ -122,21 +150,29 @@ def score_pairs(queries, db, q_idx, t_idx, S, gap_open: int, gap_extend: int,
         qres = np.zeros(1, np.uint8)
     if tres.size == 0:
         tres = np.zeros(1, np.uint8)
-    rc = lib.swo_score_pairs(_ptr(qres), _ptr(qoff), _ptr(q_idx), _ptr(tres), _ptr(toff),
-                             _ptr(t_idx), len(q_idx), _ptr(S), A, int(gap_open), int(gap_extend),
-                             int(threads or default_threads()), _ptr(out))
-    if rc != 0 or (out < 0).any():
+    md = _mode(mode)
+    if md == 0:
+        rc = lib.swo_score_pairs(_ptr(qres), _ptr(qoff), _ptr(q_idx), _ptr(tres), _ptr(toff),
+                                 _ptr(t_idx), len(q_idx), _ptr(S), A, int(gap_open), int(gap_extend),
+                                 int(threads or default_threads()), _ptr(out))
+        bad = (out < 0).any()
+    else:
+        rc = lib.swo_score_pairs_mode(_ptr(qres), _ptr(qoff), _ptr(q_idx), _ptr(tres), _ptr(toff),
+                                      _ptr(t_idx), len(q_idx), _ptr(S), A, int(gap_open), int(gap_extend), md,
+                                      int(threads or default_threads()), _ptr(out))
+        bad = (out == np.iinfo(np.int64).min).any()
+    if rc != 0 or bad:
         raise MemoryError("oracle failed")
     return out
 
 
 def all_scores(queries, db, S, gap_open: int, gap_extend: int,
-               threads: int | None = None) -> np.ndarray:
+               threads: int | None = None, mode="local") -> np.ndarray:
     """(n_queries, n_db) matrix of scores, database in its original order."""
     nq, nt = queries.n, db.n
     qi = np.repeat(np.arange(nq, dtype=np.int64), nt)
     ti = np.tile(np.arange(nt, dtype=np.int64), nq)
-    return score_pairs(queries, db, qi, ti, S, gap_open, gap_extend, threads).reshape(nq, nt)
+    return score_pairs(queries, db, qi, ti, S, gap_open, gap_extend, threads, mode=mode).reshape(nq, nt)
 
 
 def top_k(scores_row, k: int):

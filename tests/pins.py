@@ -15,6 +15,10 @@ must equal in a special case:
 - ``enumerate_alignments``: every local alignment as an explicit list of
   columns, each gap column marked as opening its gap or extending it (the
   raw material of the traceback pins).
+- ``brute_force_global`` and the mode scores built on it: global,
+  semi-global and overlap scores as maxima over explicitly enumerated
+  end-to-end alignments of the right substrings.
+- ``levenshtein``: the classic edit distance (global score with unit costs).
 """
 from __future__ import annotations
 
@@ -151,3 +155,72 @@ def alignment_end(i0, j0, cols):
         if op in "MD":
             j += 1
     return i, j
+
+
+def brute_force_global(q, t, S, gap_open: int, gap_extend: int) -> int:
+    """Maximum over every end-to-end alignment of q against t, enumerated one
+    by one (columns M, I, D; a run of k gap columns of one kind costs open +
+    (k-1)*extend, and may be split into adjacent gaps priced open each, which
+    is what the recurrences give when open < extend)."""
+    q = [int(x) for x in q]
+    t = [int(x) for x in t]
+    m, n = len(q), len(t)
+    cont = min(gap_open, gap_extend)
+    best = None
+    sys.setrecursionlimit(max(1000, 10 * (m + n) + 100))
+
+    def dfs(i, j, last, score):
+        nonlocal best
+        if i == m and j == n:
+            best = score if best is None else max(best, score)
+            return
+        if i < m and j < n:
+            dfs(i + 1, j + 1, "M", score + int(S[q[i]][t[j]]))
+        if i < m:
+            dfs(i + 1, j, "I", score - (cont if last == "I" else gap_open))
+        if j < n:
+            dfs(i, j + 1, "D", score - (cont if last == "D" else gap_open))
+
+    dfs(0, 0, None, 0)
+    return best
+
+
+def brute_force_mode(q, t, S, gap_open: int, gap_extend: int, mode: str) -> int:
+    """Global: q against t end to end.  Semi-global: q end to end against any
+    substring t[j0:j1].  Overlap: q[i0:i1] against t[j0:j1] where the
+    alignment starts on the first row or column (i0 = 0 or j0 = 0) and ends
+    on the last row or column (i1 = m or j1 = n)."""
+    m, n = len(q), len(t)
+    if mode == "global":
+        return brute_force_global(q, t, S, gap_open, gap_extend)
+    if mode == "semiglobal":
+        return max(brute_force_global(q, t[j0:j1], S, gap_open, gap_extend)
+                   for j0 in range(n + 1) for j1 in range(j0, n + 1))
+    if mode == "overlap":
+        best = None
+        for i0 in range(m + 1):
+            for j0 in range(n + 1):
+                if i0 and j0:
+                    continue
+                for i1 in range(i0, m + 1):
+                    for j1 in range(j0, n + 1):
+                        if i1 != m and j1 != n:
+                            continue
+                        v = brute_force_global(q[i0:i1], t[j0:j1], S, gap_open, gap_extend)
+                        best = v if best is None else max(best, v)
+        return best
+    raise ValueError(mode)
+
+
+def levenshtein(a, b) -> int:
+    """Classic edit distance: D[i][j] = min(D[i-1][j] + 1, D[i][j-1] + 1,
+    D[i-1][j-1] + (a_i != b_j))."""
+    a = list(a)
+    b = list(b)
+    prev = list(range(len(b) + 1))
+    for i in range(1, len(a) + 1):
+        cur = [i] + [0] * len(b)
+        for j in range(1, len(b) + 1):
+            cur[j] = min(prev[j] + 1, cur[j - 1] + 1, prev[j - 1] + (a[i - 1] != b[j - 1]))
+        prev = cur
+    return prev[-1]
