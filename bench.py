@@ -44,6 +44,8 @@ UNIT = "GCUPS"
 # Minimum packed int16x2 DPX operations per cell update of the recurrences:
 # E, F, H (2), H-o, running max per cell pair = 5.5 per 2 cells.
 DPX_OPS_PER_CELL = 2.75
+I32_DPX_OPS_PER_CELL = 3.0
+ALIGNMENTS = {"local": 0, "global": 1, "semiglobal": 2, "overlap": 3}
 RESULT_TIMEOUT_S = 300.0   # a served request that takes longer than this is a failure
 
 
@@ -72,6 +74,8 @@ def parse_args(argv=None):
                    help="fraction of the 20M-sequence serving database (0.1 = 2M sequences)")
     p.add_argument("--serve-requests", type=int, default=96)
     p.add_argument("--serve-max-batch", type=int, default=16)
+    p.add_argument("--alignment", choices=["local", "global", "semiglobal", "overlap"], default="local",
+                   help="alignment mode of the search (local = Smith-Waterman, the paper's)")
     p.add_argument("--sweep", action="store_true",
                    help="GCUPS against query length: each query of the workload searched alone, at the "
                         "workload's gap penalties and at 10/2")
@@ -206,8 +210,10 @@ class ClockSampler:
 
 def launch_key(args) -> str:
     """The launch configuration a DRAM-traffic record was measured under."""
-    return (f"{args.workload}/scale{args.db_scale:g}/{args.mode}/lanes{args.lanes}/rows{args.rows}"
-            f"/prec{args.precision}/longrows{args.long_rows}/cutoff{args.long_cutoff}")
+    key = (f"{args.workload}/scale{args.db_scale:g}/{args.mode}/lanes{args.lanes}/rows{args.rows}"
+           f"/prec{args.precision}/longrows{args.long_rows}/cutoff{args.long_cutoff}")
+    alignment = getattr(args, "alignment", "local")
+    return key if alignment == "local" else key + f"/{alignment}"
 
 
 def traffic_per_launch(args):
@@ -230,7 +236,7 @@ def traffic_per_launch(args):
     return None
 
 
-def cpu_baseline(w, gpu_scores, seed: int, target_cells: float):
+def cpu_baseline(w, gpu_scores, seed: int, target_cells: float, mode: str = "local"):
     """Time the oracle (as it stands) on a bounded sample of the workload, on
     all host cores, and check the GPU's scores for the same pairs."""
     import oracle
@@ -246,7 +252,7 @@ def cpu_baseline(w, gpu_scores, seed: int, target_cells: float):
     cells = float((qlen[qi] * w.db.lengths[ti]).sum())
     threads = oracle.default_threads()
     t0 = time.perf_counter()
-    got = oracle.score_pairs(w.queries, w.db, qi, ti, w.matrix, w.gap_open, w.gap_extend, threads=threads)
+    got = oracle.score_pairs(w.queries, w.db, qi, ti, w.matrix, w.gap_open, w.gap_extend, threads=threads, mode=mode)
     dt = time.perf_counter() - t0
     exact = None
     if gpu_scores is not None:
@@ -279,7 +285,8 @@ def run_ours(args, dist: Dist):
     hits = torch.empty((nq, w.top_k, 2), dtype=torch.int64, device=f"cuda:{dev}")
     kw = dict(lanes=args.lanes, rows_per_lane=args.rows, precision=args.precision, long_rows_per_lane=args.long_rows,
               long_cutoff=args.long_cutoff,
-              mode=swdb.SW_MODE_BATCHED if args.mode == "batched" else swdb.SW_MODE_PLAIN)
+              mode=swdb.SW_MODE_BATCHED if args.mode == "batched" else swdb.SW_MODE_PLAIN,
+              alignment=ALIGNMENTS[args.alignment])
 
     def step(stats=True):
         return swdb.sw_search(db.handle, q_dev, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend, w.top_k,
@@ -330,19 +337,22 @@ def run_ours(args, dist: Dist):
         rate_dpx, sms = swdb.sw_probe_alu_rate(dev, 0)
         rate_cells, _ = swdb.sw_probe_alu_rate(dev, 1)
         mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
-        peak = rate_dpx * sms * mhz * 1e6 / DPX_OPS_PER_CELL / 1e9
+        local = args.alignment == "local"
+        ops_per_cell = DPX_OPS_PER_CELL if local else I32_DPX_OPS_PER_CELL
+        peak = rate_dpx * sms * mhz * 1e6 / ops_per_cell / 1e9
         ceiling = rate_cells * sms * mhz * 1e6 / 1e9
         inter_cells = float(sum(s["inter_cells"] for s in st_all))
         achieved = inter_cells / (inter_ms * 1e-3) / 1e9 if inter_ms > 0 else 0.0
         traffic = traffic_per_launch(args)
         cb = None
         if not args.no_cpu_baseline:
-            cb = cpu_baseline(w, scores.cpu().numpy(), seed + 1, args.cpu_sample_cells)
+            cb = cpu_baseline(w, scores.cpu().numpy(), seed + 1, args.cpu_sample_cells, mode=args.alignment)
         out = {
             "metric": METRIC, "value": gcups, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "i16x2", "data": "synthetic",
-            "config": {"workload": args.workload, "queries": nq, "query_residues": int(w.queries.lengths.sum()),
+            "scaling": "weak", "vs_baseline": None, "dtype": "i16x2" if local else "i32", "data": "synthetic",
+            "config": {"workload": args.workload, "alignment": args.alignment, "queries": nq,
+                       "query_residues": int(w.queries.lengths.sum()),
                        "db_seqs": n, "db_residues": int(w.db.lengths.sum()), "cells_per_step": cells_step,
                        "matrix": "BLOSUM62", "gap_open": w.gap_open, "gap_extend": w.gap_extend,
                        "top_k": w.top_k,
@@ -356,9 +366,10 @@ def run_ours(args, dist: Dist):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
                          "frac": achieved / peak if peak else None,
                          "traffic": traffic,
-                         "kernel": "k_inter_i16x2",
-                         "peak_basis": f"measured {rate_dpx:.1f} int16x2 DPX ops/SM/cycle x {sms} SMs x "
-                                       f"{mhz:.0f} MHz (median under load) / {DPX_OPS_PER_CELL} ops per cell",
+                         "kernel": "k_inter_i16x2" if local else "k_modes_i32",
+                         "peak_basis": f"measured {rate_dpx:.1f} DPX ops/SM/cycle x {sms} SMs x "
+                                       f"{mhz:.0f} MHz (median under load) / {ops_per_cell} ops per cell"
+                                       + ("" if local else " (int32: E, F and H, one cell per operation)"),
                          "register_only_ceiling_gcups": ceiling,
                          "avg_launch_ms": inter_ms / max(inter_launches, 1)},
             "cpu_baseline": cb,

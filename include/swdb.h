@@ -75,6 +75,28 @@ typedef enum {
     SW_MODE_BATCHED = 2  /* all queries in one persistent launch */
 } sw_mode;
 
+/* Which alignment score sw_search computes.  Section 2.2 defines the local
+ * (Smith-Waterman) score, the paper's subject; SW# also offers global and
+ * semi-global modes (Section 2.3) and the paper leaves other alignment
+ * operations to future work (Section 5).  The other modes use the same
+ * Gotoh recurrences without the zero floor of H; with g(k) = o +
+ * (k-1)*min(o, e) (the first column's own recurrence, o + (k-1)e when
+ * o >= e):
+ *   GLOBAL      H(i,0) = -g(i), H(0,j) = -g(j); score H(m,n)
+ *   SEMIGLOBAL  the whole query against any part of the target:
+ *               H(i,0) = -g(i), H(0,j) = 0; score max over j of H(m,j)
+ *   OVERLAP     end gaps free on both: H(i,0) = H(0,j) = 0;
+ *               score max(max_j H(m,j), max_i H(i,n))
+ * Their scores can be negative; they are computed in exact int32 (the
+ * precision and mode options do not apply) and require
+ * (m + n) * (max|S| + o + e) < 2^28 for every pair (else SW_ERR_OVERFLOW). */
+typedef enum {
+    SW_ALIGN_LOCAL = 0,
+    SW_ALIGN_GLOBAL = 1,
+    SW_ALIGN_SEMIGLOBAL = 2,
+    SW_ALIGN_OVERLAP = 3
+} sw_alignment_mode;
+
 /* Optional knobs for sw_search (pass NULL for defaults).  Zero-initialise
  * and set the fields you need. */
 typedef struct {
@@ -90,7 +112,9 @@ typedef struct {
     int32_t flags;            /* SW_FLAG_* bits */
     int32_t long_rows_per_lane; /* query rows per lane of the intra-task kernel: 16 (4-warp
                                    pipelines) or 32 (2-warp pipelines); 0 = library choice */
-} sw_search_opts;
+    int32_t alignment;        /* sw_alignment_mode; 0 = local */
+    int32_t reserved;
+} sw_search_opts;             /* 56 bytes */
 
 /* Capture the device work of the search into a CUDA graph on first use and
  * replay it while the call's signature (buffers, query lengths, matrix,
@@ -193,9 +217,10 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
 
 /*
  * Top-k of score rows already on the device (the last step of sw_search,
- * exposed on its own).  scores: device pointer, n_rows x n_cols int32 (>= 0);
- * hits: device pointer, n_rows x top_k; order score descending, then column
- * ascending; missing entries {-1, -1}.  top_k <= 4096.
+ * exposed on its own).  scores: device pointer, n_rows x n_cols int32 (any
+ * value); hits: device pointer, n_rows x top_k; order score descending, then
+ * column ascending; missing entries (top_k > n_cols) have db_index -1 and
+ * score -1.  top_k <= 4096.
  */
 int sw_top_k(const int32_t *scores, int64_t n_rows, int64_t n_cols, int32_t top_k,
              sw_hit *hits, void *stream);

@@ -8,6 +8,10 @@ CPU fallback: if the library is missing, every call raises.
 from .binding import (  # noqa: F401
     ALIGNMENT_DTYPE,
     HIT_DTYPE,
+    SW_ALIGN_GLOBAL,
+    SW_ALIGN_LOCAL,
+    SW_ALIGN_OVERLAP,
+    SW_ALIGN_SEMIGLOBAL,
     SW_OP_D,
     SW_OP_I,
     SW_OP_M,

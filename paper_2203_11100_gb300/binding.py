@@ -19,6 +19,7 @@ SW_OK = 0
 SW_PREC_AUTO, SW_PREC_I16, SW_PREC_I32 = 0, 1, 2
 SW_MODE_AUTO, SW_MODE_PLAIN, SW_MODE_BATCHED = 0, 1, 2
 SW_FLAG_GRAPH = 1
+SW_ALIGN_LOCAL, SW_ALIGN_GLOBAL, SW_ALIGN_SEMIGLOBAL, SW_ALIGN_OVERLAP = 0, 1, 2, 3
 
 HIT_DTYPE = np.dtype([("score", "<i4"), ("reserved", "<i4"), ("db_index", "<i8")])
 SW_OP_M, SW_OP_I, SW_OP_D = 0, 1, 2
@@ -39,7 +40,7 @@ class SwSearchOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("mode", ctypes.c_int32), ("long_cutoff", ctypes.c_int64),
                 ("lanes", ctypes.c_int32), ("rows_per_lane", ctypes.c_int32),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t), ("flags", ctypes.c_int32),
-                ("long_rows_per_lane", ctypes.c_int32)]
+                ("long_rows_per_lane", ctypes.c_int32), ("alignment", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class SwSearchStats(ctypes.Structure):
@@ -166,8 +167,10 @@ def sw_db_get_info(handle) -> dict:
     return {f: getattr(info, f) for f, _ in SwDbInfo._fields_}
 
 
-def _opts(precision, mode, long_cutoff, lanes, rows_per_lane, workspace, flags=0, long_rows_per_lane=0):
+def _opts(precision, mode, long_cutoff, lanes, rows_per_lane, workspace, flags=0, long_rows_per_lane=0,
+          alignment=SW_ALIGN_LOCAL):
     o = SwSearchOpts()
+    o.alignment = alignment
     o.flags = flags
     o.long_rows_per_lane = long_rows_per_lane
     o.precision = precision
@@ -185,9 +188,10 @@ def _opts(precision, mode, long_cutoff, lanes, rows_per_lane, workspace, flags=0
 
 
 def sw_search_workspace_size(handle, q_offsets, top_k: int, precision=SW_PREC_AUTO, mode=SW_MODE_AUTO,
-                             long_cutoff=0, lanes=0, rows_per_lane=0, long_rows_per_lane=0) -> int:
+                             long_cutoff=0, lanes=0, rows_per_lane=0, long_rows_per_lane=0,
+                             alignment=SW_ALIGN_LOCAL) -> int:
     q_offsets = np.ascontiguousarray(q_offsets, dtype=np.int64)
-    o = _opts(precision, mode, long_cutoff, lanes, rows_per_lane, None, 0, long_rows_per_lane)
+    o = _opts(precision, mode, long_cutoff, lanes, rows_per_lane, None, 0, long_rows_per_lane, alignment)
     n = ctypes.c_size_t()
     _check(load_library().sw_search_workspace_size(handle, q_offsets.ctypes.data, len(q_offsets) - 1, top_k,
                                                    ctypes.byref(o), ctypes.byref(n)))
@@ -197,7 +201,7 @@ def sw_search_workspace_size(handle, q_offsets, top_k: int, precision=SW_PREC_AU
 def sw_search(handle, queries, q_offsets, matrix, gap_open: int, gap_extend: int, top_k: int,
               scores_out=None, hits_out=None, precision=SW_PREC_AUTO, mode=SW_MODE_AUTO, long_cutoff=0,
               lanes=0, rows_per_lane=0, workspace=None, stats: bool = False, stream=None, graph: bool = False,
-              long_rows_per_lane=0):
+              long_rows_per_lane=0, alignment=SW_ALIGN_LOCAL):
     """Run sw_search.  Outputs are written into scores_out / hits_out (numpy =
     host, torch CUDA tensor = device).  Returns a stats dict when stats=True."""
     lib = load_library()
@@ -209,7 +213,7 @@ def sw_search(handle, queries, q_offsets, matrix, gap_open: int, gap_extend: int
         raise TypeError("hits_out must have dtype HIT_DTYPE")
     hp, h_cuda = _addr(hits_out, None, "hits_out")
     o = _opts(precision, mode, long_cutoff, lanes, rows_per_lane, workspace, SW_FLAG_GRAPH if graph else 0,
-              long_rows_per_lane)
+              long_rows_per_lane, alignment)
     st = SwSearchStats() if stats else None
     if stream is None and (q_cuda or s_cuda or h_cuda or workspace is not None):
         import torch

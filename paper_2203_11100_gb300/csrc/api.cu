@@ -230,6 +230,10 @@ struct Plan {
     int32_t inter_min_lanes = 8;     // sets the most pairs per CTA
     int32_t inter_max_cols = 0;      // columns of the longest non-long pair
     bool inter_scratch = false;
+    // non-local alignment modes (k_modes.cu)
+    int32_t alignment = SW_ALIGN_LOCAL;
+    int32_t mode_grid = 0;           // persistent CTAs
+    int64_t mode_mpad = 0;           // profile rows, a multiple of the 256-row strip
 };
 
 // Choose arithmetic and launch shapes for this call.
@@ -258,6 +262,24 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
     const int64_t span = std::min<int64_t>(p.max_m, db->max_len) * std::max<int64_t>(smax, 0);
     if (absmax > (1 << 20) || int64_t(o) + e > (1 << 28) || span + int64_t(o) + e + absmax > (int64_t(1) << 30))
         return fail(SW_ERR_OVERFLOW, "matrix entries, penalties or lengths too large for exact int32 scores");
+
+    const int32_t alignment = opts ? opts->alignment : SW_ALIGN_LOCAL;
+    if (alignment < SW_ALIGN_LOCAL || alignment > SW_ALIGN_OVERLAP)
+        return fail(SW_ERR_INVALID_ARG, "unknown alignment mode");
+    if (alignment != SW_ALIGN_LOCAL) {
+        // No zero floor: values go down to about -(m + n) * (max|S| + o + e).
+        if ((int64_t(p.max_m) + db->max_len) * (absmax + int64_t(o) + e) >= (int64_t(1) << 28))
+            return fail(SW_ERR_OVERFLOW, "lengths, matrix entries or penalties too large for exact int32 "
+                                         "scores of this alignment mode");
+        p.alignment = alignment;
+        p.precision = SW_PREC_I32;
+        p.mode = SW_MODE_PLAIN;
+        p.mode_grid = modes_slots(std::max(1, db->sm_count));
+        if (p.mode_grid <= 0) return fail(SW_ERR_CUDA, "could not size the alignment-mode grid");
+        p.mode_mpad = round_up(std::max<int64_t>(p.max_m, 1), modes_strip_rows());
+        *plan = std::move(p);
+        return SW_OK;
+    }
 
     // int16x2 with int8 profile: S + o must fit int8, and o, e small enough
     // that no shifted value leaves int16 (see k_inter16.cu).
@@ -439,6 +461,8 @@ struct Buffers {
     int32_t *qp = nullptr;            // batched mode: qp_a then qp_b
     uint2 *batch_scratch = nullptr;   // batched mode: per CTA slot boundary rows
     uint2 *inter_scratch = nullptr;   // plain mode: per CTA slot boundary rows
+    int32_t *mode_prof = nullptr;     // alignment modes: [32][mode_mpad] S(q_i, c)
+    int2 *mode_bnd = nullptr;         // alignment modes: per warp slot, max_len + 1 (H, F)
     int32_t *ovf_list = nullptr;
     int32_t *counters = nullptr;   // [n_q] list lengths, [n_q] work counters, [n_q] flagged sequences,
                                    // then one status word
@@ -471,6 +495,11 @@ size_t carve(const sw_db *db, const Plan &p, int32_t n_q, int32_t top_k, bool q_
         x.inter_scratch = static_cast<uint2 *>(c.take(sizeof(uint2) * size_t(p.inter_grid_max) *
                                                       size_t(kCtaThreads / p.inter_min_lanes) *
                                                       size_t(p.inter_max_cols)));
+    if (p.alignment != SW_ALIGN_LOCAL) {
+        x.mode_prof = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(kProfRows) * size_t(p.mode_mpad)));
+        x.mode_bnd = static_cast<int2 *>(c.take(sizeof(int2) * size_t(p.mode_grid) * size_t(kCtaThreads / 32) *
+                                                size_t(db->max_len + 1)));
+    }
     // [n_q] list lengths, [n_q] work counters, [n_q] flagged, [n_q] chunk counters,
     // status, 4 tile counters
     x.counters = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(4 * std::max<int32_t>(n_q, 1) + 5)));
@@ -822,6 +851,37 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
     auto enqueue = [&]() -> int {
     SW_CUDA_TRY(cudaMemsetAsync(buf.counters, 0, sizeof(int32_t) * (4 * size_t(std::max<int32_t>(n_q, 1)) + 5), st));
 
+    if (plan.alignment != SW_ALIGN_LOCAL) {
+        // Non-local modes: per query, its profile S(q_i, c) and one persistent
+        // launch over every sequence (k_modes.cu), then the top-k.
+        for (int32_t qi = 0; qi < n_q; ++qi) {
+            const int64_t q0 = q_offsets[qi];
+            const int32_t m = int32_t(q_offsets[qi + 1] - q0);
+            if (m > 0)
+                TIMED(LaunchTimer::OTHER, launch_profile32(d_queries + q0, m, int32_t(plan.mode_mpad), matrix, db->A,
+                                                           0, buf.mode_prof, st));
+            ModeArgs ma;
+            memset(&ma, 0, sizeof ma);
+            ma.db = db->view();
+            ma.seq_begin = 0;
+            ma.seq_end = db->n_sorted;
+            ma.prof = buf.mode_prof;
+            ma.m = m;
+            ma.m_pad = int32_t(plan.mode_mpad);
+            ma.gap_open = gap_open;
+            ma.gap_extend = gap_extend;
+            ma.mode = plan.alignment;
+            ma.max_cols = int32_t(db->max_len);
+            ma.boundary = buf.mode_bnd;
+            ma.work_counter = buf.counters + n_q + qi;
+            ma.scores = d_scores + int64_t(qi) * db->n_seqs;
+            TIMED(LaunchTimer::INTER, launch_modes_i32(ma, plan.mode_grid, st));
+        }
+        if (top_k > 0 && n_q > 0 && (hits_out != nullptr))
+            TIMED(LaunchTimer::OTHER, launch_topk(d_scores, n_q, db->n_seqs, top_k, d_hits, st));
+        return SW_OK;
+    }
+
     // (1) Long sequences of every query: one intra-task launch on the side
     //     stream, concurrent with the per-query launches below.
     if (split) {
@@ -968,7 +1028,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
         const void *ptrs[] = {d_queries, d_scores, d_hits, ws, st};
         put(ptrs, sizeof ptrs);
         const int32_t ints[] = {n_q, gap_open, gap_extend, top_k, plan.mode, plan.precision, plan.lanes, plan.rows,
-                                hits_out != nullptr, plan.rows_long, plan.warps_long};
+                                hits_out != nullptr, plan.rows_long, plan.warps_long, plan.alignment};
         put(ints, sizeof ints);
         put(&plan.long_end_pair, sizeof plan.long_end_pair);
         if (n_q > 0) put(q_offsets, sizeof(int64_t) * size_t(n_q + 1));

@@ -1,0 +1,173 @@
+// Global, semi-global and overlap scores of one query against the database:
+// the non-local alignment modes (SW# offers them besides local, Section 2.3;
+// the paper leaves other alignment operations to future work, Section 5).
+// Same Gotoh recurrences as the local kernels (Section 2.2, affine gaps of
+// Section 4.1) without the zero floor of H; the modes differ only in the
+// first row and column and in the cells the score is read from:
+//
+//   global       H(i,0) = -g(i), H(0,j) = -g(j);  score H(m,n)
+//   semi-global  H(i,0) = -g(i), H(0,j) = 0;     score max_j H(m,j)
+//   overlap      H(i,0) = H(0,j) = 0;            score max(max_j H(m,j), max_i H(i,n))
+//
+// with g(k) = o + (k-1)*min(o,e), the first column's own recurrence from
+// H(0,0) = 0.  Scores can be negative, so these modes run in exact int32
+// (the host rejects inputs whose values could leave +-2^29).
+//
+// One warp per database sequence: lane k holds query rows 8k+1 .. 8k+8 of a
+// 256-row strip and runs one column behind lane k-1 (H and F of a lane's
+// bottom row reach the next lane by shuffle).  The query profile S(q_i, c)
+// is a global [code][row] table (it stays in L1/L2); a lane reads its 8 rows
+// for the current target code with two 16-byte loads.  Between strips the
+// bottom row (H, F per column) goes through this warp slot's scratch row in
+// global memory, rewritten in place: lane 31 writes column j - 30 while lane
+// 0 reads column j + 1, so a column is always read before it is rewritten.
+// Warps take sequences from an atomic counter, longest first.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/swdb.h"
+#include "swdb_internal.cuh"
+
+namespace swdb {
+namespace {
+
+constexpr int kMR = 8;                   // query rows per lane
+constexpr int kMStrip = 32 * kMR;        // rows per strip
+constexpr int32_t kMNeg = -(1 << 30);    // -infinity of E and F
+
+__device__ __forceinline__ int32_t lead_gap(int64_t k, int32_t o, int32_t gmin) {
+    return k <= 0 ? 0 : int32_t(o + (k - 1) * int64_t(gmin));
+}
+
+// H(i, 0) of the mode
+__device__ __forceinline__ int32_t col0(int mode, int64_t i, int32_t o, int32_t gmin) {
+    return mode == SW_ALIGN_OVERLAP ? 0 : -lead_gap(i, o, gmin);
+}
+
+__global__ void __launch_bounds__(kCtaThreads) k_modes_i32(const __grid_constant__ ModeArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int warp_slot = blockIdx.x * (kCtaThreads / 32) + (threadIdx.x >> 5);
+    int2 *bnd = a.boundary + int64_t(warp_slot) * (a.max_cols + 1);
+    const int mode = a.mode;
+    const int32_t o = a.gap_open, e = a.gap_extend, gmin = e < o ? e : o;
+    const int m = a.m;
+    const int64_t count = a.seq_end - a.seq_begin;
+
+    for (;;) {
+        int64_t item = 0;
+        if (lane == 0) item = atomicAdd(a.work_counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= count) break;
+        const int64_t s = a.seq_begin + item;
+        const int64_t orig = a.db.perm[s];
+        if (orig < 0) continue;                              // padding slot of the last bundle
+        const int n = a.db.len[s];
+        if (m == 0 || n == 0) {
+            if (lane == 0) {
+                int32_t v = 0;
+                if (mode == SW_ALIGN_GLOBAL) v = -lead_gap(m == 0 ? n : m, o, gmin);
+                else if (mode == SW_ALIGN_SEMIGLOBAL) v = (n == 0) ? -lead_gap(m, o, gmin) : 0;
+                a.scores[orig] = v;
+            }
+            continue;
+        }
+        const uint8_t *tb = a.db.codes + a.db.bundle_off[s / kBundleSeqs] + int((s % kBundleSeqs) >> 1) * kQuadBytes +
+                            int(s & 1);
+        int32_t last_row = kMNeg;      // max over j >= 1 of H(m, j) (the lane holding row m)
+        int32_t last_col = kMNeg;      // max over rows <= m of H(i, n)
+        int32_t hmn = kMNeg;           // H(m, n)
+        for (int r0 = 0; r0 < m; r0 += kMStrip) {
+            __syncwarp();                                    // last strip's boundary writes are visible
+            const int row0 = r0 + lane * kMR + 1;            // 1-based first row of this lane
+            int32_t H[kMR], E[kMR];
+#pragma unroll
+            for (int r = 0; r < kMR; ++r) {
+                H[r] = col0(mode, row0 + r, o, gmin);        // H(i, 0)
+                E[r] = kMNeg;                                // E(i, 0)
+            }
+            int32_t hd = (row0 - 1 == 0) ? 0 : col0(mode, row0 - 1, o, gmin);   // H(row0-1, 0)
+            int32_t pub_h = 0, pub_f = kMNeg;
+            const bool more = r0 + kMStrip < m;
+            const int rm = m - row0;                         // index of row m in this lane, if 0..7
+            const int32_t *prow = a.prof + r0 + lane * kMR;
+            for (int st = 0; st < n + 31; ++st) {
+                int32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1);
+                int32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1);
+                const int j = st - lane + 1;
+                if (j >= 1 && j <= n) {
+                    if (lane == 0) {
+                        if (r0 == 0) {                       // H(0, j), F(0, j)
+                            hin = (mode == SW_ALIGN_GLOBAL) ? -lead_gap(j, o, gmin) : 0;
+                            fin = kMNeg;
+                        } else {
+                            const int2 v = bnd[j];
+                            hin = v.x;
+                            fin = v.y;
+                        }
+                    }
+                    const int c = tb[int64_t((j - 1) >> 2) * kBundleRowBytes + ((j - 1) & 3) * 2];
+                    const int4 *pp = reinterpret_cast<const int4 *>(prow + int64_t(c) * a.m_pad);
+                    const int4 p0 = __ldg(pp), p1 = __ldg(pp + 1);
+                    const int32_t sc[kMR] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+                    int32_t f = fin, up = hin, d = hd, hm = kMNeg;
+#pragma unroll
+                    for (int r = 0; r < kMR; ++r) {
+                        const int32_t e_r = __viaddmax_s32(E[r], -e, H[r] - o);   // E(i,j)
+                        f = __viaddmax_s32(f, -e, up - o);                         // F(i,j)
+                        const int32_t h = __vimax3_s32(d + sc[r], e_r, f);         // H(i,j)
+                        d = H[r];
+                        E[r] = e_r;
+                        H[r] = h;
+                        up = h;
+                        if (r == rm) hm = h;
+                    }
+                    last_row = max(last_row, hm);
+                    if (j == n) {
+                        int32_t lc = kMNeg;
+#pragma unroll
+                        for (int r = 0; r < kMR; ++r)
+                            if (row0 + r <= m) lc = max(lc, H[r]);
+                        last_col = max(last_col, lc);
+                        if (hm != kMNeg) hmn = hm;
+                    }
+                    hd = hin;
+                    pub_h = H[kMR - 1];
+                    pub_f = f;
+                    if (more && lane == 31) bnd[j] = make_int2(H[kMR - 1], f);
+                }
+            }
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            last_row = max(last_row, __shfl_xor_sync(0xffffffffu, last_row, off));
+            last_col = max(last_col, __shfl_xor_sync(0xffffffffu, last_col, off));
+            hmn = max(hmn, __shfl_xor_sync(0xffffffffu, hmn, off));
+        }
+        if (lane == 0) {
+            int32_t v;
+            if (mode == SW_ALIGN_GLOBAL) v = hmn;
+            else if (mode == SW_ALIGN_SEMIGLOBAL) v = max(last_row, -lead_gap(m, o, gmin));   // j = 0 too
+            else v = max(max(last_row, last_col), 0);          // H(m,0) = H(0,n) = 0
+            a.scores[orig] = v;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_modes_i32(const ModeArgs &a, int grid, cudaStream_t s) {
+    if (a.seq_end <= a.seq_begin) return cudaSuccess;
+    k_modes_i32<<<grid, kCtaThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int modes_slots(int sms) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_modes_i32, kCtaThreads, 0) != cudaSuccess)
+        return 0;
+    return per_sm * sms;
+}
+
+int32_t modes_strip_rows() { return kMStrip; }
+
+}  // namespace swdb

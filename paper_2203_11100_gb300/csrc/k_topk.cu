@@ -2,7 +2,11 @@
 // score descending and then database index ascending (the paper does not
 // say how ties are ordered; this order is the library's convention).
 //
-// One CTA per row.  (1) A radix select over the 32-bit scores, 8 bits per
+// Scores are signed (the non-local alignment modes give negative ones); the
+// kernel orders the keys v = score XOR 0x80000000 as unsigned, which keeps
+// the order of signed values.
+//
+// One CTA per row.  (1) A radix select over the 32-bit keys, 8 bits per
 // round, finds the k-th largest score tau and how many ties with tau are
 // needed.  (2) One ordered sweep over the row collects every score > tau
 // (any order) and the first `need` entries equal to tau in index order
@@ -41,7 +45,7 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const int32_t *scores, in
     while (P < kk) P <<= 1;
     for (int i = tid; i < P; i += kTopkThreads) keys[i] = 0ull;
 
-    // (1) radix select of the kk-th largest score (all scores >= 0).
+    // (1) radix select of the kk-th largest key.
     uint32_t prefix = 0, pmask = 0;
     uint32_t remaining = uint32_t(kk);
     bool take_all = (int64_t(kk) == n_cols);
@@ -50,7 +54,7 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const int32_t *scores, in
             for (int i = tid; i < 256; i += kTopkThreads) hist[i] = 0;
             __syncthreads();
             for (int64_t i = tid; i < n_cols; i += kTopkThreads) {
-                const uint32_t v = uint32_t(s[i]);
+                const uint32_t v = uint32_t(s[i]) ^ 0x80000000u;
                 if ((v & pmask) == prefix) atomicAdd(&hist[(v >> shift) & 255u], 1u);
             }
             __syncthreads();
@@ -84,7 +88,7 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const int32_t *scores, in
             const int64_t i = base + tid;
             uint32_t v = 0;
             bool in = i < n_cols;
-            if (in) v = uint32_t(s[i]);
+            if (in) v = uint32_t(s[i]) ^ 0x80000000u;
             const unsigned long long key =
                 (static_cast<unsigned long long>(v) << 32) | (0xffffffffull - uint64_t(i));
             bool is_eq = false;
@@ -138,7 +142,7 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(const int32_t *scores, in
         h.reserved = 0;
         if (i < kk) {
             const unsigned long long key = keys[i];
-            h.score = int32_t(key >> 32);
+            h.score = int32_t(uint32_t(key >> 32) ^ 0x80000000u);
             h.db_index = int64_t(0xffffffffull - (key & 0xffffffffull));
         } else {
             h.score = -1;

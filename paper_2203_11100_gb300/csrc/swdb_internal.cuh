@@ -164,6 +164,21 @@ struct AlignArgs {
     int32_t gap_open, gap_extend;
 };
 
+// Non-local alignment modes (k_modes.cu): one query against the sorted
+// sequences [seq_begin, seq_end), one warp per sequence.
+struct ModeArgs {
+    DbView db;
+    int64_t seq_begin, seq_end;
+    const int32_t *prof;        // [kProfRows][m_pad] = S(q_i, c), pads -2^28
+    int32_t m, m_pad;           // m_pad a multiple of 256
+    int32_t gap_open, gap_extend;
+    int32_t mode;               // SW_ALIGN_GLOBAL / SEMIGLOBAL / OVERLAP
+    int32_t max_cols;           // longest sequence; each warp slot owns max_cols + 1 int2
+    int2 *boundary;             // grid * 8 warp slots
+    int32_t *work_counter;      // zeroed before launch
+    int32_t *scores;            // row of this query, original database order
+};
+
 // Launchers (return cudaGetLastError() after the launch).
 // grid_slots > 0 launches a persistent grid of that many CTAs (slot-layout
 // scratch); 0 launches one CTA per chunk of pairs (per-pair scratch).
@@ -184,6 +199,9 @@ bool i32_config_supported(int lanes, int rows);
 cudaError_t launch_probe(int mode, int grid, int iters, unsigned long long *cycles, uint32_t *sink,
                          cudaStream_t s);
 int probe_blocks_per_sm(int mode);
+cudaError_t launch_modes_i32(const ModeArgs &a, int grid, cudaStream_t s);
+int modes_slots(int sms);            // resident CTAs of the modes kernel
+int32_t modes_strip_rows();
 cudaError_t launch_align(const AlignArgs &a, int which, cudaStream_t s);   // 0 forward, 1 traceback
 int64_t align_checkpoint_rows(int32_t m);
 int32_t align_strip_rows();

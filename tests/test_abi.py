@@ -99,3 +99,21 @@ def test_alignment_struct_sizes():
     from paper_2203_11100_gb300 import binding
     assert binding.ALIGNMENT_DTYPE.itemsize == 56
     assert ctypes.sizeof(binding.SwAlignStats) == 32
+
+
+def test_struct_sizes_match_the_header(tmp_path):
+    """The binding's structs have the sizes the C compiler gives the header's."""
+    import subprocess
+    from paper_2203_11100_gb300 import binding
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include "swdb.h"\nint main(void) {\n'
+                   '  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(sw_search_opts), sizeof(sw_search_stats),\n'
+                   '         sizeof(sw_alignment), sizeof(sw_align_stats), sizeof(sw_hit), sizeof(sw_db_info));\n'
+                   '  return 0;\n}\n')
+    exe = tmp_path / "sizes"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    want = [ctypes.sizeof(binding.SwSearchOpts), ctypes.sizeof(binding.SwSearchStats),
+            binding.ALIGNMENT_DTYPE.itemsize, ctypes.sizeof(binding.SwAlignStats), binding.HIT_DTYPE.itemsize,
+            ctypes.sizeof(binding.SwDbInfo)]
+    assert got == want
