@@ -461,7 +461,7 @@ struct Buffers {
     int32_t *qp = nullptr;            // batched mode: qp_a then qp_b
     uint2 *batch_scratch = nullptr;   // batched mode: per CTA slot boundary rows
     uint2 *inter_scratch = nullptr;   // plain mode: per CTA slot boundary rows
-    int32_t *mode_prof = nullptr;     // alignment modes: [32][mode_mpad] S(q_i, c)
+    int32_t *mode_prof = nullptr;     // alignment modes: [32][mode_mpad] S(q_i, c) + o
     int2 *mode_bnd = nullptr;         // alignment modes: per warp slot, max_len + 1 (H, F)
     int32_t *ovf_list = nullptr;
     int32_t *counters = nullptr;   // [n_q] list lengths, [n_q] work counters, [n_q] flagged sequences,
@@ -852,14 +852,14 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
     SW_CUDA_TRY(cudaMemsetAsync(buf.counters, 0, sizeof(int32_t) * (4 * size_t(std::max<int32_t>(n_q, 1)) + 5), st));
 
     if (plan.alignment != SW_ALIGN_LOCAL) {
-        // Non-local modes: per query, its profile S(q_i, c) and one persistent
+        // Non-local modes: per query, its profile S(q_i, c) + o and one persistent
         // launch over every sequence (k_modes.cu), then the top-k.
         for (int32_t qi = 0; qi < n_q; ++qi) {
             const int64_t q0 = q_offsets[qi];
             const int32_t m = int32_t(q_offsets[qi + 1] - q0);
             if (m > 0)
                 TIMED(LaunchTimer::OTHER, launch_profile32(d_queries + q0, m, int32_t(plan.mode_mpad), matrix, db->A,
-                                                           0, buf.mode_prof, st));
+                                                           gap_open, buf.mode_prof, st));
             ModeArgs ma;
             memset(&ma, 0, sizeof ma);
             ma.db = db->view();

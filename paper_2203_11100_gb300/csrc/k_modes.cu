@@ -15,15 +15,19 @@
 //
 // One warp per database sequence: lane k holds query rows 8k+1 .. 8k+8 of a
 // 256-row strip and runs one column behind lane k-1 (H and F of a lane's
-// bottom row reach the next lane by shuffle).  The query profile S(q_i, c)
+// bottom row reach the next lane by shuffle).  The query profile S(q_i, c) + o
 // is a global [code][row] table (it stays in L1/L2); a lane reads its 8 rows
-// for the current target code with two 16-byte loads.  Between strips the
+// for the current target code with two 16-byte loads.  Only the strip that
+// holds row m picks out H(m, j) (a compile-time variant of the strip loop).  Between strips the
 // bottom row (H, F per column) goes through this warp slot's scratch row in
-// global memory, rewritten in place: lane 31 writes column j - 30 while lane
+// global memory (H - o of the strip's last row and F of the row below),
+// rewritten in place: lane 31 writes column j - 30 while lane
 // 0 reads column j + 1, so a column is always read before it is rewritten.
 // Warps take sequences from an atomic counter, longest first.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "../../include/swdb.h"
 #include "swdb_internal.cuh"
@@ -76,30 +80,38 @@ __global__ void __launch_bounds__(kCtaThreads) k_modes_i32(const __grid_constant
         int32_t last_row = kMNeg;      // max over j >= 1 of H(m, j) (the lane holding row m)
         int32_t last_col = kMNeg;      // max over rows <= m of H(i, n)
         int32_t hmn = kMNeg;           // H(m, n)
-        for (int r0 = 0; r0 < m; r0 += kMStrip) {
+        auto strip = [&](const int r0, auto last_c) {
+            constexpr bool LAST = decltype(last_c)::value;   // this strip holds row m
             __syncwarp();                                    // last strip's boundary writes are visible
             const int row0 = r0 + lane * kMR + 1;            // 1-based first row of this lane
-            int32_t H[kMR], E[kMR];
+            // Registers carry Ho = H - o (as the local kernels do): then E and
+            // F are one add-max each, and the diagonal term is one add-max with
+            // the profile S + o.
+            int32_t Ho[kMR], E[kMR];
 #pragma unroll
             for (int r = 0; r < kMR; ++r) {
-                H[r] = col0(mode, row0 + r, o, gmin);        // H(i, 0)
+                Ho[r] = col0(mode, row0 + r, o, gmin) - o;   // H(i, 0) - o
                 E[r] = kMNeg;                                // E(i, 0)
             }
-            int32_t hd = (row0 - 1 == 0) ? 0 : col0(mode, row0 - 1, o, gmin);   // H(row0-1, 0)
+            int32_t hd = ((row0 - 1 == 0) ? 0 : col0(mode, row0 - 1, o, gmin)) - o;   // H(row0-1, 0) - o
             int32_t pub_h = 0, pub_f = kMNeg;
             const bool more = r0 + kMStrip < m;
             const int rm = m - row0;                         // index of row m in this lane, if 0..7
             const int32_t *prow = a.prof + r0 + lane * kMR;
-            for (int st = 0; st < n + 31; ++st) {
+            // One column step.  STEADY: every lane inside its sequence and none at
+            // the last column (31 <= st <= n - 2), so the range checks fold away.
+            auto step = [&](const int st, auto steady_c) {
+                constexpr bool STEADY = decltype(steady_c)::value;
+                // from lane k-1: Ho of its bottom row at column j, F of our top row
                 int32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1);
                 int32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1);
                 const int j = st - lane + 1;
-                if (j >= 1 && j <= n) {
+                if (STEADY || (j >= 1 && j <= n)) {
                     if (lane == 0) {
-                        if (r0 == 0) {                       // H(0, j), F(0, j)
-                            hin = (mode == SW_ALIGN_GLOBAL) ? -lead_gap(j, o, gmin) : 0;
-                            fin = kMNeg;
-                        } else {
+                        if (r0 == 0) {                       // H(0, j) - o; F(1, j) = H(0, j) - o
+                            hin = ((mode == SW_ALIGN_GLOBAL) ? -lead_gap(j, o, gmin) : 0) - o;
+                            fin = hin;
+                        } else {                             // H(r0, j) - o, F(r0+1, j)
                             const int2 v = bnd[j];
                             hin = v.x;
                             fin = v.y;
@@ -107,36 +119,48 @@ __global__ void __launch_bounds__(kCtaThreads) k_modes_i32(const __grid_constant
                     }
                     const int c = tb[int64_t((j - 1) >> 2) * kBundleRowBytes + ((j - 1) & 3) * 2];
                     const int4 *pp = reinterpret_cast<const int4 *>(prow + int64_t(c) * a.m_pad);
-                    const int4 p0 = __ldg(pp), p1 = __ldg(pp + 1);
-                    const int32_t sc[kMR] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
-                    int32_t f = fin, up = hin, d = hd, hm = kMNeg;
+                    int32_t sc[kMR];
+#pragma unroll
+                    for (int v = 0; v < kMR / 4; ++v) {
+                        const int4 x4 = __ldg(pp + v);
+                        sc[4 * v] = x4.x; sc[4 * v + 1] = x4.y; sc[4 * v + 2] = x4.z; sc[4 * v + 3] = x4.w;
+                    }
+                    int32_t f = fin, d = hd, hm = kMNeg;
 #pragma unroll
                     for (int r = 0; r < kMR; ++r) {
-                        const int32_t e_r = __viaddmax_s32(E[r], -e, H[r] - o);   // E(i,j)
-                        f = __viaddmax_s32(f, -e, up - o);                         // F(i,j)
-                        const int32_t h = __vimax3_s32(d + sc[r], e_r, f);         // H(i,j)
-                        d = H[r];
+                        const int32_t e_r = __viaddmax_s32(E[r], -e, Ho[r]);   // E(i,j)
+                        const int32_t x = __viaddmax_s32(d, sc[r], e_r);       // max(H(i-1,j-1) + S, E(i,j))
+                        const int32_t h = max(x, f);                            // H(i,j)
+                        const int32_t ho = h - o;
+                        f = __viaddmax_s32(f, -e, ho);                          // F(i+1,j)
+                        d = Ho[r];
                         E[r] = e_r;
-                        H[r] = h;
-                        up = h;
-                        if (r == rm) hm = h;
+                        Ho[r] = ho;
+                        if (LAST && r == rm) hm = h;
                     }
-                    last_row = max(last_row, hm);
-                    if (j == n) {
+                    if (LAST) last_row = max(last_row, hm);
+                    if (!STEADY && j == n) {
                         int32_t lc = kMNeg;
 #pragma unroll
                         for (int r = 0; r < kMR; ++r)
-                            if (row0 + r <= m) lc = max(lc, H[r]);
+                            if (row0 + r <= m) lc = max(lc, Ho[r] + o);
                         last_col = max(last_col, lc);
                         if (hm != kMNeg) hmn = hm;
                     }
                     hd = hin;
-                    pub_h = H[kMR - 1];
+                    pub_h = Ho[kMR - 1];
                     pub_f = f;
-                    if (more && lane == 31) bnd[j] = make_int2(H[kMR - 1], f);
+                    if (more && lane == 31) bnd[j] = make_int2(Ho[kMR - 1], f);
                 }
-            }
-        }
+            };
+            int st = 0;
+            for (; st < 31 && st < n + 31; ++st) step(st, std::false_type());
+            for (; st <= n - 2; ++st) step(st, std::true_type());
+            for (; st < n + 31; ++st) step(st, std::false_type());
+        };
+        int r0 = 0;
+        for (; r0 + kMStrip < m; r0 += kMStrip) strip(r0, std::false_type());
+        strip(r0, std::true_type());
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) {
             last_row = max(last_row, __shfl_xor_sync(0xffffffffu, last_row, off));

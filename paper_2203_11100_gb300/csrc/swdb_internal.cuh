@@ -169,7 +169,7 @@ struct AlignArgs {
 struct ModeArgs {
     DbView db;
     int64_t seq_begin, seq_end;
-    const int32_t *prof;        // [kProfRows][m_pad] = S(q_i, c), pads -2^28
+    const int32_t *prof;        // [kProfRows][m_pad] = S(q_i, c) + o, pads -2^28
     int32_t m, m_pad;           // m_pad a multiple of 256
     int32_t gap_open, gap_extend;
     int32_t mode;               // SW_ALIGN_GLOBAL / SEMIGLOBAL / OVERLAP
