@@ -21,8 +21,8 @@
 // holds row m picks out H(m, j) (a compile-time variant of the strip loop).  Between strips the
 // bottom row (H, F per column) goes through this warp slot's scratch row in
 // global memory (H - o of the strip's last row and F of the row below),
-// rewritten in place: lane 31 writes column j - 30 while lane
-// 0 reads column j + 1, so a column is always read before it is rewritten.
+// rewritten in place: lane 31 writes column j - 30 while lane 0 prefetches
+// column j + 2, so a column is always read before it is rewritten.
 // Warps take sequences from an atomic counter, longest first.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -75,8 +75,12 @@ __global__ void __launch_bounds__(kCtaThreads) k_modes_i32(const __grid_constant
             }
             continue;
         }
-        const uint8_t *tb = a.db.codes + a.db.bundle_off[s / kBundleSeqs] + int((s % kBundleSeqs) >> 1) * kQuadBytes +
-                            int(s & 1);
+        // Lane 0 reads the codes 4 columns at a time (one 8-byte word holds 4
+        // columns of this sequence and its pair partner), one word ahead of use;
+        // the other lanes receive a column's code from the lane before them.
+        const uint2 *cptr = reinterpret_cast<const uint2 *>(a.db.codes + a.db.bundle_off[s / kBundleSeqs]) +
+                            int((s % kBundleSeqs) >> 1);
+        const int hsh = int(s & 1);                           // byte of this sequence within a column pair
         int32_t last_row = kMNeg;      // max over j >= 1 of H(m, j) (the lane holding row m)
         int32_t last_col = kMNeg;      // max over rows <= m of H(i, n)
         int32_t hmn = kMNeg;           // H(m, n)
@@ -94,7 +98,13 @@ __global__ void __launch_bounds__(kCtaThreads) k_modes_i32(const __grid_constant
                 E[r] = kMNeg;                                // E(i, 0)
             }
             int32_t hd = ((row0 - 1 == 0) ? 0 : col0(mode, row0 - 1, o, gmin)) - o;   // H(row0-1, 0) - o
-            int32_t pub_h = 0, pub_f = kMNeg;
+            int32_t pub_h = 0, pub_f = kMNeg, pub_c = 0;
+            uint2 quad = make_uint2(0, 0), quad_next = make_uint2(0, 0);
+            int2 bn_next = make_int2(0, 0);                  // lane 0: boundary entry of its next column
+            if (lane == 0) {
+                quad_next = __ldg(cptr);
+                if (r0 > 0) bn_next = bnd[1];
+            }
             const bool more = r0 + kMStrip < m;
             const int rm = m - row0;                         // index of row m in this lane, if 0..7
             const int32_t *prow = a.prof + r0 + lane * kMR;
@@ -105,19 +115,27 @@ __global__ void __launch_bounds__(kCtaThreads) k_modes_i32(const __grid_constant
                 // from lane k-1: Ho of its bottom row at column j, F of our top row
                 int32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1);
                 int32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1);
+                int cin = __shfl_up_sync(0xffffffffu, pub_c, 1);
                 const int j = st - lane + 1;
                 if (STEADY || (j >= 1 && j <= n)) {
-                    if (lane == 0) {
+                    if (lane == 0) {                         // column j = st + 1
+                        const int u = st & 3;
+                        if (u == 0) {
+                            quad = quad_next;
+                            if (st + 4 < n) quad_next = __ldg(cptr + ((st >> 2) + 1) * kBundlePairs);
+                        }
+                        const uint32_t w = (u & 2) ? quad.y : quad.x;
+                        cin = int((w >> (8 * ((u & 1) * 2 + hsh))) & 0xffu);
                         if (r0 == 0) {                       // H(0, j) - o; F(1, j) = H(0, j) - o
                             hin = ((mode == SW_ALIGN_GLOBAL) ? -lead_gap(j, o, gmin) : 0) - o;
                             fin = hin;
                         } else {                             // H(r0, j) - o, F(r0+1, j)
-                            const int2 v = bnd[j];
-                            hin = v.x;
-                            fin = v.y;
+                            hin = bn_next.x;
+                            fin = bn_next.y;
+                            if (j < n) bn_next = bnd[j + 1];
                         }
                     }
-                    const int c = tb[int64_t((j - 1) >> 2) * kBundleRowBytes + ((j - 1) & 3) * 2];
+                    const int c = cin;
                     const int4 *pp = reinterpret_cast<const int4 *>(prow + int64_t(c) * a.m_pad);
                     int32_t sc[kMR];
 #pragma unroll
@@ -150,6 +168,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_modes_i32(const __grid_constant
                     hd = hin;
                     pub_h = Ho[kMR - 1];
                     pub_f = f;
+                    pub_c = c;
                     if (more && lane == 31) bnd[j] = make_int2(Ho[kMR - 1], f);
                 }
             };

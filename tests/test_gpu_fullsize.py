@@ -107,3 +107,51 @@ def test_batched_512_queries_sampled(gpu):
     ti = rng.integers(0, w.db.n, 800).astype(np.int64)
     want = oracle.score_pairs(w.queries, w.db, qi, ti, w.matrix, w.gap_open, w.gap_extend)
     np.testing.assert_array_equal(s[qi, ti].astype(np.int64), want)
+
+
+def test_traceback_of_the_default_workloads_hits(gpu):
+    """sw_align on the 200 top-10 hits of the default workload, in the
+    configuration bench.py --align times: every alignment equals the oracle's."""
+    w = synth.make_workload("swissprot_like_20q")
+    with gpu.Database(w.db.residues, w.db.offsets, len(synth.ALPHABET)) as d:
+        _, hits, _ = d.search(w.queries.residues, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend,
+                              top_k=w.top_k, want_scores=False)
+        pq = np.repeat(np.arange(w.queries.n, dtype=np.int32), w.top_k)
+        pt = hits["db_index"].reshape(-1).astype(np.int64)
+        aln, ops, _ = d.align(w.queries.residues, w.queries.offsets, pq, pt, w.matrix, w.gap_open, w.gap_extend)
+    np.testing.assert_array_equal(aln["score"], hits["score"].reshape(-1))
+    for k, wa in enumerate(oracle.align_pairs(w.queries, w.db, pq, pt, w.matrix, w.gap_open, w.gap_extend)):
+        assert (int(aln["q_begin"][k]), int(aln["q_end"][k]), int(aln["t_begin"][k]), int(aln["t_end"][k])) == \
+            (wa["q_begin"], wa["q_end"], wa["t_begin"], wa["t_end"]), k
+        o0 = int(aln["ops_offset"][k])
+        np.testing.assert_array_equal(ops[o0:o0 + int(aln["ops_len"][k])], wa["ops"])
+
+
+@pytest.mark.parametrize("mode,code", [("global", 1), ("semiglobal", 2), ("overlap", 3)])
+def test_alignment_modes_full_size_sampled(gpu, mode, code):
+    """The default workload in each non-local mode (the configuration
+    bench.py --alignment times), checked on every top-k hit, the longest
+    sequences and random pairs; the hits are the best entries of the table."""
+    w = synth.make_workload("swissprot_like_20q")
+    rng = np.random.default_rng(80 + code)
+    with gpu.Database(w.db.residues, w.db.offsets, len(synth.ALPHABET)) as d:
+        s, h, _ = d.search(w.queries.residues, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend,
+                           top_k=w.top_k, stats=True, alignment=code)
+    for q in range(w.queries.n):
+        _hits_consistent(s[q], h[q], w.top_k)
+    qi, ti = [], []
+    for q in range(w.queries.n):
+        for t in h[q]["db_index"]:
+            qi.append(q)
+            ti.append(int(t))
+    longest = np.argsort(w.db.lengths)[::-1][:2]
+    for q in range(w.queries.n):
+        for t in longest:
+            qi.append(q)
+            ti.append(int(t))
+    qi += list(rng.integers(0, w.queries.n, 400))
+    ti += list(rng.integers(0, w.db.n, 400))
+    qi = np.array(qi, np.int64)
+    ti = np.array(ti, np.int64)
+    want = oracle.score_pairs(w.queries, w.db, qi, ti, w.matrix, w.gap_open, w.gap_extend, mode=mode)
+    np.testing.assert_array_equal(s[qi, ti].astype(np.int64), want)
