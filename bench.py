@@ -655,6 +655,7 @@ def run_reference(args, dist: Dist):
         cells += c
         secs += s
     v = cells / secs / 1e9
+    single = single_thread_oracle()
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": dist.world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
@@ -664,7 +665,49 @@ def run_reference(args, dist: Dist):
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"per step: all {w.queries.n} queries x {per_query} random database "
                                        f"sequences (~{cells / args.steps:.3g} cells)"},
-            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "single_thread_oracle": single, "host": host_info()}
+
+
+def host_info() -> dict:
+    """Core count and CPU model of the host the oracle runs on."""
+    import platform
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu part", "processor name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu": model}
+
+
+def single_thread_oracle() -> dict:
+    """Single-thread oracle GCUPS: the whole 1 x 100 vs 2,000 workload, and a
+    fixed ~1e9-cell sample of the default workload (all 20 queries x the
+    same random database sequences)."""
+    import oracle
+    out = {}
+    w = synth.make_workload("db2k_q100", seed=synth.SEED)
+    qi = np.zeros(w.db.n, dtype=np.int64)
+    ti = np.arange(w.db.n, dtype=np.int64)
+    t0 = time.perf_counter()
+    oracle.score_pairs(w.queries, w.db, qi, ti, w.matrix, w.gap_open, w.gap_extend, threads=1)
+    out["db2k_q100_gcups"] = float(w.cells) / (time.perf_counter() - t0) / 1e9
+    w = synth.make_workload("swissprot_like_20q", seed=synth.SEED)
+    rng = np.random.default_rng(synth.SEED + 5)
+    per_query = int(1e9 / w.queries.lengths.sum() / w.db.lengths.mean())
+    t_idx = np.sort(rng.choice(w.db.n, size=per_query, replace=False)).astype(np.int64)
+    qi = np.repeat(np.arange(w.queries.n, dtype=np.int64), len(t_idx))
+    ti = np.tile(t_idx, w.queries.n)
+    cells = float((w.queries.lengths[qi].astype(np.float64) * w.db.lengths[ti]).sum())
+    t0 = time.perf_counter()
+    oracle.score_pairs(w.queries, w.db, qi, ti, w.matrix, w.gap_open, w.gap_extend, threads=1)
+    out["swissprot_like_20q_sample_gcups"] = cells / (time.perf_counter() - t0) / 1e9
+    out["swissprot_like_20q_sample_cells"] = cells
+    return out
 
 
 def main(argv=None):

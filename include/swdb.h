@@ -237,6 +237,21 @@ int sw_top_k(const int32_t *scores, int64_t n_rows, int64_t n_cols, int32_t top_
 int sw_probe_alu_rate(int device, int32_t mode, double *per_sm_cycle, int32_t *sm_count);
 
 /*
+ * Self-test of failure detection (no counterpart in the paper, which has no
+ * error handling beyond CUDA_SAFE_CALL, Section 3.2).  The intra-task
+ * kernel's warps wait on each other through shared-memory flags; every such
+ * wait is bounded, and when its limit runs out the kernel records
+ * SW_ERR_TIMEOUT in a status word, stops waiting and finishes, so the
+ * search returns an error instead of hanging and the CUDA context stays
+ * usable.  This entry point runs that same wait routine on a flag that
+ * nothing sets, with spin_iters iterations of about 32 ns each (1 ..
+ * 2^25, about a second at most), and returns the status the kernel recorded
+ * in *status_out (SW_ERR_TIMEOUT when the mechanism works) and the elapsed
+ * host time in *elapsed_ms.  Errors: SW_ERR_INVALID_ARG, SW_ERR_CUDA.
+ */
+int sw_probe_wait_timeout(int device, int64_t spin_iters, int32_t *status_out, double *elapsed_ms);
+
+/*
  * Alignments (traceback) of chosen (query, database sequence) pairs, for
  * instance the hits of sw_search.  Section 2.2 defines the optimal local
  * alignment score by the Smith-Waterman recurrences (here in the affine-gap

@@ -33,6 +33,7 @@ from .binding import (  # noqa: F401
     sw_db_load,
     sw_last_error,
     sw_probe_alu_rate,
+    sw_probe_wait_timeout,
     sw_search,
     sw_search_no_alloc,
     sw_search_workspace_size,

@@ -91,6 +91,7 @@ def load_library():
     lib.sw_top_k.argtypes = [vp, i64, i64, i32, vp, vp]
     lib.sw_probe_alu_rate.argtypes = [ctypes.c_int, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
     lib.sw_search_no_alloc.argtypes = [vp, vp, i32, vp, i32, i32, vp, vp]
+    lib.sw_probe_wait_timeout.argtypes = [ctypes.c_int, i64, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]
     lib.sw_align_ops_capacity.argtypes = [vp, vp, i32, vp, vp, i64, ctypes.POINTER(i64)]
     lib.sw_align.argtypes = [vp, vp, vp, i32, vp, vp, i64, vp, i32, i32, vp, vp, i64,
                              ctypes.POINTER(SwAlignStats), vp]
@@ -246,6 +247,16 @@ def sw_probe_alu_rate(device: int = 0, mode: int = 0):
     sms = ctypes.c_int32()
     _check(load_library().sw_probe_alu_rate(device, mode, ctypes.byref(rate), ctypes.byref(sms)))
     return float(rate.value), int(sms.value)
+
+
+def sw_probe_wait_timeout(device: int = 0, spin_iters: int = 100000):
+    """Run the kernels' bounded wait on a flag nothing sets; returns
+    (status recorded by the kernel, elapsed ms).  SW_ERR_TIMEOUT (4) means the
+    wait gave up as designed."""
+    st = ctypes.c_int32(0)
+    ms = ctypes.c_double(0.0)
+    _check(load_library().sw_probe_wait_timeout(int(device), int(spin_iters), ctypes.byref(st), ctypes.byref(ms)))
+    return st.value, ms.value
 
 
 def sw_search_no_alloc(handle, query, matrix, gap_open: int, gap_extend: int, scores, stream=None) -> None:

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <chrono>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -1122,6 +1123,31 @@ int sw_top_k(const int32_t *scores, int64_t n_rows, int64_t n_cols, int32_t top_
     if (!hits) return fail(SW_ERR_INVALID_ARG, "hits is NULL");
     if (n_cols > (int64_t(1) << 31) - 2) return fail(SW_ERR_INVALID_ARG, "n_cols too large");
     SW_CUDA_TRY(launch_topk(scores, n_rows, n_cols, top_k, hits, static_cast<cudaStream_t>(stream)));
+    return SW_OK;
+}
+
+int sw_probe_wait_timeout(int device, int64_t spin_iters, int32_t *status_out, double *elapsed_ms) {
+    g_last_error.clear();
+    if (!status_out || !elapsed_ms) return fail(SW_ERR_INVALID_ARG, "NULL argument");
+    if (spin_iters < 1 || spin_iters > (int64_t(1) << 25)) return fail(SW_ERR_INVALID_ARG, "spin_iters must be 1..2^25");
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return fail(SW_ERR_INVALID_ARG, "no such CUDA device");
+    }
+    DeviceGuard guard(device);
+    int32_t *status = nullptr;
+    SW_CUDA_TRY(cudaMalloc(&status, sizeof(int32_t)));
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaError_t err = cudaMemset(status, 0, sizeof(int32_t));
+    if (err == cudaSuccess) err = launch_wait_probe((long long)spin_iters, status, nullptr);
+    if (err == cudaSuccess) err = cudaDeviceSynchronize();
+    int32_t h = 0;
+    if (err == cudaSuccess) err = cudaMemcpy(&h, status, sizeof h, cudaMemcpyDeviceToHost);
+    *elapsed_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    cudaFree(status);
+    if (err != cudaSuccess) return fail(SW_ERR_CUDA, cudaGetErrorString(err));
+    *status_out = h;
     return SW_OK;
 }
 

@@ -75,8 +75,9 @@ __device__ __forceinline__ void st_release(int *p, int v) {
 
 // Spin (all lanes of a warp) until *flag >= target, the CTA aborts, or the
 // spin limit runs out (then record a timeout and abort the CTA).
-__device__ bool wait_flag(const int *flag, int target, int *abort_flag, int32_t *status) {
-    for (long long it = 0; it < kSpinLimit; ++it) {
+__device__ bool wait_flag(const int *flag, int target, int *abort_flag, int32_t *status,
+                          long long limit = kSpinLimit) {
+    for (long long it = 0; it < limit; ++it) {
         if (ld_acquire(flag) >= target) return true;
         if (*reinterpret_cast<volatile int *>(abort_flag)) return false;
         __nanosleep(32);
@@ -361,6 +362,19 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
     }
 }
 
+// Self-test of the bounded wait: one warp waits on a shared-memory flag that
+// nothing sets, with the given spin limit, and must give up and record
+// SW_ERR_TIMEOUT in *status rather than hang.
+__global__ void k_wait_probe(long long limit, int32_t *status) {
+    __shared__ int flag, abort_flag;
+    if (threadIdx.x == 0) {
+        flag = 0;
+        abort_flag = 0;
+    }
+    __syncthreads();
+    wait_flag(&flag, 1, &abort_flag, status, limit);
+}
+
 template <int R, int NW, int P>
 size_t intra_smem() {
     return size_t(NW) * kProfRows * 32 * R + size_t(P) * NW * kDepth * kChunk * sizeof(uint2) +
@@ -394,6 +408,12 @@ bool intra_config_supported(int warps, int rows) {
 }
 
 int intra_rows_per_superpass(int warps, int rows) { return warps * 32 * rows; }
+
+cudaError_t launch_wait_probe(long long limit, int32_t *status, cudaStream_t s) {
+    if (limit < 1 || limit > kSpinLimit) return cudaErrorInvalidValue;
+    k_wait_probe<<<1, 32, 0, s>>>(limit, status);
+    return cudaGetLastError();
+}
 
 cudaError_t prepare_intra_i16x2(int warps, int rows) {
     if (rows == 16 && warps == 4) return prepare_rnp<16, 4, 3>();

@@ -202,6 +202,7 @@ int probe_blocks_per_sm(int mode);
 cudaError_t launch_modes_i32(const ModeArgs &a, int grid, cudaStream_t s);
 int modes_slots(int sms);            // resident CTAs of the modes kernel
 int32_t modes_strip_rows();
+cudaError_t launch_wait_probe(long long limit, int32_t *status, cudaStream_t s);   // limit 1 .. 2^25
 cudaError_t launch_align(const AlignArgs &a, int which, cudaStream_t s);   // 0 forward, 1 traceback
 int64_t align_checkpoint_rows(int32_t m);
 int32_t align_strip_rows();

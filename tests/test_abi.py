@@ -117,3 +117,13 @@ def test_struct_sizes_match_the_header(tmp_path):
             binding.ALIGNMENT_DTYPE.itemsize, ctypes.sizeof(binding.SwAlignStats), binding.HIT_DTYPE.itemsize,
             ctypes.sizeof(binding.SwDbInfo)]
     assert got == want
+
+
+def test_wait_probe_rejects_bad_arguments_on_host(lib):
+    from paper_2203_11100_gb300 import binding
+    st = ctypes.c_int32(0)
+    ms = ctypes.c_double(0.0)
+    assert lib.sw_probe_wait_timeout(0, 0, ctypes.byref(st), ctypes.byref(ms)) == 1
+    assert "spin_iters" in binding.sw_last_error()
+    assert lib.sw_probe_wait_timeout(0, 1 << 26, ctypes.byref(st), ctypes.byref(ms)) == 1
+    assert lib.sw_probe_wait_timeout(0, 1000, None, ctypes.byref(ms)) == 1
