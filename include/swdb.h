@@ -312,9 +312,11 @@ int sw_align_ops_capacity(const sw_db *db, const int64_t *q_offsets, int32_t n_q
  *   stream          cudaStream_t, or NULL for the handle's stream
  * The call is synchronous.  Device scratch comes from the handle's own
  * workspace (grown as needed): for each pair about 8 * ceil(m/256) * (n+1)
- * bytes of strip checkpoints plus 256 * n bytes of traceback flags.
+ * bytes of strip checkpoints plus 256 * n bytes of traceback flags, and for
+ * each query that appears 128 * round_up(m, 256) bytes of profile.
  * Errors: SW_ERR_INVALID_ARG (NULL or out-of-range argument, ops_capacity too
- * small), SW_ERR_OVERFLOW (as sw_search's int32 limits), SW_ERR_OOM,
+ * small), SW_ERR_OVERFLOW (as sw_search's int32 limits), SW_ERR_TIMEOUT (a
+ * bounded wait between the strips of a pair ran out), SW_ERR_OOM,
  * SW_ERR_CUDA.
  */
 int sw_align(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_t n_q,

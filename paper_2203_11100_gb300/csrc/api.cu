@@ -1316,9 +1316,19 @@ int sw_align(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_
     auto r256 = [](size_t x) { return (x + 255) & ~size_t(255); };
     const size_t q_bytes = q_dev ? 0 : r256(size_t(total_q));
     const size_t mat_bytes = r256(sizeof(int32_t) * kProfRows * kProfRows);
+    // forward pass: one profile table S(q_i, c), [32][round_up(m, 256)], per query in the pairs
+    std::vector<int64_t> prof_off(size_t(n_q), -1);
+    int64_t prof_elems = 0;
+    for (int64_t k = 0; k < n_pairs; ++k) {
+        const int32_t q = pair_query[k];
+        if (prof_off[size_t(q)] >= 0) continue;
+        prof_off[size_t(q)] = prof_elems;
+        prof_elems += int64_t(kProfRows) * round_up(std::max<int64_t>(pair_len_q(q_offsets, q), 1), align_strip_rows());
+    }
+    const size_t prof_bytes = r256(sizeof(int32_t) * size_t(prof_elems));
     const size_t pairs_bytes = r256(sizeof(AlignPairDev) * size_t(max_chunk_pairs));
     const size_t res_bytes = r256(sizeof(AlignResultDev) * size_t(max_chunk_pairs));
-    const size_t need = q_bytes + mat_bytes + pairs_bytes + res_bytes + size_t(max_chunk_scratch) + 256;
+    const size_t need = q_bytes + mat_bytes + prof_bytes + pairs_bytes + res_bytes + size_t(max_chunk_scratch) + 256;
     if (db->ws_bytes < need) {
         SW_CUDA_TRY(cudaDeviceSynchronize());
         cudaFree(db->ws);
@@ -1330,15 +1340,22 @@ int sw_align(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_
     uint8_t *w = static_cast<uint8_t *>(db->ws);
     uint8_t *d_q = q_dev ? const_cast<uint8_t *>(queries) : w;
     int32_t *d_mat = reinterpret_cast<int32_t *>(w + q_bytes);
-    AlignPairDev *d_pairs = reinterpret_cast<AlignPairDev *>(w + q_bytes + mat_bytes);
-    AlignResultDev *d_res = reinterpret_cast<AlignResultDev *>(w + q_bytes + mat_bytes + pairs_bytes);
-    uint8_t *d_scratch = w + q_bytes + mat_bytes + pairs_bytes + res_bytes;
+    int32_t *d_prof = reinterpret_cast<int32_t *>(w + q_bytes + mat_bytes);
+    AlignPairDev *d_pairs = reinterpret_cast<AlignPairDev *>(w + q_bytes + mat_bytes + prof_bytes);
+    AlignResultDev *d_res = reinterpret_cast<AlignResultDev *>(w + q_bytes + mat_bytes + prof_bytes + pairs_bytes);
+    uint8_t *d_scratch = w + q_bytes + mat_bytes + prof_bytes + pairs_bytes + res_bytes;
 
     std::vector<int32_t> mat(kProfRows * kProfRows, 0);
     for (int x = 0; x < A; ++x)
         for (int y = 0; y < A; ++y) mat[size_t(x * kProfRows + y)] = matrix[x * A + y];
     if (!q_dev && total_q > 0) SW_CUDA_TRY(cudaMemcpyAsync(d_q, queries, size_t(total_q), cudaMemcpyHostToDevice, st));
     SW_CUDA_TRY(cudaMemcpyAsync(d_mat, mat.data(), sizeof(int32_t) * mat.size(), cudaMemcpyHostToDevice, st));
+    for (int32_t q = 0; q < n_q; ++q) {
+        const int64_t m = pair_len_q(q_offsets, q);
+        if (prof_off[size_t(q)] < 0 || m == 0) continue;
+        const int32_t m_pad = int32_t(round_up(m, align_strip_rows()));
+        SW_CUDA_TRY(launch_profile32(d_q + q_offsets[q], int32_t(m), m_pad, matrix, A, 0, d_prof + prof_off[size_t(q)], st));
+    }
 
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     if (stats)
@@ -1366,6 +1383,8 @@ int sw_align(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_
             d.t_sorted = db->h_sorted_pos[size_t(pair_target[k])];
             d.m = int32_t(m);
             d.n = int32_t(n);
+            d.prof_off = prof_off[size_t(pair_query[k])];
+            d.m_pad = int32_t(round_up(std::max<int64_t>(m, 1), align_strip_rows()));
             d.ckpt_off = ck / int64_t(sizeof(int2));
             ck += r256(size_t(align_checkpoint_rows(int32_t(m)) * (n + 1) * int64_t(sizeof(int2))));
             d.flags_off = fl;
@@ -1383,6 +1402,7 @@ int sw_align(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_
         a.n_pairs = np;
         a.results = d_res;
         a.mat = d_mat;
+        a.prof = d_prof;
         a.ckpt = reinterpret_cast<int2 *>(d_scratch);
         a.flags = d_scratch + ck;
         a.rev = d_scratch + ck + fl;
@@ -1401,6 +1421,7 @@ int sw_align(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_
         SW_CUDA_TRY(cudaStreamSynchronize(st));
         for (int64_t k = k0; k < k1; ++k) {
             const AlignResultDev &r = hr[size_t(k - k0)];
+            if (r.status == 5) return fail(SW_ERR_TIMEOUT, "traceback forward pass: a wait between strips ran out");
             if (r.status != 0) return fail(SW_ERR_CUDA, "traceback walk met an inconsistent cell");
             sw_alignment &o = alignments_out[k];
             o.score = r.score;

@@ -3,19 +3,21 @@
 // from the Gotoh matrices (affine gaps as in Section 4.1) with the tie rules
 // stated in swdb.h.
 //
-// One warp per pair, int32 arithmetic.  Lane k holds query rows
-// 8k+1 .. 8k+8 of a 256-row strip and runs one column behind lane k-1 (a
-// skewed wavefront: H and F of a lane's bottom row reach the next lane by
-// shuffle).  The int32 profile of the strip, [target code][row], sits in
-// shared memory, so a lane reads its 8 rows with two 16-byte loads.
+// int32 arithmetic.  A warp works on one 256-row strip at a time: lane k
+// holds query rows 8k+1 .. 8k+8 of the strip and runs one column behind lane
+// k-1 (a skewed wavefront: H and F of a lane's bottom row reach the next lane
+// by shuffle).
 //
-// Forward pass (k_align_fwd): every strip in turn over all n columns; the
-// last lane writes its bottom row's H and F for every column (the strip's
-// checkpoint row, the top boundary of the next strip).  The maximum and the
-// first cell in row-major order that holds it are kept per lane and reduced
-// over the warp at the end.
+// Forward pass (k_align_fwd, one CTA of 8 warps per pair): the strips run as
+// a wavefront over the warps, each a few dozen columns behind the strip
+// above.  The last lane of a strip writes its bottom row's H and F for every
+// column (the strip's checkpoint row, the top boundary of the next strip);
+// the warp below reads it once published.  The profile S(q_i, c) of each
+// query is a global [code][row] table.  The maximum and the first cell in
+// row-major order that holds it are kept per lane and reduced over the CTA.
 //
-// Traceback pass (k_align_bwd): starting from the end cell's strip, the
+// Traceback pass (k_align_bwd, one warp per pair; the strip's int32 profile
+// [code][row] in shared memory): starting from the end cell's strip, the
 // warp recomputes that strip's rows up to the current row and columns up to
 // the current column from the checkpoint row above it, storing one flag byte
 // per cell (which of the candidates H equals, whether E and F open at the
@@ -36,6 +38,9 @@ namespace {
 constexpr int kAR = 8;                   // query rows per lane
 constexpr int kStrip = 32 * kAR;         // rows per strip
 constexpr int32_t kNegInf = -(1 << 29);  // -infinity of the recurrences
+constexpr int kFW = 8;                   // warps per pair in the forward pass
+constexpr int kPub = 32;                 // forward pass: columns per progress publication
+constexpr long long kAlignSpin = 1ll << 25;   // x ~32 ns sleep: about a second
 
 // flag bits of one cell (i, j)
 constexpr uint8_t F_ZERO = 1;    // H(i,j) = 0
@@ -75,29 +80,53 @@ __device__ __forceinline__ void load_profile(int32_t (*prof)[kStrip], const int3
 
 __device__ __forceinline__ int32_t max3(int32_t a, int32_t b, int32_t c) { return __vimax3_s32(a, b, c); }
 
-__global__ void __launch_bounds__(32) k_align_fwd(const AlignArgs a) {
-    __shared__ __align__(16) int32_t prof[kProfRows][kStrip];
-    __shared__ int32_t mat[kProfRows * kProfRows];
-    const int lane = threadIdx.x;
+__device__ __forceinline__ int ld_acquire_cta(const int *p) {
+    int v;
+    asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_cta(int *p, int v) {
+    asm volatile("st.release.cta.shared.u32 [%0], %1;" :: "r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+}
+
+// Forward pass, one CTA of kFW warps per pair.  Warp w takes strips w,
+// w + kFW, ... in order.  Strip s reads the bottom row of strip s - 1 from
+// its checkpoint row in global memory, column by column, once the warp that
+// writes it has published the columns: pub[w] = strip * (n + 1) + columns
+// written, monotonic over the warp's strips and released after the writes
+// (every kPub columns and at the last column).  Every checkpoint row stays
+// in memory, so a writer never waits for a reader, and strips run as a
+// wavefront about kPub + 31 columns apart.  Each wait is bounded; when it
+// runs out the pair's status records a timeout and the CTA stops waiting.
+__global__ void __launch_bounds__(kFW * 32) k_align_fwd(const AlignArgs a) {
+    __shared__ int pub[kFW];
+    __shared__ int abort_flag;
+    __shared__ int32_t red_best[kFW];
+    __shared__ long long red_key[kFW];
+    __shared__ int red_status[kFW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const AlignPairDev P = a.pairs[blockIdx.x];
     AlignResultDev *R = a.results + blockIdx.x;
-    for (int i = lane; i < kProfRows * kProfRows; i += 32) mat[i] = a.mat[i];
     const int m = P.m, n = P.n;
     if (m <= 0 || n <= 0) {
-        if (lane == 0) *R = AlignResultDev{};
+        if (threadIdx.x == 0) *R = AlignResultDev{};
         return;
     }
-    const uint8_t *q = a.queries + P.q_off;
+    if (threadIdx.x < kFW) pub[threadIdx.x] = -1;
+    if (threadIdx.x == 0) abort_flag = 0;
+    __syncthreads();
+    const int32_t *prof = a.prof + P.prof_off;        // [code][m_pad] = S(q_i, code)
     const uint8_t *tb = target_base(a.db, P.t_sorted);
     const int32_t o = a.gap_open, e = a.gap_extend;
+    const int nstrips = (m + kStrip - 1) / kStrip;
+    const int prevw = (warp + kFW - 1) % kFW;         // writes the strip above ours
 
     int32_t best = 0;
     int64_t bkey = INT64_MAX;              // (i << 32) | j of the first maximum in row-major order
-    for (int r0 = 0; r0 < m; r0 += kStrip) {
-        const int strip = r0 / kStrip;
-        __syncwarp();
-        load_profile(prof, mat, q, m, r0, lane);
-        __syncwarp();
+    int status = 0;
+    for (int strip = warp; strip < nstrips && status == 0; strip += kFW) {
+        const int r0 = strip * kStrip;
         int32_t H[kAR], E[kAR];
 #pragma unroll
         for (int r = 0; r < kAR; ++r) { H[r] = 0; E[r] = kNegInf; }
@@ -106,7 +135,26 @@ __global__ void __launch_bounds__(32) k_align_fwd(const AlignArgs a) {
         int2 *ck_out = a.ckpt + P.ckpt_off + int64_t(strip) * (n + 1);
         const bool write_ck = r0 + kStrip < m;
         const int row0 = r0 + lane * kAR + 1;          // 1-based first row of this lane
+        const int32_t *prow = prof + r0 + lane * kAR;
+        const int need_base = (strip - 1) * (n + 1);
+        int avail = 0;                                 // columns of ck_in known to be written
+        if (write_ck && lane == 31) ck_out[0] = make_int2(0, kNegInf);
         for (int s = 0; s < n + 31; ++s) {
+            if (strip > 0 && s + 1 <= n && s + 1 > avail) {   // warp-uniform
+                const int want = min(s + kPub, n);
+                bool ok = false;
+                for (long long it = 0; it < kAlignSpin; ++it) {
+                    if (ld_acquire_cta(&pub[prevw]) >= need_base + want) { ok = true; break; }
+                    if (*reinterpret_cast<volatile int *>(&abort_flag)) break;
+                    __nanosleep(32);
+                }
+                if (!ok) {
+                    status = 5;                        // timeout (or another warp's)
+                    if (lane == 0) *reinterpret_cast<volatile int *>(&abort_flag) = 1;
+                    break;
+                }
+                avail = want;
+            }
             int32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1);
             int32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1);
             const int j = s - lane + 1;                 // 1-based column
@@ -116,8 +164,8 @@ __global__ void __launch_bounds__(32) k_align_fwd(const AlignArgs a) {
                     else { const int2 v = ck_in[j]; hin = v.x; fin = v.y; }
                 }
                 const int c = target_code(tb, j - 1);
-                const int4 p0 = *reinterpret_cast<const int4 *>(&prof[c][lane * kAR]);
-                const int4 p1 = *reinterpret_cast<const int4 *>(&prof[c][lane * kAR + 4]);
+                const int4 *pp = reinterpret_cast<const int4 *>(prow + int64_t(c) * P.m_pad);
+                const int4 p0 = __ldg(pp), p1 = __ldg(pp + 1);
                 const int32_t sc[kAR] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
                 int32_t f = fin, up = hin, d = hd;
 #pragma unroll
@@ -138,10 +186,12 @@ __global__ void __launch_bounds__(32) k_align_fwd(const AlignArgs a) {
                 hd = hin;
                 pub_h = H[kAR - 1];
                 pub_f = f;
-                if (write_ck && lane == 31) ck_out[j] = make_int2(H[kAR - 1], f);
+                if (write_ck && lane == 31) {
+                    ck_out[j] = make_int2(H[kAR - 1], f);
+                    if (j % kPub == 0 || j == n) st_release_cta(&pub[warp], strip * (n + 1) + j);
+                }
             }
         }
-        if (write_ck && lane == 31) ck_out[0] = make_int2(0, kNegInf);
     }
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) {
@@ -150,12 +200,24 @@ __global__ void __launch_bounds__(32) k_align_fwd(const AlignArgs a) {
         if (ob > best || (ob == best && ok < bkey)) { best = ob; bkey = ok; }
     }
     if (lane == 0) {
+        red_best[warp] = best;
+        red_key[warp] = bkey;
+        red_status[warp] = status;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int st = 0;
+        for (int w = 0; w < kFW; ++w) {
+            if (red_best[w] > best || (red_best[w] == best && red_key[w] < bkey)) { best = red_best[w]; bkey = red_key[w]; }
+            st = max(st, red_status[w]);
+        }
         AlignResultDev res{};
         res.score = best;
         if (best > 0) {
             res.i_end = int32_t(bkey >> 32);
             res.j_end = int32_t(bkey & 0xffffffff);
         }
+        res.status = st;
         *R = res;
     }
 }
@@ -291,7 +353,7 @@ __global__ void __launch_bounds__(32) k_align_bwd(const AlignArgs a) {
 cudaError_t launch_align(const AlignArgs &a, int which, cudaStream_t s) {
     if (a.n_pairs <= 0) return cudaSuccess;
     if (a.n_pairs > 0x7fffffff) return cudaErrorInvalidValue;
-    if (which == 0) k_align_fwd<<<unsigned(a.n_pairs), 32, 0, s>>>(a);
+    if (which == 0) k_align_fwd<<<unsigned(a.n_pairs), kFW * 32, 0, s>>>(a);
     else k_align_bwd<<<unsigned(a.n_pairs), 32, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -139,14 +139,17 @@ struct AlignPairDev {
     int64_t flags_off;    // flags (bytes): one strip, 256 x n
     int64_t rev_off;      // rev (bytes): m + n reversed ops
     int64_t ops_off;      // ops (bytes): m + n ops in order
+    int64_t prof_off;     // prof (int32 units): the query's [32][m_pad] table S(q_i, c)
     int32_t m, n;
+    int32_t m_pad;        // m rounded up to the 256-row strip
+    int32_t pad;
 };
 struct AlignResultDev {
     int32_t score;
     int32_t i_end, j_end;      // 1-based end cell (0 when the score is 0)
     int32_t i_begin, j_begin;  // rows / columns before the alignment's first column
     int32_t n_ops;
-    int32_t status;            // 0, or where the walk found an inconsistent flag
+    int32_t status;            // 0; 1-4 the walk found an inconsistent flag; 5 a forward-pass wait ran out
     int32_t pad;
     int64_t cells;             // cells recomputed by the traceback pass
 };
@@ -157,6 +160,7 @@ struct AlignArgs {
     int64_t n_pairs;
     AlignResultDev *results;
     const int32_t *mat;        // [32][32] int32, entries outside the alphabet unused
+    const int32_t *prof;       // per-query profiles (forward pass), see AlignPairDev::prof_off
     int2 *ckpt;
     uint8_t *flags;
     uint8_t *rev;
