@@ -143,3 +143,14 @@ def test_pairs_beyond_one_chunk(gpu):
     pq = (np.arange(100) % 4).astype(np.int32)
     pt = np.arange(100, dtype=np.int64)
     _check_pairs(gpu, qs, db, synth.blosum62(), 10, 1, pq, pt)
+
+
+def test_more_strips_than_warps(gpu):
+    """Queries of 9 and 12 strips: warps of the forward pass take a second
+    strip each (the wavefront wraps around the CTA's 8 warps)."""
+    rng = np.random.default_rng(70)
+    db = synth.seqset_from_lengths(rng, [1, 700, 2500, 4100])
+    qs = synth.seqset_from_lengths(rng, [2049, 3000])
+    pq, pt = _all_pairs(qs.n, db.n)
+    for o, e in ((10, 1), (3, 5), (0, 2)):
+        _check_pairs(gpu, qs, db, synth.blosum62(), o, e, pq, pt)
