@@ -162,7 +162,7 @@ struct ShapeRate {
     int lanes, rows;
     double gcups;
 };
-constexpr ShapeRate kShapes[] = {{8, 16, 5000.0}, {16, 16, 5300.0}, {8, 32, 5900.0}, {16, 32, 5700.0}};
+constexpr ShapeRate kShapes[] = {{8, 16, 5000.0}, {16, 16, 5300.0}, {8, 24, 5680.0}, {8, 32, 5900.0}, {16, 32, 5700.0}};
 
 void choose_shape(int64_t m, int *lanes, int *rows) {
     double best = 1e300;

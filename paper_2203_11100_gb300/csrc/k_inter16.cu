@@ -82,11 +82,13 @@ __device__ __forceinline__ uint32_t pack2(int v) {
 // boundary in the database layout's shape.
 template <int T, int R, bool SLOTS>
 __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_inter_i16x2(const __grid_constant__ InterArgs a) {
-    static_assert(R % 16 == 0, "rows per lane must be a multiple of 16");
+    static_assert(R % 8 == 0, "rows per lane must be a multiple of 8");
     static_assert(32 % T == 0 && T >= 4, "lanes must divide the warp");
     constexpr int PAIRS_PER_CTA = kCtaThreads / T;
     constexpr int TR = T * R;
-    constexpr int PROF_BYTES = kProfRows * TR;
+    constexpr int H16 = (R + 15) / 16;                // 16-row groups per lane (the last may hold 8)
+    constexpr int SLOT = T * 16 * H16;                // profile bytes per residue
+    constexpr int PROF_BYTES = kProfRows * SLOT;
 
     __shared__ __align__(16) int8_t prof[PROF_BYTES];
     __shared__ int8_t mat[kProfRows * kProfRows];
@@ -158,17 +160,18 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_inter_i16x2(
     for (int pass = 0; pass < npass; ++pass) {
         __syncthreads();
         // Profile strip for rows pass*TR .. pass*TR+TR-1, layout
-        // [residue a][half h][lane k][16 rows]: lane k's rows 16h..16h+15 sit at
-        // a*TR + h*T*16 + k*16, so the 8 lanes of a quarter-warp read 8
-        // consecutive 16-byte slots (no bank conflicts) and a lane's second
-        // half is a compile-time offset from its first.
-        for (int w = tid; w < PROF_BYTES / 4; w += kCtaThreads) {
+        // [residue a][group h][lane k][16 rows]: lane k's rows 16h..16h+15 sit at
+        // a*SLOT + h*T*16 + k*16, so the 8 lanes of a quarter-warp read 8
+        // consecutive 16-byte slots (no bank conflicts) and a lane's later
+        // groups are compile-time offsets from its first.  With R = 24 the
+        // second group holds 8 rows in the first half of its slot.
+        for (int w = tid; w < kProfRows * TR / 4; w += kCtaThreads) {
             const int e0 = w * 4;
             const int res = e0 / TR;
             const int within = e0 % TR;
             const int row0 = pass * TR + within;
             const int kk = within / R, rr = within % R;
-            const int phys = res * TR + (rr >> 4) * (T * 16) + kk * 16 + (rr & 15);
+            const int phys = res * SLOT + (rr >> 4) * (T * 16) + kk * 16 + (rr & 15);
             uint32_t word = 0;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -253,8 +256,8 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_inter_i16x2(
             }
             if (act) {
                 const int ta = int(cin & 0xffu), tb = int((cin >> 8) & 0xffu);
-                const uint4 *pa = reinterpret_cast<const uint4 *>(prof + ta * TR + k * 16);
-                const uint4 *pb = reinterpret_cast<const uint4 *>(prof + tb * TR + k * 16);
+                const uint4 *pa = reinterpret_cast<const uint4 *>(prof + ta * SLOT + k * 16);
+                const uint4 *pb = reinterpret_cast<const uint4 *>(prof + tb * SLOT + k * 16);
                 uint32_t wa[R / 4], wb[R / 4];
 #pragma unroll
                 for (int v = 0; v < R / 16; ++v) {
@@ -262,6 +265,12 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_inter_i16x2(
                     const uint4 y = pb[v * T];
                     wa[4 * v + 0] = x.x; wa[4 * v + 1] = x.y; wa[4 * v + 2] = x.z; wa[4 * v + 3] = x.w;
                     wb[4 * v + 0] = y.x; wb[4 * v + 1] = y.y; wb[4 * v + 2] = y.z; wb[4 * v + 3] = y.w;
+                }
+                if (R % 16) {                     // last group of 8 rows: an 8-byte load
+                    const uint2 x = *reinterpret_cast<const uint2 *>(pa + (R / 16) * T);
+                    const uint2 y = *reinterpret_cast<const uint2 *>(pb + (R / 16) * T);
+                    wa[R / 4 - 2] = x.x; wa[R / 4 - 1] = x.y;
+                    wb[R / 4 - 2] = y.x; wb[R / 4 - 1] = y.y;
                 }
                 uint32_t f = fin;                 // B(F) of this lane's top row
                 uint32_t d = hd;
@@ -368,7 +377,7 @@ int slots_tr(int sms) {
 
 bool inter_config_supported(int lanes, int rows) {
     switch (lanes * 100 + rows) {
-        case 416: case 816: case 1616: case 3216: case 832: case 1632: case 3232: return true;
+        case 416: case 816: case 1616: case 3216: case 824: case 832: case 1632: case 3232: return true;
         default: return false;
     }
 }
@@ -377,6 +386,7 @@ cudaError_t launch_inter_i16x2(const InterArgs &a, int lanes, int rows, cudaStre
     switch (lanes * 100 + rows) {
         case 416: return launch_tr<4, 16>(a, s, grid_slots);
         case 816: return launch_tr<8, 16>(a, s, grid_slots);
+        case 824: return launch_tr<8, 24>(a, s, grid_slots);
         case 1616: return launch_tr<16, 16>(a, s, grid_slots);
         case 3216: return launch_tr<32, 16>(a, s, grid_slots);
         case 832: return launch_tr<8, 32>(a, s, grid_slots);
@@ -390,6 +400,7 @@ int inter_slots(int lanes, int rows, int sms) {
     switch (lanes * 100 + rows) {
         case 416: return slots_tr<4, 16>(sms);
         case 816: return slots_tr<8, 16>(sms);
+        case 824: return slots_tr<8, 24>(sms);
         case 1616: return slots_tr<16, 16>(sms);
         case 3216: return slots_tr<32, 16>(sms);
         case 832: return slots_tr<8, 32>(sms);

@@ -13,7 +13,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-I16_SHAPES = [(4, 16), (8, 16), (16, 16), (32, 16), (8, 32), (16, 32), (32, 32)]
+I16_SHAPES = [(4, 16), (8, 16), (16, 16), (32, 16), (8, 24), (8, 32), (16, 32), (32, 32)]
 I32_SHAPES = [(8, 16), (16, 16), (32, 16), (32, 32)]
 
 
@@ -48,7 +48,7 @@ def test_int16x2_blosum62_shapes(gpu, lanes, rows):
     assert st["cells"] == int(qs.lengths.sum()) * int(db.lengths.sum())
 
 
-@pytest.mark.parametrize("lanes,rows", [(4, 16), (8, 16), (32, 32)])
+@pytest.mark.parametrize("lanes,rows", [(4, 16), (8, 16), (8, 24), (32, 32)])
 def test_int16x2_persistent_slots_reused(gpu, lanes, rows):
     """Far more sequence chunks than resident blocks: each block slot takes many
     chunks in turn and reuses its strip-boundary scratch for every pass of every
