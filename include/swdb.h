@@ -87,9 +87,20 @@ typedef enum {
  *               H(i,0) = -g(i), H(0,j) = 0; score max over j of H(m,j)
  *   OVERLAP     end gaps free on both: H(i,0) = H(0,j) = 0;
  *               score max(max_j H(m,j), max_i H(i,n))
- * Their scores can be negative; they are computed in exact int32 (the
- * precision and mode options do not apply) and require
- * (m + n) * (max|S| + o + e) < 2^28 for every pair (else SW_ERR_OVERFLOW). */
+ * Their scores can be negative and are exact.  They require
+ * (m + n) * (max|S| + o + e) < 2^28 for every pair (else SW_ERR_OVERFLOW).
+ * precision: with SW_PREC_AUTO or SW_PREC_I16, when S + o fits int8 and
+ * o <= 127, each query's pairs that provably stay inside int16 run in packed
+ * int16x2 (two database sequences per operation, no saturation check needed:
+ * with Lp the pair's longer length rounded up to 4, the host requires
+ * g(m) + g(Lp) + o + max(e, 128) <= 32768, g(m) counted as 0 for OVERLAP, and
+ * max(S, 0) * (min(m, Lp) + 1) <= 32767, and for a query taller than one strip
+ * Lp <= 4096); the other pairs (the longest) run in int32, concurrently.
+ * SW_PREC_I16 returns SW_ERR_UNSUPPORTED when S + o does not fit; SW_PREC_I32
+ * runs every pair in int32.  lanes / rows_per_lane: 8 and 16, 24 or 32 for
+ * the packed kernel (0 = chosen per query); stats->long_cells counts the
+ * cells scored in int32 and long_sequences the sequences sent there (largest
+ * over the queries).  The mode option does not apply. */
 typedef enum {
     SW_ALIGN_LOCAL = 0,
     SW_ALIGN_GLOBAL = 1,
@@ -106,7 +117,7 @@ typedef struct {
                                  intra-task kernel; 0 = library default, <0 = never */
     int32_t lanes;            /* lanes per database-sequence pair in the inter-task kernel
                                  (4, 8, 16 or 32); 0 = chosen per query by the library */
-    int32_t rows_per_lane;    /* query rows held per lane (16 or 32); 0 = chosen per query */
+    int32_t rows_per_lane;    /* query rows held per lane (16, 24 or 32); 0 = chosen per query */
     void *workspace;          /* caller-owned device scratch, or NULL for the handle's own */
     size_t workspace_bytes;   /* size of workspace */
     int32_t flags;            /* SW_FLAG_* bits */

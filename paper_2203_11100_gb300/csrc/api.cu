@@ -179,6 +179,26 @@ void choose_shape(int64_t m, int *lanes, int *rows) {
 
 // Batched-kernel shapes (lanes, rows) with measured rates (GCUPS, GB300);
 // each query pair takes the one with the least predicted time.
+// Shapes of the int16x2 alignment-mode kernel (k_modes16.cu), same rule.
+constexpr ShapeRate kModeShapes[] = {{8, 16, 5000.0}, {8, 24, 5680.0}, {8, 32, 5900.0}};
+
+void choose_mode_shape(int64_t m, int *lanes, int *rows) {
+    double best = 1e300;
+    for (const ShapeRate &c : kModeShapes) {
+        const int64_t tr = int64_t(c.lanes) * c.rows;
+        const double t = double((m + tr - 1) / tr * tr) / c.gcups;
+        if (t < best) {
+            best = t;
+            *lanes = c.lanes;
+            *rows = c.rows;
+        }
+    }
+}
+
+// Columns of strip-boundary scratch per subwarp of the int16x2 mode kernel: a
+// query taller than one strip sends longer sequences to the int32 kernel.
+constexpr int32_t kMode16Cols = 4096;
+
 constexpr ShapeRate kBatchShapes[] = {{8, 16, 5000.0}, {8, 24, 5850.0}, {8, 32, 5850.0}};
 
 int choose_batch_shape(int64_t m) {
@@ -231,11 +251,25 @@ struct Plan {
     int32_t inter_min_lanes = 8;     // sets the most pairs per CTA
     int32_t inter_max_cols = 0;      // columns of the longest non-long pair
     bool inter_scratch = false;
-    // non-local alignment modes (k_modes.cu)
+    // non-local alignment modes (k_modes.cu; k_modes16.cu when precision is int16x2)
     int32_t alignment = SW_ALIGN_LOCAL;
-    int32_t mode_grid = 0;           // persistent CTAs
-    int64_t mode_mpad = 0;           // profile rows, a multiple of the 256-row strip
+    int32_t mode_grid = 0;           // persistent CTAs of the int32 kernel
+    int32_t smax_pos = 0;            // max(S, 0)
+    int32_t mode16_grid_max = 0;     // persistent CTAs of the int16x2 kernel (largest over its shapes)
+    int32_t mode16_cols = 0;         // scratch columns per subwarp (0: every query fits one strip)
+    // per query: shape of the int16x2 launch and its first pair (the pairs
+    // before it go to the int32 kernel)
+    std::vector<int32_t> mode16_lanes, mode16_rows;
+    std::vector<int64_t> mode16_cut;
+    int64_t mode_i32_cells = 0;      // cells scored by the int32 kernel
+    // the int32 kernel's work: one entry per query with sequences for it
+    // (longest query first), its profiles packed one after another
+    std::vector<ModeEntry> mode_entries;
+    int64_t mode_items = 0;
+    int64_t mode_prof_ints = 0;
 };
+
+int64_t mode16_first_pair(const sw_db *db, const Plan &p, int32_t m, int tr, int32_t o, int32_t e);
 
 // Choose arithmetic and launch shapes for this call.
 int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int32_t *matrix,
@@ -273,11 +307,69 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
             return fail(SW_ERR_OVERFLOW, "lengths, matrix entries or penalties too large for exact int32 "
                                          "scores of this alignment mode");
         p.alignment = alignment;
-        p.precision = SW_PREC_I32;
         p.mode = SW_MODE_PLAIN;
         p.mode_grid = modes_slots(std::max(1, db->sm_count));
         if (p.mode_grid <= 0) return fail(SW_ERR_CUDA, "could not size the alignment-mode grid");
-        p.mode_mpad = round_up(std::max<int64_t>(p.max_m, 1), modes_strip_rows());
+        // int16x2 (k_modes16.cu) where the int8 profile holds S + o and the
+        // virtual rows' o; each pair's own bounds are checked per query.
+        const bool fits16 = (int64_t(smax) + o <= 127) && (int64_t(smin) + o >= -128) && (o <= 127);
+        const int want = opts ? opts->precision : SW_PREC_AUTO;
+        if (want < 0 || want > SW_PREC_I32) return fail(SW_ERR_INVALID_ARG, "unknown precision");
+        if (want == SW_PREC_I16 && !fits16)
+            return fail(SW_ERR_UNSUPPORTED, "matrix or penalties do not fit the int16x2 alignment-mode kernel");
+        p.precision = (want != SW_PREC_I32 && fits16) ? SW_PREC_I16 : SW_PREC_I32;
+        p.smax_pos = std::max(smax, 0);
+        if (p.precision == SW_PREC_I16) {
+            const int sms = std::max(1, db->sm_count);
+            p.auto_shape = !(opts && (opts->lanes || opts->rows_per_lane));
+            if (!p.auto_shape) {
+                const int l = opts->lanes ? opts->lanes : 8, r = opts->rows_per_lane ? opts->rows_per_lane : 32;
+                if (!modes16_config_supported(l, r))
+                    return fail(SW_ERR_UNSUPPORTED, "lanes/rows_per_lane combination not built for the alignment modes");
+                p.lanes = l;
+                p.rows = r;
+            }
+            int min_tr = 1 << 30;
+            for (const ShapeRate &c : kModeShapes) {
+                if (!p.auto_shape && (c.lanes != p.lanes || c.rows != p.rows)) continue;
+                p.mode16_grid_max = std::max(p.mode16_grid_max, modes16_slots(c.lanes, c.rows, sms));
+                min_tr = std::min(min_tr, c.lanes * c.rows);
+            }
+            if (p.mode16_grid_max <= 0) return fail(SW_ERR_CUDA, "could not size the int16x2 alignment-mode grid");
+            p.mode16_cols = p.max_m > min_tr ? kMode16Cols : 0;
+        }
+        for (int32_t i = 0; i < n_q; ++i) {
+            const int32_t m = int32_t(q_offsets[i + 1] - q_offsets[i]);
+            int l = p.lanes, r = p.rows;
+            if (p.precision == SW_PREC_I16 && p.auto_shape) choose_mode_shape(m, &l, &r);
+            const int64_t cut = mode16_first_pair(db, p, m, l * r, o, e);
+            int64_t res = 0;
+            for (int64_t t = 0; t < 2 * cut && t < int64_t(db->h_len.size()); ++t) res += db->h_len[size_t(t)];
+            p.mode16_lanes.push_back(l);
+            p.mode16_rows.push_back(r);
+            p.mode16_cut.push_back(cut);
+            if (p.precision == SW_PREC_I16 && m > 0 && cut > 0) {   // the int32 kernel takes these pairs
+                p.mode_i32_cells += int64_t(m) * res;
+                p.n_long = std::max<int64_t>(p.n_long, std::min<int64_t>(2 * cut, db->n_seqs));
+            }
+            if (cut > 0) {
+                ModeEntry en;
+                memset(&en, 0, sizeof en);
+                en.n_seqs = 2 * cut;
+                en.query = i;
+                en.m = m;
+                en.m_pad = int32_t(round_up(std::max<int64_t>(m, 1), modes_strip_rows()));
+                p.mode_entries.push_back(en);
+            }
+        }
+        std::stable_sort(p.mode_entries.begin(), p.mode_entries.end(),
+                         [](const ModeEntry &x, const ModeEntry &y) { return x.m > y.m; });
+        for (ModeEntry &en : p.mode_entries) {
+            en.item_start = p.mode_items;
+            en.prof_off = p.mode_prof_ints;
+            p.mode_items += en.n_seqs;
+            p.mode_prof_ints += int64_t(kProfRows) * en.m_pad;
+        }
         *plan = std::move(p);
         return SW_OK;
     }
@@ -462,12 +554,47 @@ struct Buffers {
     int32_t *qp = nullptr;            // batched mode: qp_a then qp_b
     uint2 *batch_scratch = nullptr;   // batched mode: per CTA slot boundary rows
     uint2 *inter_scratch = nullptr;   // plain mode: per CTA slot boundary rows
-    int32_t *mode_prof = nullptr;     // alignment modes: [32][mode_mpad] S(q_i, c) + o
+    int32_t *mode_prof = nullptr;     // alignment modes, int32 kernel: per entry [32][m_pad] S(q_i, c) + o
+    ModeEntry *mode_entries = nullptr;
+    unsigned long long *mode_counter = nullptr;
     int2 *mode_bnd = nullptr;         // alignment modes: per warp slot, max_len + 1 (H, F)
+    uint2 *mode16_scratch = nullptr;  // int16x2 alignment modes: per CTA slot boundary rows
     int32_t *ovf_list = nullptr;
     int32_t *counters = nullptr;   // [n_q] list lengths, [n_q] work counters, [n_q] flagged sequences,
                                    // then one status word
 };
+
+// First pair of the sorted database whose alignment-mode scores against a
+// query of m rows provably stay inside int16 in k_modes16.cu; the pairs
+// before it (the longest) go to the int32 kernel.  With Lp the pair's
+// columns, every H lies between min_i H(i, 0) - g(Lp) (the E chain along a
+// row) >= -g(m) - g(Lp) (overlap: -g(Lp)) and max(S, 0) * min(m, Lp); the
+// kernel's intermediate values reach at most o + max(e, 128) below the
+// lower bound (gap and profile addends) and max(S) above the upper one.  Both
+// bounds grow with Lp, which falls along the sorted order, so the pairs that
+// fit are a suffix.
+int64_t mode16_first_pair(const sw_db *db, const Plan &p, int32_t m, int tr, int32_t o, int32_t e) {
+    const int64_t n_pairs = db->n_sorted / 2;
+    if (p.precision != SW_PREC_I16 || m <= 0) return n_pairs;
+    const int64_t gmin = std::min(o, e);
+    auto g = [&](int64_t k) { return k <= 0 ? int64_t(0) : int64_t(o) + (k - 1) * gmin; };
+    const bool multi = m > tr;
+    const int64_t gm = p.alignment == SW_ALIGN_OVERLAP ? 0 : g(m);
+    auto ok = [&](int64_t pair) {
+        const int64_t Lp = round_up(db->h_len[size_t(2 * pair)], 4);
+        if (multi && Lp > kMode16Cols) return false;
+        if (gm + g(Lp) + o + std::max<int64_t>(e, 128) > 32768) return false;
+        if (int64_t(p.smax_pos) * (std::min<int64_t>(m, Lp) + 1) > 32767) return false;
+        return true;
+    };
+    int64_t lo = 0, hi = n_pairs;   // the first pair that fits lies in [lo, hi]
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (ok(mid)) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
 
 size_t carve(const sw_db *db, const Plan &p, int32_t n_q, int32_t top_k, bool q_dev, bool s_dev,
              bool h_dev, void *base, size_t cap, Buffers *b) {
@@ -497,9 +624,14 @@ size_t carve(const sw_db *db, const Plan &p, int32_t n_q, int32_t top_k, bool q_
                                                       size_t(kCtaThreads / p.inter_min_lanes) *
                                                       size_t(p.inter_max_cols)));
     if (p.alignment != SW_ALIGN_LOCAL) {
-        x.mode_prof = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(kProfRows) * size_t(p.mode_mpad)));
+        x.mode_prof = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(std::max<int64_t>(p.mode_prof_ints, 1))));
+        x.mode_entries = static_cast<ModeEntry *>(c.take(sizeof(ModeEntry) * std::max<size_t>(p.mode_entries.size(), 1)));
+        x.mode_counter = static_cast<unsigned long long *>(c.take(sizeof(unsigned long long)));
         x.mode_bnd = static_cast<int2 *>(c.take(sizeof(int2) * size_t(p.mode_grid) * size_t(kCtaThreads / 32) *
                                                 size_t(db->max_len + 1)));
+        if (p.precision == SW_PREC_I16 && p.mode16_cols > 0)
+            x.mode16_scratch = static_cast<uint2 *>(c.take(sizeof(uint2) * size_t(p.mode16_grid_max) *
+                                                           size_t(kCtaThreads / 8) * size_t(p.mode16_cols)));
     }
     // [n_q] list lengths, [n_q] work counters, [n_q] flagged, [n_q] chunk counters,
     // status, 4 tile counters
@@ -838,6 +970,9 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
     const int32_t n_qp = int32_t(plan.qp_a.size());
 
     // Host-to-device inputs first: they stay outside any captured graph.
+    if (!plan.mode_entries.empty())
+        SW_CUDA_TRY(cudaMemcpyAsync(buf.mode_entries, plan.mode_entries.data(),
+                                    sizeof(ModeEntry) * plan.mode_entries.size(), cudaMemcpyHostToDevice, st));
     if ((split || plan.mode == SW_MODE_BATCHED) && n_q > 0)
         SW_CUDA_TRY(cudaMemcpyAsync(buf.q_off, q_offsets, sizeof(int64_t) * size_t(n_q + 1), cudaMemcpyHostToDevice, st));
     if (plan.mode == SW_MODE_BATCHED && n_qp > 0) {
@@ -853,30 +988,74 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
     SW_CUDA_TRY(cudaMemsetAsync(buf.counters, 0, sizeof(int32_t) * (4 * size_t(std::max<int32_t>(n_q, 1)) + 5), st));
 
     if (plan.alignment != SW_ALIGN_LOCAL) {
-        // Non-local modes: per query, its profile S(q_i, c) + o and one persistent
-        // launch over every sequence (k_modes.cu), then the top-k.
-        for (int32_t qi = 0; qi < n_q; ++qi) {
-            const int64_t q0 = q_offsets[qi];
-            const int32_t m = int32_t(q_offsets[qi + 1] - q0);
-            if (m > 0)
-                TIMED(LaunchTimer::OTHER, launch_profile32(d_queries + q0, m, int32_t(plan.mode_mpad), matrix, db->A,
-                                                           gap_open, buf.mode_prof, st));
+        // Non-local modes, per query: the pairs whose scores provably fit int16
+        // (a suffix of the sorted order) in one persistent int16x2 launch
+        // (k_modes16.cu); the longer ones, with the query's int32 profile
+        // S(q_i, c) + o, in the int32 kernel (k_modes.cu), on the side stream
+        // when both run.  Then the top-k.
+        const bool packed = plan.precision == SW_PREC_I16;
+        cudaStream_t s32 = packed ? db->side : st;
+        const bool forked = packed && !plan.mode_entries.empty();
+        if (!plan.mode_entries.empty()) {
+            if (forked) {
+                SW_CUDA_TRY(cudaEventRecord(db->ev_fork, st));
+                SW_CUDA_TRY(cudaStreamWaitEvent(db->side, db->ev_fork, 0));
+            }
+            for (const ModeEntry &en : plan.mode_entries)
+                if (en.m > 0)
+                    TIMED_ON(LaunchTimer::OTHER, s32,
+                             launch_profile32(d_queries + q_offsets[en.query], en.m, en.m_pad, matrix, db->A,
+                                              gap_open, buf.mode_prof + en.prof_off, s32));
+            SW_CUDA_TRY(cudaMemsetAsync(buf.mode_counter, 0, sizeof(unsigned long long), s32));
             ModeArgs ma;
             memset(&ma, 0, sizeof ma);
             ma.db = db->view();
-            ma.seq_begin = 0;
-            ma.seq_end = db->n_sorted;
+            ma.entries = buf.mode_entries;
+            ma.n_entries = int32_t(plan.mode_entries.size());
+            ma.n_items = plan.mode_items;
             ma.prof = buf.mode_prof;
-            ma.m = m;
-            ma.m_pad = int32_t(plan.mode_mpad);
             ma.gap_open = gap_open;
             ma.gap_extend = gap_extend;
             ma.mode = plan.alignment;
             ma.max_cols = int32_t(db->max_len);
             ma.boundary = buf.mode_bnd;
-            ma.work_counter = buf.counters + n_q + qi;
-            ma.scores = d_scores + int64_t(qi) * db->n_seqs;
-            TIMED(LaunchTimer::INTER, launch_modes_i32(ma, plan.mode_grid, st));
+            ma.work_counter = buf.mode_counter;
+            ma.scores = d_scores;
+            ma.scores_stride = db->n_seqs;
+            TIMED_ON(packed ? LaunchTimer::INTRA : LaunchTimer::INTER, s32, launch_modes_i32(ma, plan.mode_grid, s32));
+        }
+        for (int32_t qi = 0; qi < n_q; ++qi) {
+            const int64_t q0 = q_offsets[qi];
+            const int32_t m = int32_t(q_offsets[qi + 1] - q0);
+            const int lanes = plan.mode16_lanes[size_t(qi)], rows = plan.mode16_rows[size_t(qi)];
+            const int tr = lanes * rows;
+            const int64_t cut = plan.mode16_cut[size_t(qi)];
+            if (cut < n_pairs) {
+                Mode16Args a16;
+                memset(&a16, 0, sizeof a16);
+                a16.db = db->view();
+                a16.pair_begin = cut;
+                a16.pair_end = n_pairs;
+                a16.query = d_queries + q0;
+                a16.m = m;
+                a16.virt_rows = int32_t(round_up(m, tr) - m);
+                a16.gap_open = gap_open;
+                a16.gap_extend = gap_extend;
+                memcpy(a16.prof8, ia.prof8, sizeof a16.prof8);
+                a16.boundary = m > tr ? buf.mode16_scratch : nullptr;
+                a16.slot_stride = int64_t(kCtaThreads / 8) * plan.mode16_cols;
+                a16.max_cols = plan.mode16_cols;
+                a16.chunk_counter = buf.counters + 3 * n_q + qi;
+                a16.scores = d_scores + int64_t(qi) * db->n_seqs;
+                TIMED(LaunchTimer::INTER, launch_modes_i16x2(a16, plan.alignment, lanes, rows,
+                                                              plan.mode16_grid_max, st));
+                last_lanes = lanes;
+                last_rows = rows;
+            }
+        }
+        if (forked) {
+            SW_CUDA_TRY(cudaEventRecord(db->ev_join, db->side));
+            SW_CUDA_TRY(cudaStreamWaitEvent(st, db->ev_join, 0));
         }
         if (top_k > 0 && n_q > 0 && (hits_out != nullptr))
             TIMED(LaunchTimer::OTHER, launch_topk(d_scores, n_q, db->n_seqs, top_k, d_hits, st));
@@ -1058,8 +1237,14 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
         } else {
             graph_replayed = true;
             // the plan's per-query launch shapes are the same as when captured
-            if (plan.precision == SW_PREC_I16 && plan.mode == SW_MODE_PLAIN && plan.auto_shape && n_q > 0)
+            if (plan.alignment != SW_ALIGN_LOCAL) {
+                if (plan.precision == SW_PREC_I16 && n_q > 0) {
+                    last_lanes = plan.mode16_lanes.back();
+                    last_rows = plan.mode16_rows.back();
+                }
+            } else if (plan.precision == SW_PREC_I16 && plan.mode == SW_MODE_PLAIN && plan.auto_shape && n_q > 0) {
                 choose_shape(q_offsets[n_q] - q_offsets[n_q - 1], &last_lanes, &last_rows);
+            }
         }
         SW_CUDA_TRY(cudaGraphLaunch(db->graph_exec, st));
     } else {
@@ -1090,7 +1275,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
             for (int32_t i = 0; i < n_q; ++i) r += cnt[size_t(i)];
         stats->rescored = r;
         stats->long_sequences = plan.n_long;
-        stats->long_cells = plan.total_m * plan.long_residues;
+        stats->long_cells = plan.alignment != SW_ALIGN_LOCAL ? plan.mode_i32_cells : plan.total_m * plan.long_residues;
         stats->inter_cells = stats->cells - stats->long_cells;
         stats->precision_used = plan.precision;
         stats->mode_used = plan.mode;

@@ -10,8 +10,10 @@
 //   overlap      H(i,0) = H(0,j) = 0;            score max(max_j H(m,j), max_i H(i,n))
 //
 // with g(k) = o + (k-1)*min(o,e), the first column's own recurrence from
-// H(0,0) = 0.  Scores can be negative, so these modes run in exact int32
-// (the host rejects inputs whose values could leave +-2^29).
+// H(0,0) = 0.  Scores can be negative.  This kernel computes them in exact
+// int32 (the host rejects inputs whose values could leave +-2^29) for the
+// pairs the packed int16x2 kernel (k_modes16.cu) cannot take exactly (the
+// longest sequences), or for every pair when int32 is requested.
 //
 // One warp per database sequence: lane k holds query rows 8k+1 .. 8k+8 of a
 // 256-row strip and runs one column behind lane k-1 (H and F of a lane's
@@ -23,10 +25,14 @@
 // global memory (H - o of the strip's last row and F of the row below),
 // rewritten in place: lane 31 writes column j - 30 while lane 0 prefetches
 // column j + 2, so a column is always read before it is rewritten.
-// Warps take sequences from an atomic counter, longest first.
+// Warps take (query, sequence) items from one atomic counter: the queries'
+// entries one after another (the host orders them longest query first), each
+// entry's sequences longest first, so the longest items start first and the
+// queries' long sequences run side by side rather than one launch after another.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "../../include/swdb.h"
@@ -54,15 +60,25 @@ __global__ void __launch_bounds__(kCtaThreads) k_modes_i32(const __grid_constant
     int2 *bnd = a.boundary + int64_t(warp_slot) * (a.max_cols + 1);
     const int mode = a.mode;
     const int32_t o = a.gap_open, e = a.gap_extend, gmin = e < o ? e : o;
-    const int m = a.m;
-    const int64_t count = a.seq_end - a.seq_begin;
 
     for (;;) {
         int64_t item = 0;
-        if (lane == 0) item = atomicAdd(a.work_counter, 1);
+        if (lane == 0) item = int64_t(atomicAdd(a.work_counter, 1ull));
         item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= count) break;
-        const int64_t s = a.seq_begin + item;
+        if (item >= a.n_items) break;
+        // the entry holding this item: the last with item_start <= item
+        int lo = 0, hi = a.n_entries - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.entries[mid].item_start <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const ModeEntry &en = a.entries[lo];
+        const int64_t s = item - en.item_start;
+        const int m = en.m;
+        const int m_pad = en.m_pad;
+        const int32_t *prof = a.prof + en.prof_off;
+        int32_t *scores = a.scores + int64_t(en.query) * a.scores_stride;
         const int64_t orig = a.db.perm[s];
         if (orig < 0) continue;                              // padding slot of the last bundle
         const int n = a.db.len[s];
@@ -71,7 +87,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_modes_i32(const __grid_constant
                 int32_t v = 0;
                 if (mode == SW_ALIGN_GLOBAL) v = -lead_gap(m == 0 ? n : m, o, gmin);
                 else if (mode == SW_ALIGN_SEMIGLOBAL) v = (n == 0) ? -lead_gap(m, o, gmin) : 0;
-                a.scores[orig] = v;
+                scores[orig] = v;
             }
             continue;
         }
@@ -107,7 +123,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_modes_i32(const __grid_constant
             }
             const bool more = r0 + kMStrip < m;
             const int rm = m - row0;                         // index of row m in this lane, if 0..7
-            const int32_t *prow = a.prof + r0 + lane * kMR;
+            const int32_t *prow = prof + r0 + lane * kMR;
             // One column step.  STEADY: every lane inside its sequence and none at
             // the last column (31 <= st <= n - 2), so the range checks fold away.
             auto step = [&](const int st, auto steady_c) {
@@ -136,7 +152,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_modes_i32(const __grid_constant
                         }
                     }
                     const int c = cin;
-                    const int4 *pp = reinterpret_cast<const int4 *>(prow + int64_t(c) * a.m_pad);
+                    const int4 *pp = reinterpret_cast<const int4 *>(prow + int64_t(c) * m_pad);
                     int32_t sc[kMR];
 #pragma unroll
                     for (int v = 0; v < kMR / 4; ++v) {
@@ -191,7 +207,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_modes_i32(const __grid_constant
             if (mode == SW_ALIGN_GLOBAL) v = hmn;
             else if (mode == SW_ALIGN_SEMIGLOBAL) v = max(last_row, -lead_gap(m, o, gmin));   // j = 0 too
             else v = max(max(last_row, last_col), 0);          // H(m,0) = H(0,n) = 0
-            a.scores[orig] = v;
+            scores[orig] = v;
         }
     }
 }
@@ -199,8 +215,11 @@ __global__ void __launch_bounds__(kCtaThreads) k_modes_i32(const __grid_constant
 }  // namespace
 
 cudaError_t launch_modes_i32(const ModeArgs &a, int grid, cudaStream_t s) {
-    if (a.seq_end <= a.seq_begin) return cudaSuccess;
-    k_modes_i32<<<grid, kCtaThreads, 0, s>>>(a);
+    if (a.n_items <= 0 || a.n_entries <= 0) return cudaSuccess;
+    if (!a.entries || !a.work_counter || grid <= 0) return cudaErrorInvalidValue;
+    const int64_t warps = kCtaThreads / 32;
+    const int64_t need = (a.n_items + warps - 1) / warps;
+    k_modes_i32<<<unsigned(std::min<int64_t>(grid, need)), kCtaThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -168,18 +168,52 @@ struct AlignArgs {
     int32_t gap_open, gap_extend;
 };
 
-// Non-local alignment modes (k_modes.cu): one query against the sorted
-// sequences [seq_begin, seq_end), one warp per sequence.
+// Non-local alignment modes in int32 (k_modes.cu): several queries, each
+// against a prefix [0, n_seqs) of the sorted database, in one launch, one warp
+// per (query, sequence) item.  Items are numbered entry by entry (entry e
+// owns items [item_start[e], item_start[e] + n_seqs)), and within an entry
+// longest sequence first.
+struct ModeEntry {
+    int64_t item_start;         // first item of this entry
+    int64_t n_seqs;             // sorted sequences [0, n_seqs)
+    int64_t prof_off;           // the query's profile in prof (int32 units)
+    int32_t query;              // score row
+    int32_t m;                  // query length
+    int32_t m_pad;              // m rounded up to the 256-row strip (profile row stride)
+    int32_t pad;
+};
 struct ModeArgs {
     DbView db;
-    int64_t seq_begin, seq_end;
-    const int32_t *prof;        // [kProfRows][m_pad] = S(q_i, c) + o, pads -2^28
-    int32_t m, m_pad;           // m_pad a multiple of 256
+    const ModeEntry *entries;   // device, n_entries, item_start increasing
+    int32_t n_entries;
+    int64_t n_items;            // items of all entries
+    const int32_t *prof;        // per entry [kProfRows][m_pad] = S(q_i, c) + o, pads -2^28
     int32_t gap_open, gap_extend;
     int32_t mode;               // SW_ALIGN_GLOBAL / SEMIGLOBAL / OVERLAP
     int32_t max_cols;           // longest sequence; each warp slot owns max_cols + 1 int2
     int2 *boundary;             // grid * 8 warp slots
-    int32_t *work_counter;      // zeroed before launch
+    unsigned long long *work_counter;   // zeroed before launch
+    int32_t *scores;            // [n_q][n_seqs], original database order
+    int64_t scores_stride;      // n_seqs
+};
+
+// Non-local alignment modes in packed int16x2 (k_modes16.cu): one query
+// against the pairs [pair_begin, pair_end) of the sorted database, every one
+// of which the host has shown to stay inside int16 (no saturation check on
+// the device).  The query is padded at the TOP with virt_rows rows so that
+// m + virt_rows is a whole number of strips and row m is the last row of the
+// last lane.
+struct Mode16Args {
+    DbView db;
+    int64_t pair_begin, pair_end;
+    const uint8_t *query;       // device, m codes
+    int32_t m, virt_rows;
+    int32_t gap_open, gap_extend;
+    int8_t prof8[kProfRows][kProfRows];  // [query code][db code] = S + o, pads = -128
+    uint2 *boundary;            // per CTA slot, max_cols entries per subwarp (null: one strip)
+    int64_t slot_stride;        // uint2 entries per CTA slot
+    int32_t max_cols;           // >= every pair's columns (a multiple of 4)
+    int32_t *chunk_counter;     // zeroed before launch
     int32_t *scores;            // row of this query, original database order
 };
 
@@ -203,9 +237,12 @@ bool i32_config_supported(int lanes, int rows);
 cudaError_t launch_probe(int mode, int grid, int iters, unsigned long long *cycles, uint32_t *sink,
                          cudaStream_t s);
 int probe_blocks_per_sm(int mode);
-cudaError_t launch_modes_i32(const ModeArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_modes_i32(const ModeArgs &a, int grid, cudaStream_t s);   // grid capped by the items
 int modes_slots(int sms);            // resident CTAs of the modes kernel
 int32_t modes_strip_rows();
+cudaError_t launch_modes_i16x2(const Mode16Args &a, int mode, int lanes, int rows, int grid, cudaStream_t s);
+bool modes16_config_supported(int lanes, int rows);
+int modes16_slots(int lanes, int rows, int sms);   // resident CTAs (the largest over the three modes)
 cudaError_t launch_wait_probe(long long limit, int32_t *status, cudaStream_t s);   // limit 1 .. 2^25
 cudaError_t launch_align(const AlignArgs &a, int which, cudaStream_t s);   // 0 forward, 1 traceback
 int64_t align_checkpoint_rows(int32_t m);

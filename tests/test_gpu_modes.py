@@ -35,7 +35,10 @@ def test_blosum62_strips_and_tails(gpu, mode):
     scores, st = _check(gpu, qs, db, synth.blosum62(), 10, 1, mode)
     if mode == "global":
         assert (scores < 0).any()
-    assert st["precision_used"] == gpu.SW_PREC_I32
+    assert st["precision_used"] == gpu.SW_PREC_I16
+    assert st["long_cells"] == 0                      # every pair fits the packed kernel
+    _, st32 = _check(gpu, qs, db, synth.blosum62(), 10, 1, mode, precision=gpu.SW_PREC_I32)
+    assert st32["precision_used"] == gpu.SW_PREC_I32
 
 
 @pytest.mark.parametrize("mode", sorted(MODES))
@@ -123,3 +126,80 @@ def test_workspace_and_graph(gpu):
                 ws_, wi = oracle.top_k(want[i], 5)
                 np.testing.assert_array_equal((h[i, :, 0] & 0xffffffff).astype(np.int64).astype(np.int32), ws_)
                 np.testing.assert_array_equal(h[i, :, 1], wi)
+
+
+# ---- packed int16x2 kernel (k_modes16.cu) ----------------------------------
+
+@pytest.mark.parametrize("rows", [16, 24, 32])
+@pytest.mark.parametrize("mode", sorted(MODES))
+def test_packed_shapes_and_virtual_rows(gpu, mode, rows):
+    """Each shape, with queries that fill whole strips (no virtual rows) and
+    queries padded at the top (1 .. 8*rows - 1 virtual rows), one and several
+    strips, against pairs of unequal and empty sequences."""
+    rng = np.random.default_rng(500 + rows + MODES[mode])
+    tr = 8 * rows
+    db = synth.seqset_from_lengths(rng, np.concatenate([rng.integers(1, 500, 120), [0, 1, 2, 3, 4, 5, 257, 600]]))
+    qs = synth.seqset_from_lengths(rng, [1, tr - 1, tr, tr + 1, 2 * tr, 3 * tr - 5])
+    _, st = _check(gpu, qs, db, synth.blosum62(), 10, 1, mode, lanes=8, rows_per_lane=rows)
+    assert st["precision_used"] == gpu.SW_PREC_I16
+    assert st["rows_per_lane_used"] == rows
+    assert st["long_cells"] == 0
+
+
+@pytest.mark.parametrize("mode", sorted(MODES))
+@pytest.mark.parametrize("o,e", [(10, 1), (3, 7), (0, 2), (5, 5)])
+def test_packed_equals_int32_and_oracle(gpu, mode, o, e):
+    """Random non-symmetric matrices; open above, below and equal to extend, and free opening
+    (the global virtual rows then score S = -min(o, e) with H(v, 0) = -(o - min(o, e)) = 0 or not)."""
+    rng = np.random.default_rng(600 + 7 * o + e + MODES[mode])
+    S = synth.random_matrix(rng, 20, -6, 9, symmetric=False)
+    db = synth.random_seqset(rng, 90, 0, 700, 20)
+    qs = synth.random_seqset(rng, 4, 1, 900, 20)
+    packed, st = _check(gpu, qs, db, S, o, e, mode)
+    assert st["precision_used"] == gpu.SW_PREC_I16
+    i32, _ = _check(gpu, qs, db, S, o, e, mode, precision=gpu.SW_PREC_I32)
+    np.testing.assert_array_equal(packed, i32)
+
+
+@pytest.mark.parametrize("mode", sorted(MODES))
+def test_packed_lower_bound_edge(gpu, mode):
+    """o = 10, e = 1: g(k) = k + 9.  A pair of Lp columns (the longer length rounded up to
+    4) runs packed when g(m) (0 for overlap) + g(Lp) + o + 128 <= 32768.  The pair at the
+    largest such Lp runs packed, with global scores near -32,500; the pair above it, int32."""
+    rng = np.random.default_rng(700 + MODES[mode])
+    m = 100
+    gm = 0 if mode == "overlap" else m + 9
+    lp = 32768 - 10 - 128 - 9 - gm
+    lp -= lp % 4
+    db = synth.seqset_from_lengths(rng, [lp + 1, lp + 1, lp, lp - 3, 2000, 10])
+    qs = synth.seqset_from_lengths(rng, [m])
+    scores, st = _check(gpu, qs, db, synth.blosum62(), 10, 1, mode, k=6)
+    assert st["long_cells"] == m * 2 * (lp + 1)        # only the first pair went to int32
+    if mode == "global":
+        assert scores[0, 2] < -32000
+
+
+@pytest.mark.parametrize("mode", sorted(MODES))
+def test_packed_upper_bound_edge(gpu, mode):
+    """BLOSUM62 max(S) = 11 (W/W).  A pair runs packed when 11 * (min(m, Lp) + 1) <= 32767,
+    i.e. min(m, Lp) <= 2977: an all-W query of 2977 against an all-W target of 2977 scores
+    11 * 2977 = 32,747 in the packed kernel; a query of 2978 sends that pair to int32."""
+    w = synth.ALPHABET.index("W")
+    rng = np.random.default_rng(800 + MODES[mode])
+    other = synth.seqset_from_lengths(rng, [500])
+    db = synth.seqset_from_list([np.full(2977, w), np.full(2977, w), other.residues, np.full(3, w)])
+    qs = synth.seqset_from_list([np.full(2977, w), np.full(2978, w)])
+    scores, st = _check(gpu, qs, db, synth.blosum62(), 10, 1, mode, k=4)
+    assert scores[0, 0] == 11 * 2977
+    assert st["long_cells"] == 2978 * 2 * 2977         # query 2's first pair only
+
+
+@pytest.mark.parametrize("mode", sorted(MODES))
+def test_packed_column_cap_of_taller_queries(gpu, mode):
+    """A query taller than one strip keeps strip-boundary rows for at most 4096 columns:
+    a pair of 4100 columns goes to int32, one of exactly 4096 runs packed."""
+    rng = np.random.default_rng(900 + MODES[mode])
+    db = synth.seqset_from_lengths(rng, [4097, 4096, 4093, 100, 64])
+    qs = synth.seqset_from_lengths(rng, [300, 90])
+    _, st = _check(gpu, qs, db, synth.blosum62(), 10, 1, mode, k=5)
+    assert st["long_cells"] == 300 * (4097 + 4096)     # the 90-row query fits one strip: no cap
