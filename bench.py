@@ -222,19 +222,22 @@ def launch_key(args) -> str:
 
 
 def traffic_per_launch(args):
-    """Average DRAM bytes (read + written) per inter-task launch, from the
-    committed ncu record of every launch of one step of this same launch
-    configuration, if it was taken on the current kernel source (else None)."""
-    src = os.path.join(ROOT, "paper_2203_11100_gb300", "csrc", "k_inter16.cu")
+    """Average DRAM bytes (read + written) per launch of the step's dominant
+    kernel, from the committed ncu record of every launch of one step of this
+    same launch configuration, if it was taken on the current source of that
+    kernel (the record's source= file, k_inter16.cu when absent; else None)."""
+    csrc = os.path.join(ROOT, "paper_2203_11100_gb300", "csrc")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
         key = launch_key(args)
         for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
             for line in open(path):
                 if not line.startswith("traffic:"):
                     continue
                 rec = dict(kv.split("=", 1) for kv in line.split()[1:])
-                if rec.get("launch") == key and rec.get("source_sha256") == sha:
+                if rec.get("launch") != key:
+                    continue
+                src = os.path.join(csrc, os.path.basename(rec.get("source", "k_inter16.cu")))
+                if rec.get("source_sha256") == hashlib.sha256(open(src, "rb").read()).hexdigest():
                     return float(rec["dram_bytes_per_launch"])
     except Exception:
         return None
