@@ -63,7 +63,7 @@ def parse_args(argv=None):
     p.add_argument("--lanes", type=int, default=0)
     p.add_argument("--rows", type=int, default=0)
     p.add_argument("--precision", type=int, default=0)
-    p.add_argument("--long-rows", type=int, default=0, help="rows per lane of the intra-task kernel (16 or 32)")
+    p.add_argument("--long-rows", type=int, default=0, help="rows per lane of the intra-task kernel (8, 16 or 32)")
     p.add_argument("--long-cutoff", type=int, default=0,
                    help="database sequences longer than this go to the intra-task kernel (0 = library default)")
     p.add_argument("--mode", choices=["plain", "batched"], default="plain",

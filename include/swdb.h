@@ -121,7 +121,7 @@ typedef struct {
     void *workspace;          /* caller-owned device scratch, or NULL for the handle's own */
     size_t workspace_bytes;   /* size of workspace */
     int32_t flags;            /* SW_FLAG_* bits */
-    int32_t long_rows_per_lane; /* query rows per lane of the intra-task kernel: 16 (4-warp
+    int32_t long_rows_per_lane; /* query rows per lane of the intra-task kernel: 8 or 16 (4-warp
                                    pipelines) or 32 (2-warp pipelines); 0 = library choice */
     int32_t alignment;        /* sw_alignment_mode; 0 = local */
     int32_t reserved;

@@ -195,6 +195,11 @@ void choose_mode_shape(int64_t m, int *lanes, int *rows) {
     }
 }
 
+// The long-sequence path for few tasks of short queries (see Plan::long_inter):
+// the inter-task kernel at 32 lanes x 8 rows, one 256-row strip.
+constexpr int kLongInterLanes = 32;
+constexpr int kLongInterRows = 256;
+
 // Columns of strip-boundary scratch per subwarp of the int16x2 mode kernel: a
 // query taller than one strip sends longer sequences to the int32 kernel.
 constexpr int32_t kMode16Cols = 4096;
@@ -229,6 +234,10 @@ struct Plan {
     int warps_long = 2;
     int64_t long_codes_bytes = 0;          // layout bytes of the long bundles (a prefix)
     bool need_long_boundary = false;
+    // few (long pair, query) tasks and every query within one 256-row strip:
+    // the long pairs go through the inter-task kernel at 32 lanes x 8 rows
+    // (the shortest per-column chain) instead of the intra-task kernel
+    bool long_inter = false;
     // batched mode: query pairs (a = longer, b = next, -1 if none), persistent grid
     std::vector<int32_t> qp_a, qp_b;
     struct BatchGroup {
@@ -435,9 +444,10 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
     // handful of very long sequences do not set the length of the main launch.
     const int64_t cutoff = opts && opts->long_cutoff ? opts->long_cutoff : 3072;
     if (opts && opts->long_rows_per_lane) {
-        if (opts->long_rows_per_lane == 16) { p.rows_long = 16; p.warps_long = 4; }
+        if (opts->long_rows_per_lane == 8) { p.rows_long = 8; p.warps_long = 4; }
+        else if (opts->long_rows_per_lane == 16) { p.rows_long = 16; p.warps_long = 4; }
         else if (opts->long_rows_per_lane == 32) { p.rows_long = 32; p.warps_long = 2; }
-        else return fail(SW_ERR_UNSUPPORTED, "long_rows_per_lane must be 16 or 32");
+        else return fail(SW_ERR_UNSUPPORTED, "long_rows_per_lane must be 8, 16 or 32");
     }
     int64_t nlb = 0;
     if (cutoff > 0 && p.precision == SW_PREC_I16)
@@ -458,10 +468,13 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
         int32_t nonempty = 0;
         for (int32_t i = 0; i < n_q; ++i) nonempty += q_offsets[i + 1] > q_offsets[i];
         const bool few = p.long_end_pair * int64_t(nonempty) <= 4 * int64_t(std::max(1, db->sm_count));
-        p.rows_long = few ? 16 : 32;
+        // few tasks: the shortest column step that keeps one super-pass (8 rows
+        // per lane up to 1,024 query rows, else 16)
+        p.rows_long = few ? (p.max_m <= 4 * 32 * 8 ? 8 : 16) : 32;
         p.warps_long = few ? 4 : 2;
+        p.long_inter = few && p.max_m <= kLongInterRows;
     }
-    p.need_long_boundary = nlb > 0 && p.max_m > intra_rows_per_superpass(p.warps_long, p.rows_long);
+    p.need_long_boundary = nlb > 0 && !p.long_inter && p.max_m > intra_rows_per_superpass(p.warps_long, p.rows_long);
     if (nlb > 0 && p.precision == SW_PREC_I16) {
         const cudaError_t e = prepare_intra_i16x2(p.warps_long, p.rows_long);
         if (e != cudaSuccess) return fail(SW_ERR_CUDA, std::string("intra-task kernel set-up: ") + cudaGetErrorString(e));
@@ -635,7 +648,7 @@ size_t carve(const sw_db *db, const Plan &p, int32_t n_q, int32_t top_k, bool q_
     }
     // [n_q] list lengths, [n_q] work counters, [n_q] flagged, [n_q] chunk counters,
     // status, 4 tile counters
-    x.counters = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(4 * std::max<int32_t>(n_q, 1) + 5)));
+    x.counters = static_cast<int32_t *>(c.take(sizeof(int32_t) * size_t(5 * std::max<int32_t>(n_q, 1) + 5)));
     *b = x;
     return c.used + 256;
 }
@@ -985,7 +998,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
     // All device work of the search, in stream order.  Run directly, or
     // captured once into a CUDA graph and replayed (SW_FLAG_GRAPH).
     auto enqueue = [&]() -> int {
-    SW_CUDA_TRY(cudaMemsetAsync(buf.counters, 0, sizeof(int32_t) * (4 * size_t(std::max<int32_t>(n_q, 1)) + 5), st));
+    SW_CUDA_TRY(cudaMemsetAsync(buf.counters, 0, sizeof(int32_t) * (5 * size_t(std::max<int32_t>(n_q, 1)) + 5), st));
 
     if (plan.alignment != SW_ALIGN_LOCAL) {
         // Non-local modes, per query: the pairs whose scores provably fit int16
@@ -1087,7 +1100,31 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
         la.status = d_status;
         SW_CUDA_TRY(cudaEventRecord(db->ev_fork, st));
         SW_CUDA_TRY(cudaStreamWaitEvent(db->side, db->ev_fork, 0));
-        TIMED_ON(LaunchTimer::INTRA, db->side, launch_intra_i16x2(la, plan.warps_long, plan.rows_long, db->side));
+        if (plan.long_inter) {
+            // one single-strip launch per query, persistent over chunks of 8 long pairs
+            const int slots = inter_slots(kLongInterLanes, kLongInterRows / kLongInterLanes, std::max(1, db->sm_count));
+            for (int32_t qi = 0; qi < n_q; ++qi) {
+                const int32_t m = int32_t(q_offsets[qi + 1] - q_offsets[qi]);
+                if (m == 0) continue;
+                InterArgs lb = ia;
+                lb.query = d_queries + q_offsets[qi];
+                lb.m = m;
+                lb.scores = d_scores + size_t(qi) * size_t(db->n_seqs);
+                lb.ovf_list = buf.ovf_list + size_t(qi) * size_t(list_stride);
+                lb.ovf_count = buf.counters + qi;
+                lb.ovf_seqs = buf.counters + 2 * n_q + qi;
+                lb.pair_begin = 0;
+                lb.pair_end = plan.long_end_pair;
+                lb.boundary = nullptr;
+                lb.max_cols = 0;
+                lb.slot_stride = 0;
+                lb.chunk_counter = buf.counters + 4 * std::max<int32_t>(n_q, 1) + 5 + qi;
+                TIMED_ON(LaunchTimer::INTRA, db->side,
+                         launch_inter_i16x2(lb, kLongInterLanes, kLongInterRows / kLongInterLanes, db->side, slots));
+            }
+        } else {
+            TIMED_ON(LaunchTimer::INTRA, db->side, launch_intra_i16x2(la, plan.warps_long, plan.rows_long, db->side));
+        }
         SW_CUDA_TRY(cudaEventRecord(db->ev_join, db->side));
     }
 

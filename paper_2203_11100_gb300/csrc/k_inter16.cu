@@ -377,7 +377,7 @@ int slots_tr(int sms) {
 
 bool inter_config_supported(int lanes, int rows) {
     switch (lanes * 100 + rows) {
-        case 416: case 816: case 1616: case 3216: case 824: case 832: case 1632: case 3232: return true;
+        case 416: case 816: case 1616: case 3216: case 824: case 832: case 1632: case 3232: case 3208: return true;
         default: return false;
     }
 }
@@ -388,6 +388,7 @@ cudaError_t launch_inter_i16x2(const InterArgs &a, int lanes, int rows, cudaStre
         case 816: return launch_tr<8, 16>(a, s, grid_slots);
         case 824: return launch_tr<8, 24>(a, s, grid_slots);
         case 1616: return launch_tr<16, 16>(a, s, grid_slots);
+        case 3208: return launch_tr<32, 8>(a, s, grid_slots);
         case 3216: return launch_tr<32, 16>(a, s, grid_slots);
         case 832: return launch_tr<8, 32>(a, s, grid_slots);
         case 1632: return launch_tr<16, 32>(a, s, grid_slots);
@@ -402,6 +403,7 @@ int inter_slots(int lanes, int rows, int sms) {
         case 816: return slots_tr<8, 16>(sms);
         case 824: return slots_tr<8, 24>(sms);
         case 1616: return slots_tr<16, 16>(sms);
+        case 3208: return slots_tr<32, 8>(sms);
         case 3216: return slots_tr<32, 16>(sms);
         case 832: return slots_tr<8, 32>(sms);
         case 1632: return slots_tr<16, 32>(sms);

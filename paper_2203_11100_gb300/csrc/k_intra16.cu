@@ -92,15 +92,17 @@ __device__ bool wait_flag(const int *flag, int target, int *abort_flag, int32_t 
 
 template <int R, int NW, int P>
 __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_constant__ IntraArgs a) {
+    static_assert(R % 8 == 0, "rows per lane must be a multiple of 8");
     constexpr int T = 32;
     constexpr int TR = T * R;
     constexpr int SPR = NW * TR;
     constexpr int C = kChunk;
     constexpr int D = kDepth;
     constexpr int NT = NW * P * 32;
-    constexpr int SLICE = kProfRows * TR;                                      // bytes per profile slice
+    constexpr int SLOT = T * 16 * ((R + 15) / 16);                             // bytes per residue (16-row groups)
+    constexpr int SLICE = kProfRows * SLOT;                                    // bytes per profile slice
     extern __shared__ __align__(16) uint8_t smem[];
-    int8_t *prof_all = reinterpret_cast<int8_t *>(smem);                      // [NW][32][TR]
+    int8_t *prof_all = reinterpret_cast<int8_t *>(smem);                      // [NW][32][SLOT]
     uint2 *ring_all = reinterpret_cast<uint2 *>(smem + NW * SLICE);           // [P][NW][D*C], link into warp w
     uint2 *stage_all = ring_all + P * NW * D * C;                             // [P][8] boundary staging
     int8_t *mat = reinterpret_cast<int8_t *>(stage_all + P * 8);              // [32*32]
@@ -166,15 +168,16 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
     for (int sp = 0; sp < nsp; ++sp) {
         __syncthreads();
         // All NW profile slices of this super-pass.  Within a slice the layout is
-        // [residue a][16-row half h][lane k][16 rows]: lane k's rows 16h..16h+15 sit
-        // at a*TR + h*32*16 + k*16 (quarter-warp lanes read consecutive 16-byte slots).
-        for (int wi = threadIdx.x; wi < NW * SLICE / 4; wi += NT) {
-            const int slice = wi / (SLICE / 4);
-            const int e0 = (wi % (SLICE / 4)) * 4;
+        // [residue a][16-row group h][lane k][16 rows]: lane k's rows 16h..16h+15 sit
+        // at a*SLOT + h*32*16 + k*16 (quarter-warp lanes read consecutive 16-byte
+        // slots); with R = 8 a lane's one group fills half its slot.
+        for (int wi = threadIdx.x; wi < NW * kProfRows * TR / 4; wi += NT) {
+            const int slice = wi / (kProfRows * TR / 4);
+            const int e0 = (wi % (kProfRows * TR / 4)) * 4;
             const int res = e0 / TR;
             const int within = e0 % TR;                 // kk * R + r
             const int kk = within / R, rl = within % R;
-            const int phys = slice * SLICE + res * TR + (rl >> 4) * (T * 16) + kk * 16 + (rl & 15);
+            const int phys = slice * SLICE + res * SLOT + (rl >> 4) * (T * 16) + kk * 16 + (rl & 15);
             const int rr = sp * SPR + slice * TR + within;
             uint32_t word = 0;
 #pragma unroll
@@ -267,8 +270,8 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
             }
             if (act) {
                 const int ta = int(cin & 0xffu), tb = int((cin >> 8) & 0xffu);
-                const uint4 *pa = reinterpret_cast<const uint4 *>(prof + ta * TR + k * 16);
-                const uint4 *pb = reinterpret_cast<const uint4 *>(prof + tb * TR + k * 16);
+                const uint4 *pa = reinterpret_cast<const uint4 *>(prof + ta * SLOT + k * 16);
+                const uint4 *pb = reinterpret_cast<const uint4 *>(prof + tb * SLOT + k * 16);
                 uint32_t wa[R / 4], wb[R / 4];
 #pragma unroll
                 for (int v = 0; v < R / 16; ++v) {
@@ -276,6 +279,12 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
                     const uint4 y = pb[v * T];
                     wa[4 * v + 0] = x.x; wa[4 * v + 1] = x.y; wa[4 * v + 2] = x.z; wa[4 * v + 3] = x.w;
                     wb[4 * v + 0] = y.x; wb[4 * v + 1] = y.y; wb[4 * v + 2] = y.z; wb[4 * v + 3] = y.w;
+                }
+                if (R % 16) {                     // last group of 8 rows: an 8-byte load
+                    const uint2 x = *reinterpret_cast<const uint2 *>(pa + (R / 16) * T);
+                    const uint2 y = *reinterpret_cast<const uint2 *>(pb + (R / 16) * T);
+                    wa[R / 4 - 2] = x.x; wa[R / 4 - 1] = x.y;
+                    wb[R / 4 - 2] = y.x; wb[R / 4 - 1] = y.y;
                 }
                 uint32_t f = fin;
                 uint32_t d = hd;
@@ -377,7 +386,7 @@ __global__ void k_wait_probe(long long limit, int32_t *status) {
 
 template <int R, int NW, int P>
 size_t intra_smem() {
-    return size_t(NW) * kProfRows * 32 * R + size_t(P) * NW * kDepth * kChunk * sizeof(uint2) +
+    return size_t(NW) * kProfRows * 32 * 16 * ((R + 15) / 16) + size_t(P) * NW * kDepth * kChunk * sizeof(uint2) +
            size_t(P) * 8 * sizeof(uint2) + kProfRows * kProfRows + sizeof(int) * (2 * P * NW + 1);
 }
 
@@ -402,9 +411,11 @@ cudaError_t prepare_rnp() {
 }  // namespace
 
 // Shapes: warps per pipeline (NW) and rows per lane (R); pipelines per CTA (P)
-// follow: (4 warps, 16 rows) x 3 pipelines, (2 warps, 32 rows) x 4 pipelines.
+// follow: (4 warps, 8 rows) x 3 pipelines (1,024-row super-passes, the
+// shortest column step), (4 warps, 16 rows) x 3 pipelines, (2 warps, 32 rows)
+// x 4 pipelines (2,048-row super-passes).
 bool intra_config_supported(int warps, int rows) {
-    return (warps == 4 && rows == 16) || (warps == 2 && rows == 32);
+    return (warps == 4 && rows == 8) || (warps == 4 && rows == 16) || (warps == 2 && rows == 32);
 }
 
 int intra_rows_per_superpass(int warps, int rows) { return warps * 32 * rows; }
@@ -416,12 +427,14 @@ cudaError_t launch_wait_probe(long long limit, int32_t *status, cudaStream_t s) 
 }
 
 cudaError_t prepare_intra_i16x2(int warps, int rows) {
+    if (rows == 8 && warps == 4) return prepare_rnp<8, 4, 3>();
     if (rows == 16 && warps == 4) return prepare_rnp<16, 4, 3>();
     if (rows == 32 && warps == 2) return prepare_rnp<32, 2, 4>();
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_intra_i16x2(const IntraArgs &a, int warps, int rows, cudaStream_t s) {
+    if (rows == 8 && warps == 4) return launch_rnp<8, 4, 3>(a, s);
     if (rows == 16 && warps == 4) return launch_rnp<16, 4, 3>(a, s);
     if (rows == 32 && warps == 2) return launch_rnp<32, 2, 4>(a, s);
     return cudaErrorInvalidValue;

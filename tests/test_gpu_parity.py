@@ -13,7 +13,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-I16_SHAPES = [(4, 16), (8, 16), (16, 16), (32, 16), (8, 24), (8, 32), (16, 32), (32, 32)]
+I16_SHAPES = [(4, 16), (8, 16), (16, 16), (32, 8), (32, 16), (8, 24), (8, 32), (16, 32), (32, 32)]
 I32_SHAPES = [(8, 16), (16, 16), (32, 16), (32, 32)]
 
 
@@ -151,10 +151,28 @@ def test_long_sequence_split(gpu, cutoff):
         assert st["long_sequences"] == 0
 
 
-@pytest.mark.parametrize("long_rows", [16, 32])
+@pytest.mark.parametrize("qlens", [[1, 100, 256], [256, 0, 37], [257, 40]])
+def test_long_pairs_of_short_queries(gpu, qlens):
+    """Few (long pair, query) tasks with every query within 256 rows: the long pairs run
+    in the inter-task kernel at 32 lanes x 8 rows on the side stream (a 257-row query
+    falls back to the intra-task kernel).  Within 256 rows an int8 profile cannot
+    saturate int16 (at most 117 x 256), so the second matrix only widens the scores."""
+    rng = np.random.default_rng(24)
+    lens = np.concatenate([rng.integers(1, 300, 150), rng.integers(600, 5000, 12), [9000]])
+    rng.shuffle(lens)
+    db = synth.seqset_from_lengths(rng, lens)
+    qs = synth.seqset_from_lengths(rng, qlens)
+    st = _check(gpu, qs, db, synth.blosum62(), 10, 1, long_cutoff=500, precision=gpu.SW_PREC_I16,
+                mode=gpu.SW_MODE_PLAIN)
+    assert st["long_sequences"] >= (lens > 500).sum()
+    S = synth.random_matrix(rng, 24, -20, 110, symmetric=True)
+    _check(gpu, qs, db, S, 10, 1, long_cutoff=500, precision=gpu.SW_PREC_I16, mode=gpu.SW_MODE_PLAIN)
+
+
+@pytest.mark.parametrize("long_rows", [8, 16, 32])
 def test_intra_task_multi_superpass(gpu, long_rows):
-    """Queries longer than one super-pass of the intra-task kernel (2048
-    rows in both shapes), against long sequences of ragged lengths."""
+    """Queries longer than one super-pass of the intra-task kernel (1,024 rows at 8
+    rows per lane, 2,048 at 16 and 32), against long sequences of ragged lengths."""
     rng = np.random.default_rng(23)
     lens = np.concatenate([rng.integers(65, 900, 40), rng.integers(1, 64, 30), [1, 2, 3, 4, 5]])
     db = synth.seqset_from_lengths(rng, lens)
