@@ -21,23 +21,16 @@
 // because the int32 rescore uses the pair's boundary region for both.
 #include <type_traits>
 
+#include "simd16.cuh"
 #include "swdb_internal.cuh"
 
 namespace swdb {
 namespace {
 
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem_dst)),
-                 "l"(gmem_src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
-__device__ __forceinline__ uint32_t pack2(int v) {
-    uint32_t h = uint32_t(v) & 0xffffu;
-    return h | (h << 16);
-}
+using simd16::cp_async16;
+using simd16::cp_async_commit;
+using simd16::cp_async_wait1;
+using simd16::pack2;
 
 template <int T, int R>
 __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_batch_i16x2(const __grid_constant__ BatchArgs a) {

@@ -31,6 +31,7 @@
 // permute and half a running max; see k_inter16.cu for the derivation).
 #include <type_traits>
 
+#include "simd16.cuh"
 #include "swdb_internal.cuh"
 
 namespace swdb {
@@ -40,28 +41,12 @@ constexpr int kChunk = 64;      // columns per ring chunk
 constexpr int kDepth = 4;       // chunks per ring
 constexpr long long kSpinLimit = 1ll << 25;   // x ~32 ns sleep: about a second
 
-__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
-    uint32_t d;
-    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
-    return d;
-}
-
-__host__ __device__ constexpr uint32_t pair_sel(int c) {
-    return uint32_t(c) | (uint32_t(c | 8) << 4) | (uint32_t(4 + c) << 8) | (uint32_t((4 + c) | 8) << 12);
-}
-
-__device__ __forceinline__ uint32_t pack2(int v) {
-    uint32_t h = uint32_t(v) & 0xffffu;
-    return h | (h << 16);
-}
-
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem_dst)),
-                 "l"(gmem_src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+using simd16::cp_async16;
+using simd16::cp_async_commit;
+using simd16::cp_async_wait1;
+using simd16::pack2;
+using simd16::pair_sel;
+using simd16::prmt;
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
     int v;
