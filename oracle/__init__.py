@@ -18,10 +18,13 @@ of the ``synth`` module.
 - ``align`` / ``align_pairs``: one optimal local alignment per pair, read
   off the same matrices by the traceback rules stated in ``traceback.c``
   (end cell first in row-major order; diagonal before E before F; a gap
-  opens as soon as it can), plain C, int64.
+  opens as soon as it can), plain C, int64.  With ``mode`` = "global",
+  "semiglobal" or "overlap": the same rules on the matrices of ``modes.c``
+  with the mode's end cell and boundary (``align_modes.c``).
 
-Parity of every function here is pinned by tests/test_oracle_pins.py and
-tests/test_oracle_align_pins.py (brute-force enumeration, textbook
+Parity of every function here is pinned by tests/test_oracle_pins.py,
+tests/test_oracle_mode_pins.py, tests/test_oracle_align_pins.py and
+tests/test_oracle_align_mode_pins.py (brute-force enumeration, textbook
 reductions, hand-worked examples, invariants, rescoring of the returned
 alignments).
 """
@@ -35,7 +38,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "gotoh.c"), os.path.join(_HERE, "traceback.c"), os.path.join(_HERE, "modes.c")]
+_SRCS = [os.path.join(_HERE, "gotoh.c"), os.path.join(_HERE, "traceback.c"), os.path.join(_HERE, "modes.c"),
+         os.path.join(_HERE, "align_modes.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libgotoh.so")
 _lock = threading.Lock()
@@ -73,6 +77,8 @@ def _load():
                                                  ctypes.c_int, p]
             lib.swo_align.restype = i64
             lib.swo_align.argtypes = [p, i64, p, i64, p, ctypes.c_int32, i64, i64, p, p, p]
+            lib.swo_align_mode.restype = ctypes.c_int
+            lib.swo_align_mode.argtypes = [p, i64, p, i64, p, ctypes.c_int32, i64, i64, ctypes.c_int32, p, p, p, p]
             _lib = lib
     return _lib
 
@@ -190,8 +196,9 @@ def top_k(scores_row, k: int):
     return s, i
 
 
-def align(q, t, S, gap_open: int, gap_extend: int) -> dict:
-    """One optimal local alignment of query q against target t (uint8 codes).
+def align(q, t, S, gap_open: int, gap_extend: int, mode="local") -> dict:
+    """One optimal alignment of query q against target t (uint8 codes), local
+    unless mode says otherwise.
 
     Returns {"score", "q_begin", "q_end", "t_begin", "t_end", "ops"}: the
     alignment covers q[q_begin:q_end] and t[t_begin:t_end]; ops (uint8) run
@@ -205,21 +212,30 @@ def align(q, t, S, gap_open: int, gap_extend: int) -> dict:
     A = S.shape[0]
     if len(q) and int(q.max()) >= A or len(t) and int(t.max()) >= A:
         raise ValueError("residue code outside the matrix")
+    md = _mode(mode)
     coords = np.zeros(4, dtype=np.int64)
     ops = np.zeros(max(len(q) + len(t), 1), dtype=np.uint8)
     n_ops = np.zeros(1, dtype=np.int64)
     qq = q if len(q) else np.zeros(1, np.uint8)
     tt = t if len(t) else np.zeros(1, np.uint8)
-    r = lib.swo_align(_ptr(qq), len(q), _ptr(tt), len(t), _ptr(S), A, int(gap_open), int(gap_extend),
-                      _ptr(coords), _ptr(ops), _ptr(n_ops))
-    if r < 0:
-        raise MemoryError("oracle scratch allocation failed")
+    if md == 0:
+        r = lib.swo_align(_ptr(qq), len(q), _ptr(tt), len(t), _ptr(S), A, int(gap_open), int(gap_extend),
+                          _ptr(coords), _ptr(ops), _ptr(n_ops))
+        if r < 0:
+            raise MemoryError("oracle scratch allocation failed")
+    else:
+        sc = np.zeros(1, dtype=np.int64)
+        rc = lib.swo_align_mode(_ptr(qq), len(q), _ptr(tt), len(t), _ptr(S), A, int(gap_open), int(gap_extend),
+                                md, _ptr(sc), _ptr(coords), _ptr(ops), _ptr(n_ops))
+        if rc != 0:
+            raise MemoryError("oracle scratch allocation failed")
+        r = sc[0]
     return {"score": int(r), "q_begin": int(coords[0]), "q_end": int(coords[1]),
             "t_begin": int(coords[2]), "t_end": int(coords[3]), "ops": ops[:int(n_ops[0])].copy()}
 
 
 def align_pairs(queries, db, q_idx, t_idx, S, gap_open: int, gap_extend: int,
-                threads: int | None = None) -> list:
+                threads: int | None = None, mode="local") -> list:
     """``align`` of the pairs (queries.seq(q_idx[k]), db.seq(t_idx[k])), spread
     over threads (the C call releases the interpreter lock)."""
     from concurrent.futures import ThreadPoolExecutor
@@ -227,7 +243,7 @@ def align_pairs(queries, db, q_idx, t_idx, S, gap_open: int, gap_extend: int,
     t_idx = [int(x) for x in t_idx]
 
     def one(k):
-        return align(queries.seq(q_idx[k]), db.seq(t_idx[k]), S, gap_open, gap_extend)
+        return align(queries.seq(q_idx[k]), db.seq(t_idx[k]), S, gap_open, gap_extend, mode=mode)
 
     with ThreadPoolExecutor(max_workers=threads or default_threads()) as ex:
         return list(ex.map(one, range(len(q_idx))))

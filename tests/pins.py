@@ -157,6 +157,61 @@ def alignment_end(i0, j0, cols):
     return i, j
 
 
+def enumerate_mode_alignments(q, t, S, gap_open: int, gap_extend: int, mode: str):
+    """Every alignment a non-local mode allows, as explicit column lists.
+
+    Yields (i0, j0, cols, score) as enumerate_alignments does (gap columns
+    priced open, or extend right after a gap column of the same kind, both
+    pricings listed), restricted to the mode's start and end:
+    global starts at (0, 0) and ends at (m, n); semi-global starts at (0, j0)
+    and ends at (m, j1); overlap starts with i0 = 0 or j0 = 0 and ends with
+    i1 = m or j1 = n.  Empty alignments are included where start = end is
+    allowed.
+    """
+    q = [int(x) for x in q]
+    t = [int(x) for x in t]
+    m, n = len(q), len(t)
+    out = []
+
+    def ends_ok(i, j):
+        if mode == "global":
+            return i == m and j == n
+        if mode == "semiglobal":
+            return i == m
+        return i == m or j == n
+
+    def dfs(i0, j0, i, j, cols, score):
+        if ends_ok(i, j):
+            out.append((i0, j0, tuple(cols), score))
+        last = cols[-1][0] if cols else None
+        if i < m and j < n:
+            cols.append(("M", False))
+            dfs(i0, j0, i + 1, j + 1, cols, score + int(S[q[i]][t[j]]))
+            cols.pop()
+        for op, di, dj in (("I", 1, 0), ("D", 0, 1)):
+            if i + di > m or j + dj > n:
+                continue
+            cols.append((op, True))
+            dfs(i0, j0, i + di, j + dj, cols, score - gap_open)
+            cols.pop()
+            if last == op:
+                cols.append((op, False))
+                dfs(i0, j0, i + di, j + dj, cols, score - gap_extend)
+                cols.pop()
+
+    if mode == "global":
+        starts = [(0, 0)]
+    elif mode == "semiglobal":
+        starts = [(0, j0) for j0 in range(n + 1)]
+    elif mode == "overlap":
+        starts = [(i0, 0) for i0 in range(m + 1)] + [(0, j0) for j0 in range(1, n + 1)]
+    else:
+        raise ValueError(mode)
+    for i0, j0 in starts:
+        dfs(i0, j0, i0, j0, [], 0)
+    return out
+
+
 def brute_force_global(q, t, S, gap_open: int, gap_extend: int) -> int:
     """Maximum over every end-to-end alignment of q against t, enumerated one
     by one (columns M, I, D; a run of k gap columns of one kind costs open +
