@@ -568,7 +568,8 @@ def run_sweep(args, dist: Dist):
 
 def run_align(args, dist: Dist):
     """Traceback of the top-k hits: search the workload once, then align every
-    (query, hit) pair with sw_align; W warm-up and K timed calls."""
+    (query, hit) pair with sw_align (sw_align_mode for --alignment other than
+    local, the hits of that mode's search); W warm-up and K timed calls."""
     import torch
     import paper_2203_11100_gb300 as swdb
 
@@ -577,14 +578,15 @@ def run_align(args, dist: Dist):
     swdb.load_library()
     w = synth.make_workload(args.workload, seed=synth.SEED, db_scale=args.db_scale)
     db = swdb.Database(w.db.residues, w.db.offsets, len(synth.ALPHABET), device=dev)
+    mode = ALIGNMENTS[args.alignment]
     _, hits, _ = db.search(w.queries.residues, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend,
-                           top_k=w.top_k, want_scores=False)
+                           top_k=w.top_k, want_scores=False, alignment=mode)
     pq = np.repeat(np.arange(w.queries.n, dtype=np.int32), w.top_k)
     pt = hits["db_index"].reshape(-1).astype(np.int64)
     keep = pt >= 0
     pq, pt = pq[keep], pt[keep]
     for _ in range(args.warmup):
-        db.align(w.queries.residues, w.queries.offsets, pq, pt, w.matrix, w.gap_open, w.gap_extend)
+        db.align(w.queries.residues, w.queries.offsets, pq, pt, w.matrix, w.gap_open, w.gap_extend, alignment=mode)
     clocks = ClockSampler(dev)
     clocks.start()
     fwd_ms = tb_ms = 0.0
@@ -592,7 +594,7 @@ def run_align(args, dist: Dist):
     for _ in range(args.steps):
         t0 = time.perf_counter()
         aln, ops, st = db.align(w.queries.residues, w.queries.offsets, pq, pt, w.matrix, w.gap_open,
-                                w.gap_extend, stats=True)
+                                w.gap_extend, stats=True, alignment=mode)
         wall.append(time.perf_counter() - t0)
         fwd_ms += st["forward_ms"]
         tb_ms += st["traceback_ms"]
@@ -616,7 +618,8 @@ def run_align(args, dist: Dist):
             pick.append(int(k))
             cells += c
         t0 = time.perf_counter()
-        want = oracle.align_pairs(w.queries, w.db, pq[pick], pt[pick], w.matrix, w.gap_open, w.gap_extend)
+        want = oracle.align_pairs(w.queries, w.db, pq[pick], pt[pick], w.matrix, w.gap_open, w.gap_extend,
+                                  mode=args.alignment)
         dt = time.perf_counter() - t0
         exact = True
         for k, wa in zip(pick, want):
@@ -635,7 +638,7 @@ def run_align(args, dist: Dist):
             "value": n * args.steps / dev_s, "unit": "alignments/s", "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": (fwd_ms + tb_ms) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
-            "config": {"workload": f"{args.workload} top-{w.top_k} hits", "pairs": n,
+            "config": {"workload": f"{args.workload} top-{w.top_k} hits", "alignment": args.alignment, "pairs": n,
                        "query_lengths": [int(lens_q.min()), int(lens_q.max())],
                        "target_lengths": [int(lens_t.min()), int(lens_t.max())],
                        "forward_cells_per_step": fwd_cells, "traceback_cells_per_step": tb_cells,

@@ -337,6 +337,35 @@ int sw_align(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_
              sw_align_stats *stats, void *stream);
 
 /*
+ * sw_align in any sw_alignment_mode (SW_ALIGN_LOCAL gives sw_align).  The
+ * non-local modes (global, semi-global, overlap, as defined for sw_search's
+ * alignment option; SW# offers them besides local alignment, Section 2.3)
+ * read one optimal alignment off their own matrices with the same tie rules,
+ * except that:
+ *   - the end cell is global (m, n); semi-global the first cell (m, j) of the
+ *     last row in row-major order whose H is the row's maximum; overlap the
+ *     first cell in row-major order, among the last column (i, n), i = 0..m,
+ *     and the last row (m, j), whose H is their maximum;
+ *   - the walk does not stop at H = 0; on reaching the first row or column it
+ *     emits the leading gap the mode prices there (global: the first row's
+ *     D ops or the first column's I ops; semi-global: the first column's I
+ *     ops) and stops.
+ * So global covers both sequences (score H(m, n), possibly negative),
+ * semi-global the whole query, and overlap starts on the first row or column
+ * and ends on the last row or column; an empty alignment may sit at a
+ * non-zero target position (overlap: q_begin = q_end = 0, t_begin = t_end = n
+ * when H(0, n) = 0 is the first maximum).  Arguments, ops capacity and
+ * scratch as for sw_align.  Errors: as sw_align, plus SW_ERR_INVALID_ARG for
+ * an unknown mode and SW_ERR_OVERFLOW when (m + n) * (max|S| + o + e) >= 2^28
+ * for some pair.
+ */
+int sw_align_mode(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_t n_q,
+                  const int32_t *pair_query, const int64_t *pair_target, int64_t n_pairs,
+                  const int32_t *matrix, int32_t gap_open, int32_t gap_extend, int32_t alignment,
+                  sw_alignment *alignments_out, uint8_t *ops_out, int64_t ops_capacity,
+                  sw_align_stats *stats, void *stream);
+
+/*
  * Score one query against a loaded database without allocating any device
  * memory during the call.  (The paper has no counterpart: this entry point
  * exists for callers of this library that cannot allocate at search time.)

@@ -95,6 +95,9 @@ def load_library():
     lib.sw_align_ops_capacity.argtypes = [vp, vp, i32, vp, vp, i64, ctypes.POINTER(i64)]
     lib.sw_align.argtypes = [vp, vp, vp, i32, vp, vp, i64, vp, i32, i32, vp, vp, i64,
                              ctypes.POINTER(SwAlignStats), vp]
+    lib.sw_align_mode.argtypes = [vp, vp, vp, i32, vp, vp, i64, vp, i32, i32, i32, vp, vp, i64,
+                                  ctypes.POINTER(SwAlignStats), vp]
+    lib.sw_align_mode.restype = ctypes.c_int
     for name in ("sw_db_load", "sw_db_free", "sw_db_get_info", "sw_search_workspace_size", "sw_search",
                  "sw_top_k", "sw_probe_alu_rate", "sw_search_no_alloc"):
         getattr(lib, name).restype = ctypes.c_int
@@ -297,9 +300,10 @@ def sw_align_ops_capacity(handle, q_offsets, pair_query, pair_target) -> int:
 
 
 def sw_align(handle, queries, q_offsets, pair_query, pair_target, matrix, gap_open: int, gap_extend: int,
-             stats: bool = False, stream=None):
+             stats: bool = False, stream=None, alignment=SW_ALIGN_LOCAL):
     """Alignments of the pairs (query pair_query[k], database sequence
-    pair_target[k]).  Returns (alignments ALIGNMENT_DTYPE [n_pairs], ops uint8,
+    pair_target[k]), local unless alignment names another mode (then
+    sw_align_mode).  Returns (alignments ALIGNMENT_DTYPE [n_pairs], ops uint8,
     stats dict or None); pair k's ops are ops[ops_offset : ops_offset + ops_len]."""
     q_offsets = np.ascontiguousarray(q_offsets, dtype=np.int64)
     pq, pt = _pairs(pair_query, pair_target)
@@ -309,11 +313,11 @@ def sw_align(handle, queries, q_offsets, pair_query, pair_target, matrix, gap_op
     aln = np.zeros(len(pq), dtype=ALIGNMENT_DTYPE)
     ops = np.zeros(max(cap, 1), dtype=np.uint8)
     st = SwAlignStats()
-    _check(load_library().sw_align(handle, qp, q_offsets.ctypes.data, len(q_offsets) - 1,
-                                   pq.ctypes.data if len(pq) else None, pt.ctypes.data if len(pt) else None,
-                                   len(pq), matrix.ctypes.data, int(gap_open), int(gap_extend),
-                                   aln.ctypes.data if len(pq) else None, ops.ctypes.data, cap,
-                                   ctypes.byref(st) if stats else None, stream))
+    _check(load_library().sw_align_mode(handle, qp, q_offsets.ctypes.data, len(q_offsets) - 1,
+                                        pq.ctypes.data if len(pq) else None, pt.ctypes.data if len(pt) else None,
+                                        len(pq), matrix.ctypes.data, int(gap_open), int(gap_extend), int(alignment),
+                                        aln.ctypes.data if len(pq) else None, ops.ctypes.data, cap,
+                                        ctypes.byref(st) if stats else None, stream))
     sd = {f: getattr(st, f) for f, _ in SwAlignStats._fields_} if stats else None
     return aln, ops[:cap], sd
 
@@ -346,10 +350,10 @@ class Database:
         return scores, hits, stats
 
     def align(self, queries, q_offsets, pair_query, pair_target, matrix, gap_open: int, gap_extend: int,
-              stats: bool = False):
-        """Alignments of chosen (query, database sequence) pairs: see sw_align."""
+              stats: bool = False, alignment=SW_ALIGN_LOCAL):
+        """Alignments of chosen (query, database sequence) pairs: see sw_align and sw_align_mode."""
         return sw_align(self.handle, queries, q_offsets, pair_query, pair_target, matrix, gap_open, gap_extend,
-                        stats=stats)
+                        stats=stats, alignment=alignment)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -1474,11 +1474,13 @@ int sw_align_ops_capacity(const sw_db *db, const int64_t *q_offsets, int32_t n_q
     return SW_OK;
 }
 
-int sw_align(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_t n_q, const int32_t *pair_query,
-             const int64_t *pair_target, int64_t n_pairs, const int32_t *matrix, int32_t gap_open,
-             int32_t gap_extend, sw_alignment *alignments_out, uint8_t *ops_out, int64_t ops_capacity,
-             sw_align_stats *stats, void *stream) {
+int sw_align_mode(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_t n_q,
+                  const int32_t *pair_query, const int64_t *pair_target, int64_t n_pairs, const int32_t *matrix,
+                  int32_t gap_open, int32_t gap_extend, int32_t alignment, sw_alignment *alignments_out,
+                  uint8_t *ops_out, int64_t ops_capacity, sw_align_stats *stats, void *stream) {
     g_last_error.clear();
+    if (alignment < SW_ALIGN_LOCAL || alignment > SW_ALIGN_OVERLAP)
+        return fail(SW_ERR_INVALID_ARG, "unknown alignment mode");
     int rc = check_align_pairs(db, q_offsets, n_q, pair_query, pair_target, n_pairs);
     if (rc) return rc;
     if (!matrix) return fail(SW_ERR_INVALID_ARG, "matrix is NULL");
@@ -1486,11 +1488,12 @@ int sw_align(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_
     if (stats) memset(stats, 0, sizeof *stats);
     if (n_pairs == 0) return SW_OK;
     if (!alignments_out) return fail(SW_ERR_INVALID_ARG, "alignments_out is NULL");
-    int64_t ops_need = 0, max_min_len = 0;
+    int64_t ops_need = 0, max_min_len = 0, max_sum_len = 0;
     for (int64_t k = 0; k < n_pairs; ++k) {
         const int64_t m = pair_len_q(q_offsets, pair_query[k]), n = pair_len_t(db, pair_target[k]);
         ops_need += m + n;
         max_min_len = std::max(max_min_len, std::min(m, n));
+        max_sum_len = std::max(max_sum_len, m + n);
     }
     if (ops_need > 0 && (!ops_out || ops_capacity < ops_need))
         return fail(SW_ERR_INVALID_ARG, "ops_capacity too small (see sw_align_ops_capacity)");
@@ -1505,6 +1508,10 @@ int sw_align(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_
     if (absmax > (1 << 20) || int64_t(gap_open) + gap_extend > (int64_t(1) << 28) ||
         max_min_len * std::max(smax, 0) + gap_open + gap_extend + absmax > (int64_t(1) << 28))
         return fail(SW_ERR_OVERFLOW, "matrix entries, penalties or lengths too large for exact int32 scores");
+    // no zero floor: values go down to about -(m + n) * (max|S| + o + e), as in sw_search
+    if (alignment != SW_ALIGN_LOCAL && max_sum_len * (absmax + int64_t(gap_open) + gap_extend) >= (int64_t(1) << 28))
+        return fail(SW_ERR_OVERFLOW, "lengths, matrix entries or penalties too large for exact int32 scores "
+                                     "of this alignment mode");
 
     std::lock_guard<std::mutex> lock(db->mu);
     DeviceGuard guard(db->device);
@@ -1631,6 +1638,7 @@ int sw_align(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_
         a.ops = d_scratch + ck + fl + rv;
         a.gap_open = gap_open;
         a.gap_extend = gap_extend;
+        a.mode = alignment;
         SW_CUDA_TRY(cudaMemcpyAsync(d_pairs, hp.data(), sizeof(AlignPairDev) * size_t(np), cudaMemcpyHostToDevice, st));
         if (stats) SW_CUDA_TRY(cudaEventRecord(ev[0], st));
         SW_CUDA_TRY(launch_align(a, 0, st));
@@ -1670,6 +1678,14 @@ int sw_align(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_
         ops_base += op;
     }
     return SW_OK;
+}
+
+int sw_align(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_t n_q, const int32_t *pair_query,
+             const int64_t *pair_target, int64_t n_pairs, const int32_t *matrix, int32_t gap_open,
+             int32_t gap_extend, sw_alignment *alignments_out, uint8_t *ops_out, int64_t ops_capacity,
+             sw_align_stats *stats, void *stream) {
+    return sw_align_mode(db, queries, q_offsets, n_q, pair_query, pair_target, n_pairs, matrix, gap_open, gap_extend,
+                         SW_ALIGN_LOCAL, alignments_out, ops_out, ops_capacity, stats, stream);
 }
 
 }  // extern "C"

@@ -26,6 +26,15 @@
 // Every strip is recomputed at most once, so the traceback costs at most
 // one more forward pass, and memory is ceil(m/256) checkpoint rows plus one
 // strip of flags instead of m x n.
+//
+// The non-local modes (global, semi-global, overlap; SW# offers them besides
+// local alignment, Section 2.3) run the same passes on their own matrices:
+// the mode's first row and column (g(k) = o + (k-1) min(o, e) for a leading
+// gap), no zero floor, and the end cell the first of the mode's candidates in
+// row-major order (global (m, n); semi-global the last row; overlap the last
+// column, then the last row) whose H is their maximum.  The walk has no stop
+// at H = 0; on reaching the first row or column it emits the leading gap the
+// mode prices there (global: both; semi-global: the first column) and stops.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -80,6 +89,26 @@ __device__ __forceinline__ void load_profile(int32_t (*prof)[kStrip], const int3
 
 __device__ __forceinline__ int32_t max3(int32_t a, int32_t b, int32_t c) { return __vimax3_s32(a, b, c); }
 
+// Leading gap of k residues on the first row or column of a non-local mode.
+__device__ __forceinline__ int32_t lead_gap(int k, int32_t o, int32_t e) {
+    return k <= 0 ? 0 : o + (k - 1) * min(o, e);
+}
+
+// H(i, 0) and H(0, j) of the mode (local: 0).
+__device__ __forceinline__ int32_t first_col(int mode, int i, int32_t o, int32_t e) {
+    return (mode == SW_ALIGN_GLOBAL || mode == SW_ALIGN_SEMIGLOBAL) ? -lead_gap(i, o, e) : 0;
+}
+__device__ __forceinline__ int32_t first_row(int mode, int j, int32_t o, int32_t e) {
+    return mode == SW_ALIGN_GLOBAL ? -lead_gap(j, o, e) : 0;
+}
+
+// Candidate end cell (1-based i <= m, j <= n) of a non-local mode.
+__device__ __forceinline__ bool end_candidate(int mode, int i, int j, int m, int n) {
+    if (mode == SW_ALIGN_GLOBAL) return i == m && j == n;
+    if (mode == SW_ALIGN_SEMIGLOBAL) return i == m;
+    return i == m || j == n;
+}
+
 __device__ __forceinline__ int ld_acquire_cta(const int *p) {
     int v;
     asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
@@ -109,8 +138,20 @@ __global__ void __launch_bounds__(kFW * 32) k_align_fwd(const AlignArgs a) {
     const AlignPairDev P = a.pairs[blockIdx.x];
     AlignResultDev *R = a.results + blockIdx.x;
     const int m = P.m, n = P.n;
+    const int mode = a.mode;
+    const bool local = mode == SW_ALIGN_LOCAL;
     if (m <= 0 || n <= 0) {
-        if (threadIdx.x == 0) *R = AlignResultDev{};
+        if (threadIdx.x == 0) {
+            // only the first row or column: global ends at (m, n), semi-global
+            // at (m, 0) (its first candidate when m = 0), overlap at (0, 0)
+            AlignResultDev res{};
+            if (mode == SW_ALIGN_GLOBAL || (mode == SW_ALIGN_SEMIGLOBAL && n == 0)) {
+                res.i_end = max(m, 0);
+                res.j_end = mode == SW_ALIGN_GLOBAL ? max(n, 0) : 0;
+                res.score = -lead_gap(max(m, 0) + max(n, 0), a.gap_open, a.gap_extend);
+            }
+            *R = res;
+        }
         return;
     }
     if (threadIdx.x < kFW) pub[threadIdx.x] = -1;
@@ -122,23 +163,33 @@ __global__ void __launch_bounds__(kFW * 32) k_align_fwd(const AlignArgs a) {
     const int nstrips = (m + kStrip - 1) / kStrip;
     const int prevw = (warp + kFW - 1) % kFW;         // writes the strip above ours
 
-    int32_t best = 0;
-    int64_t bkey = INT64_MAX;              // (i << 32) | j of the first maximum in row-major order
+    // best value and (i << 32) | j of its first cell in row-major order; the
+    // non-local modes start from their boundary candidates: H(m, 0) for
+    // semi-global, H(0, n) = 0 for overlap
+    int32_t best = local ? 0 : INT32_MIN;
+    int64_t bkey = INT64_MAX;
+    if (mode == SW_ALIGN_SEMIGLOBAL) {
+        best = first_col(mode, m, o, e);
+        bkey = int64_t(m) << 32;
+    } else if (mode == SW_ALIGN_OVERLAP) {
+        best = 0;
+        bkey = int64_t(n);
+    }
     int status = 0;
     for (int strip = warp; strip < nstrips && status == 0; strip += kFW) {
         const int r0 = strip * kStrip;
+        const int row0 = r0 + lane * kAR + 1;          // 1-based first row of this lane
         int32_t H[kAR], E[kAR];
 #pragma unroll
-        for (int r = 0; r < kAR; ++r) { H[r] = 0; E[r] = kNegInf; }
-        int32_t hd = 0, pub_h = 0, pub_f = kNegInf;
+        for (int r = 0; r < kAR; ++r) { H[r] = first_col(mode, row0 + r, o, e); E[r] = kNegInf; }
+        int32_t hd = first_col(mode, row0 - 1, o, e), pub_h = 0, pub_f = kNegInf;
         const int2 *ck_in = strip > 0 ? a.ckpt + P.ckpt_off + int64_t(strip - 1) * (n + 1) : nullptr;
         int2 *ck_out = a.ckpt + P.ckpt_off + int64_t(strip) * (n + 1);
         const bool write_ck = r0 + kStrip < m;
-        const int row0 = r0 + lane * kAR + 1;          // 1-based first row of this lane
         const int32_t *prow = prof + r0 + lane * kAR;
         const int need_base = (strip - 1) * (n + 1);
         int avail = 0;                                 // columns of ck_in known to be written
-        if (write_ck && lane == 31) ck_out[0] = make_int2(0, kNegInf);
+        if (write_ck && lane == 31) ck_out[0] = make_int2(first_col(mode, r0 + kStrip, o, e), kNegInf);
         for (int s = 0; s < n + 31; ++s) {
             if (strip > 0 && s + 1 <= n && s + 1 > avail) {   // warp-uniform
                 const int want = min(s + kPub, n);
@@ -160,7 +211,7 @@ __global__ void __launch_bounds__(kFW * 32) k_align_fwd(const AlignArgs a) {
             const int j = s - lane + 1;                 // 1-based column
             if (j >= 1 && j <= n) {
                 if (lane == 0) {
-                    if (strip == 0) { hin = 0; fin = kNegInf; }
+                    if (strip == 0) { hin = first_row(mode, j, o, e); fin = kNegInf; }
                     else { const int2 v = ck_in[j]; hin = v.x; fin = v.y; }
                 }
                 const int c = target_code(tb, j - 1);
@@ -172,13 +223,13 @@ __global__ void __launch_bounds__(kFW * 32) k_align_fwd(const AlignArgs a) {
                 for (int r = 0; r < kAR; ++r) {
                     const int32_t e_r = __viaddmax_s32(E[r], -e, H[r] - o);     // E(i,j)
                     f = __viaddmax_s32(f, -e, up - o);                           // F(i,j)
-                    const int32_t h = max3(d + sc[r], e_r, max(f, 0));           // H(i,j)
+                    const int32_t h = max3(d + sc[r], e_r, local ? max(f, 0) : f);   // H(i,j)
                     d = H[r];
                     E[r] = e_r;
                     H[r] = h;
                     up = h;
                     const int i = row0 + r;
-                    if (h >= best && h > 0 && i <= m) {
+                    if (h >= best && i <= m && (local ? h > 0 : end_candidate(mode, i, j, m, n))) {
                         const int64_t key = (int64_t(i) << 32) | uint32_t(j);
                         if (h > best || key < bkey) { best = h; bkey = key; }
                     }
@@ -213,7 +264,7 @@ __global__ void __launch_bounds__(kFW * 32) k_align_fwd(const AlignArgs a) {
         }
         AlignResultDev res{};
         res.score = best;
-        if (best > 0) {
+        if (best > 0 || !local) {
             res.i_end = int32_t(bkey >> 32);
             res.j_end = int32_t(bkey & 0xffffffff);
         }
@@ -230,7 +281,9 @@ __global__ void __launch_bounds__(32) k_align_bwd(const AlignArgs a) {
     AlignResultDev *R = a.results + blockIdx.x;
     for (int i = lane; i < kProfRows * kProfRows; i += 32) mat[i] = a.mat[i];
     const int m = P.m, n = P.n;
-    if (R->score <= 0 || m <= 0 || n <= 0) return;   // empty alignment, written by the forward pass
+    const int mode = a.mode;
+    const bool local = mode == SW_ALIGN_LOCAL;
+    if (local && (R->score <= 0 || m <= 0 || n <= 0)) return;   // empty alignment, written by the forward pass
     const uint8_t *q = a.queries + P.q_off;
     const uint8_t *tb = target_base(a.db, P.t_sorted);
     const int32_t o = a.gap_open, e = a.gap_extend;
@@ -242,6 +295,22 @@ __global__ void __launch_bounds__(32) k_align_bwd(const AlignArgs a) {
     int64_t k = 0;
     int done = 0, status = 0;
     int64_t cells = 0;
+    // State H on the first row or column of a non-local mode: the leading gap
+    // the mode prices there (global: either; semi-global: the first column),
+    // then stop.
+    auto boundary = [&]() {
+        if (i == 0 && mode == SW_ALIGN_GLOBAL)
+            while (j > 0 && k < max_ops) { rev[k++] = SW_OP_D; --j; }
+        if (j == 0 && (mode == SW_ALIGN_GLOBAL || mode == SW_ALIGN_SEMIGLOBAL))
+            while (i > 0 && k < max_ops) { rev[k++] = SW_OP_I; --i; }
+    };
+    if (!local && (i == 0 || j == 0)) {               // end cell on the boundary (or an empty side)
+        if (lane == 0) boundary();
+        done = 1;
+        i = __shfl_sync(0xffffffffu, i, 0);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        k = __shfl_sync(0xffffffffu, k, 0);
+    }
     while (!done) {
         if (i < 1) { status = 4; break; }             // not reached: a gap opens at row 1
         const int strip = (i - 1) / kStrip;
@@ -250,12 +319,12 @@ __global__ void __launch_bounds__(32) k_align_bwd(const AlignArgs a) {
         __syncwarp();
         load_profile(prof, mat, q, m, r0, lane);
         __syncwarp();
+        const int row0 = r0 + lane * kAR + 1;
         int32_t H[kAR], E[kAR];
 #pragma unroll
-        for (int r = 0; r < kAR; ++r) { H[r] = 0; E[r] = kNegInf; }
-        int32_t hd = 0, pub_h = 0, pub_f = kNegInf;
+        for (int r = 0; r < kAR; ++r) { H[r] = first_col(mode, row0 + r, o, e); E[r] = kNegInf; }
+        int32_t hd = first_col(mode, row0 - 1, o, e), pub_h = 0, pub_f = kNegInf;
         const int2 *ck_in = strip > 0 ? a.ckpt + P.ckpt_off + int64_t(strip - 1) * (n + 1) : nullptr;
-        const int row0 = r0 + lane * kAR + 1;
         const bool lane_used = row0 <= i;             // rows below the path's row are never read
         for (int s = 0; s < cols + 31; ++s) {
             int32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1);
@@ -263,7 +332,7 @@ __global__ void __launch_bounds__(32) k_align_bwd(const AlignArgs a) {
             const int jj = s - lane + 1;
             if (jj >= 1 && jj <= cols && lane_used) {
                 if (lane == 0) {
-                    if (strip == 0) { hin = 0; fin = kNegInf; }
+                    if (strip == 0) { hin = first_row(mode, jj, o, e); fin = kNegInf; }
                     else { const int2 v = ck_in[jj]; hin = v.x; fin = v.y; }
                 }
                 const int c = target_code(tb, jj - 1);
@@ -279,9 +348,9 @@ __global__ void __launch_bounds__(32) k_align_bwd(const AlignArgs a) {
                     const int32_t up_o = up - o;
                     f = __viaddmax_s32(f, -e, up_o);
                     const int32_t diag = d + sc[r];
-                    const int32_t h = max3(diag, e_r, max(f, 0));
+                    const int32_t h = max3(diag, e_r, local ? max(f, 0) : f);
                     uint32_t b = 0;
-                    if (h == 0) b |= F_ZERO;
+                    if (local && h == 0) b |= F_ZERO;
                     if (h == diag) b |= F_DIAG;
                     if (h == e_r) b |= F_HE;
                     if (h == f) b |= F_HF;
@@ -306,7 +375,11 @@ __global__ void __launch_bounds__(32) k_align_bwd(const AlignArgs a) {
             for (;;) {
                 if (k >= max_ops) { status = 1; done = 1; break; }
                 if (state == 0) {
-                    if (i == 0 || j == 0) { done = 1; break; }
+                    if (i == 0 || j == 0) {
+                        if (!local) boundary();
+                        done = 1;
+                        break;
+                    }
                     if (i <= r0) break;                // continue in the strip above
                     const uint8_t b = flags[int64_t(j - 1) * kStrip + (i - r0 - 1)];
                     if (b & F_ZERO) { done = 1; break; }

@@ -166,6 +166,7 @@ struct AlignArgs {
     uint8_t *rev;
     uint8_t *ops;
     int32_t gap_open, gap_extend;
+    int32_t mode;              // SW_ALIGN_LOCAL / GLOBAL / SEMIGLOBAL / OVERLAP
 };
 
 // Non-local alignment modes in int32 (k_modes.cu): several queries, each

@@ -93,6 +93,12 @@ def test_align_rejects_bad_arguments_on_host(lib):
     rc = lib.sw_align(None, None, off.ctypes.data, 1, pq.ctypes.data, pt.ctypes.data, 1, None, 10, 1,
                       None, None, 0, None, None)
     assert rc == 1 and "db is NULL" in binding.sw_last_error()
+    rc = lib.sw_align_mode(None, None, off.ctypes.data, 1, pq.ctypes.data, pt.ctypes.data, 1, None, 10, 1, 7,
+                           None, None, 0, None, None)
+    assert rc == 1 and "unknown alignment mode" in binding.sw_last_error()
+    rc = lib.sw_align_mode(None, None, off.ctypes.data, 1, pq.ctypes.data, pt.ctypes.data, 1, None, 10, 1, 1,
+                           None, None, 0, None, None)
+    assert rc == 1 and "db is NULL" in binding.sw_last_error()
 
 
 def test_alignment_struct_sizes():

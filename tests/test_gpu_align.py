@@ -16,11 +16,12 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-def _check_pairs(gpu, qs, db, S, o, e, pq, pt, A=None):
+def _check_pairs(gpu, qs, db, S, o, e, pq, pt, A=None, mode="local"):
     A = A or S.shape[0]
     with gpu.Database(db.residues, db.offsets, A) as d:
-        aln, ops, st = d.align(qs.residues, qs.offsets, pq, pt, S, o, e, stats=True)
-    want = oracle.align_pairs(qs, db, pq, pt, S, o, e)
+        aln, ops, st = d.align(qs.residues, qs.offsets, pq, pt, S, o, e, stats=True,
+                               alignment=oracle.MODES[mode])
+    want = oracle.align_pairs(qs, db, pq, pt, S, o, e, mode=mode)
     for k, w in enumerate(want):
         a = aln[k]
         got = {"score": int(a["score"]), "q_begin": int(a["q_begin"]), "q_end": int(a["q_end"]),
@@ -154,3 +155,59 @@ def test_more_strips_than_warps(gpu):
     pq, pt = _all_pairs(qs.n, db.n)
     for o, e in ((10, 1), (3, 5), (0, 2)):
         _check_pairs(gpu, qs, db, synth.blosum62(), o, e, pq, pt)
+
+
+# ---- non-local modes (sw_align_mode; oracle/align_modes.c) -------------------
+
+MODE_NAMES = ["global", "semiglobal", "overlap"]
+
+
+@pytest.mark.parametrize("mode", MODE_NAMES)
+def test_modes_several_strips(gpu, mode):
+    """Every pair of queries spanning 1-4 strips (ragged tails) and targets from 1 to
+    1,100 residues, including empty ones: score, coordinates and every op."""
+    rng = np.random.default_rng(300 + MODE_NAMES.index(mode))
+    db = synth.seqset_from_lengths(rng, [1, 2, 255, 256, 257, 600, 1100, 31, 0, 90])
+    qs = synth.seqset_from_lengths(rng, [1, 100, 256, 257, 513, 800, 0])
+    pq, pt = _all_pairs(qs.n, db.n)
+    aln, _, _ = _check_pairs(gpu, qs, db, synth.blosum62(), 10, 1, pq, pt, mode=mode)
+    if mode == "global":
+        assert (aln["score"] < 0).any()
+
+
+@pytest.mark.parametrize("mode", MODE_NAMES)
+@pytest.mark.parametrize("o,e", [(0, 2), (3, 7), (5, 5)])
+def test_modes_ties_and_penalties(gpu, mode, o, e):
+    """A 3-letter alphabet with free or cheap gap opening: many equal-score paths, so the
+    end cell and every step follow the tie rules; open below, above and equal to extend."""
+    rng = np.random.default_rng(400 + 10 * o + e + MODE_NAMES.index(mode))
+    S = rng.integers(-2, 3, size=(3, 3)).astype(np.int32)
+    db = synth.random_seqset(rng, 40, 0, 300, 3)
+    qs = synth.random_seqset(rng, 3, 0, 400, 3)
+    pq, pt = _all_pairs(qs.n, db.n)
+    _check_pairs(gpu, qs, db, S, o, e, pq, pt, mode=mode)
+
+
+@pytest.mark.parametrize("mode", MODE_NAMES)
+def test_mode_alignment_scores_equal_search_scores(gpu, mode):
+    """The alignment's score is the mode's search score of the same pair."""
+    rng = np.random.default_rng(500 + MODE_NAMES.index(mode))
+    db = synth.seqset_from_lengths(rng, rng.integers(0, 700, 60))
+    qs = synth.seqset_from_lengths(rng, [50, 333])
+    S = synth.blosum62()
+    with gpu.Database(db.residues, db.offsets, 24) as d:
+        scores, _, _ = d.search(qs.residues, qs.offsets, S, 11, 1, top_k=0, alignment=oracle.MODES[mode])
+        pq, pt = _all_pairs(qs.n, db.n)
+        aln, _, _ = d.align(qs.residues, qs.offsets, pq, pt, S, 11, 1, alignment=oracle.MODES[mode])
+    np.testing.assert_array_equal(aln["score"].reshape(qs.n, db.n), scores)
+
+
+def test_mode_alignment_rejects_unknown_mode_and_overflow(gpu):
+    rng = np.random.default_rng(600)
+    db = synth.seqset_from_lengths(rng, [100, 200])
+    qs = synth.seqset_from_lengths(rng, [50])
+    with gpu.Database(db.residues, db.offsets, 24) as d:
+        with pytest.raises(gpu.SwError, match="SW_ERR_INVALID_ARG"):
+            d.align(qs.residues, qs.offsets, [0], [0], synth.blosum62(), 10, 1, alignment=5)
+        with pytest.raises(gpu.SwError, match="SW_ERR_OVERFLOW"):
+            d.align(qs.residues, qs.offsets, [0], [0], synth.blosum62(), 1 << 20, 1 << 20, alignment=1)
