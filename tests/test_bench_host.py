@@ -1,0 +1,73 @@
+"""Host logic of bench.py (CPU only): the launch key and DRAM-traffic record
+lookup behind ``roofline.traffic``, and the reference arm's JSON line (the
+oracle on the host cores)."""
+import hashlib
+import importlib.util
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_launch_key_names_the_configuration():
+    b = _bench()
+    base = b.launch_key(b.parse_args([]))
+    assert base == "swissprot_like_20q/scale1/plain/lanes0/rows0/prec0/longrows0/cutoff0"
+    assert b.launch_key(b.parse_args(["--alignment", "global"])) == base + "/global"
+    assert b.launch_key(b.parse_args(["--lanes", "8", "--rows", "24"])) != base
+    assert b.launch_key(b.parse_args(["--db-scale", "0.5"])) != base
+
+
+def test_traffic_record_needs_the_same_launch_and_kernel_source(tmp_path, monkeypatch):
+    b = _bench()
+    csrc = tmp_path / "paper_2203_11100_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (csrc / "k_inter16.cu").write_text("// inter kernel v1\n")
+    (csrc / "k_modes16.cu").write_text("// modes kernel v1\n")
+    sha = lambda p: hashlib.sha256(p.read_bytes()).hexdigest()
+    key = b.launch_key(b.parse_args([]))
+    gkey = b.launch_key(b.parse_args(["--alignment", "global"]))
+    (tmp_path / "profiles" / "x.md").write_text(
+        "# a capture\n\n"
+        f"traffic: launch={key} dram_bytes_per_launch=1000 source_sha256={sha(csrc / 'k_inter16.cu')}\n"
+        f"traffic: launch={gkey} source=k_modes16.cu dram_bytes_per_launch=2000 "
+        f"source_sha256={sha(csrc / 'k_modes16.cu')}\n")
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    assert b.traffic_per_launch(b.parse_args([])) == 1000.0
+    assert b.traffic_per_launch(b.parse_args(["--alignment", "global"])) == 2000.0
+    assert b.traffic_per_launch(b.parse_args(["--alignment", "overlap"])) is None     # no record
+    assert b.traffic_per_launch(b.parse_args(["--lanes", "8", "--rows", "32"])) is None
+    (csrc / "k_inter16.cu").write_text("// inter kernel v2\n")                        # kernel changed
+    assert b.traffic_per_launch(b.parse_args([])) is None
+    assert b.traffic_per_launch(b.parse_args(["--alignment", "global"])) == 2000.0
+
+
+def test_reference_arm_prints_one_json_line():
+    """--impl reference times the oracle on the host cores and prints the contract's keys."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--cpu-sample-cells", "1e8"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["value"] > 0 and d["unit"] == "GCUPS" and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == "swissprot_like_20q"
