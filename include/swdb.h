@@ -117,7 +117,8 @@ typedef struct {
                                  intra-task kernel; 0 = library default, <0 = never */
     int32_t lanes;            /* lanes per database-sequence pair in the inter-task kernel
                                  (4, 8, 16 or 32); 0 = chosen per query by the library */
-    int32_t rows_per_lane;    /* query rows held per lane (16, 24 or 32); 0 = chosen per query */
+    int32_t rows_per_lane;    /* query rows held per lane (16, 24 or 32; 8 with 32 lanes);
+                                 0 = chosen per query */
     void *workspace;          /* caller-owned device scratch, or NULL for the handle's own */
     size_t workspace_bytes;   /* size of workspace */
     int32_t flags;            /* SW_FLAG_* bits */
