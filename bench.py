@@ -151,13 +151,34 @@ def combine_ranks(dist: Dist, local_ms: float, local_cells: float):
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 
+def smi_gpu_id(device: int) -> str:
+    """An nvidia-smi --id that names the same GPU as CUDA device `device`.
+
+    nvidia-smi ignores CUDA_VISIBLE_DEVICES, so a CUDA ordinal can name
+    another GPU of the machine; the device UUID (or else its PCI bus id)
+    names this one."""
+    import torch
+    p = torch.cuda.get_device_properties(device)
+    uuid = getattr(p, "uuid", None)
+    if uuid is not None:
+        u = str(uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    dom, bus, dv = (getattr(p, k, None) for k in ("pci_domain_id", "pci_bus_id", "pci_device_id"))
+    if bus is not None:
+        return f"{int(dom or 0):08x}:{int(bus):02x}:{int(dv or 0):02x}.0"
+    return str(device)
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
+    def __init__(self, device: int):
+        try:
+            self.gpu = smi_gpu_id(device)
+        except Exception:
+            self.gpu = str(device)
         self.proc = None
         self.path = None
 
@@ -174,7 +195,7 @@ class ClockSampler:
 
     def stop(self) -> dict:
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "gpu": self.gpu}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -203,12 +224,12 @@ class ClockSampler:
                                       "--format=csv,noheader,nounits"], capture_output=True, text=True,
                                      timeout=10).stdout.split(",")
                 return {"sm_mhz": float(out[0]), "sm_max_mhz": float(out[1]), "reasons": sorted(reasons),
-                        "samples": 0, "note": "timed region shorter than the 200 ms sampling period; "
-                                              "clocks read once right after it"}
+                        "samples": 0, "gpu": self.gpu, "note": "timed region shorter than the 200 ms sampling "
+                                                               "period; clocks read once right after it"}
             except Exception:
                 pass
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "gpu": self.gpu}
 
 
 # ---------------------------------------------------------------------------

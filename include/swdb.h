@@ -126,7 +126,13 @@ typedef struct {
                                    pipelines) or 32 (2-warp pipelines); 0 = library choice */
     int32_t alignment;        /* sw_alignment_mode; 0 = local */
     int32_t reserved;
-} sw_search_opts;             /* 56 bytes */
+    int32_t *status_out;      /* NULL, or a device (or pinned host) int32 that receives the search's
+                                 device-side status on the stream, after all of its kernels: 0, or
+                                 SW_ERR_TIMEOUT when a bounded wait of the intra-task kernel gave up
+                                 (the long sequences' scores and the hits are then not valid).  For
+                                 callers whose call returns before the device finishes (device-only
+                                 outputs, stats NULL): read it once the stream has synchronised. */
+} sw_search_opts;             /* 64 bytes */
 
 /* Capture the device work of the search into a CUDA graph on first use and
  * replay it while the call's signature (buffers, query lengths, matrix,
@@ -220,7 +226,12 @@ int sw_search_workspace_size(const sw_db *db, const int64_t *q_offsets, int32_t 
  * stream synchronises).  Calls that share a workspace (the handle's own
  * workspace when opts->workspace is NULL) must not overlap in time.
  * Errors: SW_ERR_INVALID_ARG, SW_ERR_OVERFLOW (|matrix|, o, e or lengths
- * too large for exact int32), SW_ERR_UNSUPPORTED, SW_ERR_OOM, SW_ERR_CUDA.
+ * too large for exact int32), SW_ERR_UNSUPPORTED, SW_ERR_OOM, SW_ERR_CUDA,
+ * SW_ERR_TIMEOUT (a bounded device-side wait of the intra-task kernel gave
+ * up; reported by the return code only when the call waits for the device,
+ * i.e. a host output or stats; an asynchronous call reports it through
+ * opts->status_out).  A NULL stream means the handle's own stream here,
+ * whereas sw_search_no_alloc reads NULL as the legacy default stream.
  */
 int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32_t n_q,
               const int32_t *matrix, int32_t gap_open, int32_t gap_extend, int32_t top_k,
@@ -385,7 +396,8 @@ int sw_align_mode(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, i
  *   matrix      HOST pointer, alphabet_size^2 int32, as for sw_search
  *   gap_open, gap_extend   as for sw_search
  *   scores      DEVICE pointer, n_seqs int32, database in original order
- *   stream      cudaStream_t, or NULL for the legacy default stream
+ *   stream      cudaStream_t, or NULL for the legacy default stream (unlike
+ *               sw_search, where NULL means the handle's own stream)
  * Results equal sw_search's for the same arguments.  The work is queued on
  * the stream and the call returns without waiting.
  *
@@ -393,7 +405,9 @@ int sw_align_mode(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, i
  * memory that the library defines; every GPU that loads the library holds
  * it until the process exits.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  Calls share the array: calls whose work
+ * before any stream capture.  The address is cached per device and CUDA
+ * context: after the context is destroyed and a new one created, the next
+ * call looks it up again (so make that call, too, outside any capture).  Calls share the array: calls whose work
  * overlaps on the GPU race.  A query/database combination that needs more
  * scratch than the array holds (multi-pass queries, m > 128, need about 4
  * bytes per byte of the database layout) is rejected with

@@ -40,7 +40,8 @@ class SwSearchOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("mode", ctypes.c_int32), ("long_cutoff", ctypes.c_int64),
                 ("lanes", ctypes.c_int32), ("rows_per_lane", ctypes.c_int32),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t), ("flags", ctypes.c_int32),
-                ("long_rows_per_lane", ctypes.c_int32), ("alignment", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("long_rows_per_lane", ctypes.c_int32), ("alignment", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("status_out", ctypes.c_void_p)]
 
 
 class SwSearchStats(ctypes.Structure):
@@ -172,8 +173,13 @@ def sw_db_get_info(handle) -> dict:
 
 
 def _opts(precision, mode, long_cutoff, lanes, rows_per_lane, workspace, flags=0, long_rows_per_lane=0,
-          alignment=SW_ALIGN_LOCAL):
+          alignment=SW_ALIGN_LOCAL, status_out=None):
     o = SwSearchOpts()
+    if status_out is not None:
+        addr, is_cuda = _addr(status_out, np.int32, "status_out")
+        if not is_cuda and not (_is_tensor(status_out) and status_out.is_pinned()):
+            raise ValueError("status_out must be a CUDA tensor or a pinned host tensor (int32)")
+        o.status_out = addr
     o.alignment = alignment
     o.flags = flags
     o.long_rows_per_lane = long_rows_per_lane
@@ -205,9 +211,11 @@ def sw_search_workspace_size(handle, q_offsets, top_k: int, precision=SW_PREC_AU
 def sw_search(handle, queries, q_offsets, matrix, gap_open: int, gap_extend: int, top_k: int,
               scores_out=None, hits_out=None, precision=SW_PREC_AUTO, mode=SW_MODE_AUTO, long_cutoff=0,
               lanes=0, rows_per_lane=0, workspace=None, stats: bool = False, stream=None, graph: bool = False,
-              long_rows_per_lane=0, alignment=SW_ALIGN_LOCAL):
+              long_rows_per_lane=0, alignment=SW_ALIGN_LOCAL, status_out=None):
     """Run sw_search.  Outputs are written into scores_out / hits_out (numpy =
-    host, torch CUDA tensor = device).  Returns a stats dict when stats=True."""
+    host, torch CUDA tensor = device).  Returns a stats dict when stats=True.
+    status_out (an int32 CUDA or pinned tensor) receives the device-side status
+    on the stream: 0, or SW_ERR_TIMEOUT when a bounded wait gave up."""
     lib = load_library()
     q_offsets = np.ascontiguousarray(q_offsets, dtype=np.int64)
     matrix = np.ascontiguousarray(matrix, dtype=np.int32)
@@ -217,9 +225,9 @@ def sw_search(handle, queries, q_offsets, matrix, gap_open: int, gap_extend: int
         raise TypeError("hits_out must have dtype HIT_DTYPE")
     hp, h_cuda = _addr(hits_out, None, "hits_out")
     o = _opts(precision, mode, long_cutoff, lanes, rows_per_lane, workspace, SW_FLAG_GRAPH if graph else 0,
-              long_rows_per_lane, alignment)
+              long_rows_per_lane, alignment, status_out)
     st = SwSearchStats() if stats else None
-    if stream is None and (q_cuda or s_cuda or h_cuda or workspace is not None):
+    if stream is None and (q_cuda or s_cuda or h_cuda or workspace is not None or status_out is not None):
         import torch
         stream = torch.cuda.current_stream().cuda_stream
     rc = lib.sw_search(handle, qp, q_offsets.ctypes.data, len(q_offsets) - 1, matrix.ctypes.data,

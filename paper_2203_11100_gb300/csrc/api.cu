@@ -994,6 +994,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
         SW_CUDA_TRY(cudaMemcpyAsync(buf.qp, qp.data(), sizeof(int32_t) * qp.size(), cudaMemcpyHostToDevice, st));
     }
     int last_lanes = plan.lanes, last_rows = plan.rows;
+    int32_t *status_out = opts ? opts->status_out : nullptr;
 
     // All device work of the search, in stream order.  Run directly, or
     // captured once into a CUDA graph and replayed (SW_FLAG_GRAPH).
@@ -1072,6 +1073,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
         }
         if (top_k > 0 && n_q > 0 && (hits_out != nullptr))
             TIMED(LaunchTimer::OTHER, launch_topk(d_scores, n_q, db->n_seqs, top_k, d_hits, st));
+        if (status_out) SW_CUDA_TRY(cudaMemcpyAsync(status_out, d_status, sizeof(int32_t), cudaMemcpyDefault, st));
         return SW_OK;
     }
 
@@ -1234,6 +1236,8 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
     }
     if (top_k > 0 && n_q > 0 && (hits_out != nullptr))
         TIMED(LaunchTimer::OTHER, launch_topk(d_scores, n_q, db->n_seqs, top_k, d_hits, st));
+    // the device-side status (a bounded wait that gave up), for asynchronous callers
+    if (status_out) SW_CUDA_TRY(cudaMemcpyAsync(status_out, d_status, sizeof(int32_t), cudaMemcpyDefault, st));
     return SW_OK;
     };
 
@@ -1242,7 +1246,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
         // Everything the captured work depends on, byte for byte.
         std::string key;
         auto put = [&key](const void *p, size_t n) { key.append(static_cast<const char *>(p), n); };
-        const void *ptrs[] = {d_queries, d_scores, d_hits, ws, st};
+        const void *ptrs[] = {d_queries, d_scores, d_hits, ws, st, status_out};
         put(ptrs, sizeof ptrs);
         const int32_t ints[] = {n_q, gap_open, gap_extend, top_k, plan.mode, plan.precision, plan.lanes, plan.rows,
                                 hits_out != nullptr, plan.rows_long, plan.warps_long, plan.alignment};

@@ -20,7 +20,11 @@
 // (in host code it names a host-side stand-in), so the first call on each
 // device looks the address up with cudaGetSymbolAddress while that device is
 // current, checks the result and caches it; that first call should come
-// before any stream capture.  All calls share the array and it keeps the
+// before any stream capture.  The cached address belongs to the CUDA context
+// it was looked up in: if that context is destroyed and another one created
+// (cudaDeviceReset, say), the module is loaded again and the array may move,
+// so the cache is keyed by the context's unique id as well and the lookup is
+// repeated in a new context.  All calls share the array and it keeps the
 // previous call's contents: the counters that must start at zero are cleared
 // on the stream at the start of every call, and calls whose work overlaps on
 // the GPU (on different streams, or from several threads) race on it.
@@ -39,6 +43,37 @@ static __device__ __align__(256) unsigned char g_no_alloc_scratch[kScratchBytes]
 
 std::mutex g_mu;
 unsigned char *g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};   // context id the address was looked up in
+
+// Unique id of the calling thread's current CUDA context (driver entry points
+// fetched through the runtime, so the library needs no link to the driver
+// library); 0 when there is no current context or the driver lacks the call.
+unsigned long long current_context_id() {
+    using GetCurrent = int (*)(void **);
+    using GetId = int (*)(void *, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        cudaGetLastError();
+    }
+    if (!get_current || !get_id) return 0;
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != 0 || !ctx) return 0;
+    if (get_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 bool device_ptr(const void *p) {
     cudaPointerAttributes at;
@@ -80,15 +115,18 @@ extern "C" int sw_search_no_alloc(const sw_db *db, const uint8_t *query, int32_t
     } restore{prev};
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
-    // Device address of the scratch array, looked up once per device.
+    // Device address of the scratch array, looked up once per device (and
+    // again only if the device's context has changed since).
     unsigned char *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_scratch_ptr[device]) {
+        const unsigned long long ctx = current_context_id();
+        if (!g_scratch_ptr[device] || (ctx != 0 && ctx != g_scratch_ctx[device])) {
             void *p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_no_alloc_scratch);
             if (e != cudaSuccess || !p) return set_error(SW_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
             g_scratch_ptr[device] = static_cast<unsigned char *>(p);
+            g_scratch_ctx[device] = current_context_id();
         }
         scratch = g_scratch_ptr[device];
     }

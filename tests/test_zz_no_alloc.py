@@ -7,7 +7,8 @@ start-up, and processes whose device memory belongs to another framework's
 pool.  Its scratch is a fixed device array the library owns, shared by all
 calls and keeping the previous call's contents, so this test makes two calls
 in a row (the first one leaves saturated sequences in the shared overflow
-list) and checks each against sw_search, exactly (scores are integers).
+list) and checks each against sw_search and against the CPU oracle, exactly
+(scores are integers).
 
 This file is named to be collected last, so that a run that stops at its
 first failure has already run every other test.
@@ -15,6 +16,7 @@ first failure has already run every other test.
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -58,6 +60,9 @@ def test_no_alloc_matches_sw_search_twice(gpu):
         np.testing.assert_array_equal(out[1].cpu().numpy(), wants[1])
         assert free_after == free_before
         assert (wants[0] > 32767 - 11).sum() >= 2                  # saturation was exercised
+    exact = oracle.all_scores(synth.seqset_from_list(queries), db, S, 10, 1)
+    np.testing.assert_array_equal(out[0].cpu().numpy().astype(np.int64), exact[0])
+    np.testing.assert_array_equal(out[1].cpu().numpy().astype(np.int64), exact[1])
 
 
 def test_no_alloc_rejects_oversized_scratch(gpu):
