@@ -48,6 +48,9 @@ I32_DPX_OPS_PER_CELL = 3.0
 # Non-local modes in packed int16x2: E, F, H (2) and the profile permute per
 # cell pair, no running max over the matrix = 5 per 2 cells.
 MODES16_OPS_PER_CELL = 2.5
+# Batched form (two queries against one database sequence): the profile is a
+# ready int16x2 word per row, no byte permute: 4.5 per cell pair.
+BATCH_OPS_PER_CELL = 2.25
 ALIGNMENTS = {"local": 0, "global": 1, "semiglobal": 2, "overlap": 3}
 RESULT_TIMEOUT_S = 300.0   # a served request that takes longer than this is a failure
 
@@ -86,6 +89,12 @@ def parse_args(argv=None):
                         "workload's gap penalties and at 10/2")
     p.add_argument("--align", action="store_true",
                    help="traceback benchmark: align the top-k hits of the workload's search")
+    p.add_argument("--sub-records", default="auto",
+                   help="other workloads timed after the main one, each reported with its own roofline, clocks "
+                        "and oracle sample: comma list of db2k_q100, long_4q_50k, batched_512q (batched and "
+                        "plain forms), 'none', or 'auto' (all of them on one GPU for the default workload)")
+    p.add_argument("--sub-steps", type=int, default=0, help="timed steps of every sub-record (0 = per workload)")
+    p.add_argument("--sub-warmup", type=int, default=-1, help="warm-up steps of every sub-record (-1 = per workload)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-cells", type=float, default=6e10,
                    help="cells of the oracle's bounded sample (about 10-20 s on 16 cores)")
@@ -308,7 +317,10 @@ def run_ours(args, dist: Dist):
     nq, n = w.queries.n, w.db.n
     cells_step = float(w.cells)
     db = swdb.Database(w.db.residues, w.db.offsets, len(synth.ALPHABET), device=dev)
-    stream = torch.cuda.current_stream()
+    # A stream of its own, so that the CUDA events bracket the searches on the
+    # stream they run on (the legacy default stream's handle is NULL, which the
+    # library reads as "the handle's own stream").
+    stream = torch.cuda.Stream(device=dev)
     q_dev = torch.from_numpy(w.queries.residues).to(f"cuda:{dev}")
     scores = torch.empty((nq, n), dtype=torch.int32, device=f"cuda:{dev}")
     hits = torch.empty((nq, w.top_k, 2), dtype=torch.int64, device=f"cuda:{dev}")
@@ -428,7 +440,185 @@ def run_ours(args, dist: Dist):
             "rescored_per_step": rescored / args.steps,
             "clocks": clk,
         }
+        subs = sub_record_names(args, dist)
+        if subs:
+            out["workloads"] = run_sub_records(args, subs, db, w, rate_dpx, sms, dev)
+            if "batched_512q/batched" in out["workloads"] and "batched_512q/plain" in out["workloads"]:
+                b = out["workloads"]["batched_512q/batched"]["value"]
+                p_ = out["workloads"]["batched_512q/plain"]["value"]
+                out["batched_vs_plain"] = {"workload": "batched_512q", "batched_gcups": b, "plain_gcups": p_,
+                                           "ratio": b / p_ if p_ else None}
     db.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# sub-records: the other workloads, measured after the main one
+
+SUB_DEFAULTS = {            # (warm-up, timed steps) per workload
+    "db2k_q100": (5, 50),
+    "long_4q_50k": (3, 5),
+    "batched_512q": (1, 3),     # 38-45 s per step: one warm-up step allocates and settles
+}
+
+
+def sub_record_names(args, dist) -> list:
+    if args.sub_records == "none" or args.impl != "ours":
+        return []
+    if args.sub_records == "auto":
+        default = (dist.world == 1 and args.workload == "swissprot_like_20q" and args.db_scale == 1.0
+                   and args.mode == "plain" and args.alignment == "local" and not args.graph
+                   and not (args.lanes or args.rows or args.precision or args.long_rows or args.long_cutoff))
+        return list(SUB_DEFAULTS) if default else []
+    names = [x.strip() for x in args.sub_records.split(",") if x.strip()]
+    for n in names:
+        if n not in SUB_DEFAULTS:
+            raise SystemExit(f"unknown sub-record workload {n!r}")
+    return names
+
+
+def timed_steps(step, steps: int, warmup: int, stream, dev: int):
+    """W untimed warm-up calls, then K calls bracketed by CUDA events on the
+    launching stream, with the SM clocks sampled meanwhile."""
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    st_all = [step() for _ in range(steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), st_all, clocks.stop()
+
+
+def kernel_roofline(st_all, family: str, kernel: str, ops_per_cell: float, rate_dpx: float, sms: int,
+                    mhz: float, note: str = "") -> dict:
+    """Achieved cell rate of one kernel family (its own cells over its own
+    CUDA-event time) against the DPX-issue roofline for ops_per_cell."""
+    if family == "long":
+        cells = float(sum(s["long_cells"] for s in st_all))
+        ms = sum(s["intra_ms"] for s in st_all)
+        launches = len(st_all)
+    else:
+        cells = float(sum(s["inter_cells"] for s in st_all))
+        ms = sum(s["inter_ms"] for s in st_all)
+        launches = sum(s["inter_launches"] for s in st_all)
+    peak = rate_dpx * sms * mhz * 1e6 / ops_per_cell / 1e9
+    achieved = cells / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
+            "frac": achieved / peak if peak else None, "traffic": None, "kernel": kernel,
+            "peak_basis": f"measured {rate_dpx:.1f} DPX ops/SM/cycle x {sms} SMs x {mhz:.0f} MHz (median under "
+                          f"load) / {ops_per_cell} ops per cell" + note,
+            "kernel_ms_per_step": ms / max(len(st_all), 1), "avg_launch_ms": ms / max(launches, 1)}
+
+
+def oracle_sample(w, scores_dev, hits_dev, seed: int, max_cells: float) -> dict:
+    """The GPU's scores of a bounded sample of pairs against the oracle (all
+    host cores): every query's best hit, then random pairs up to max_cells
+    (every pair when the whole workload fits), and the top-k of sampled rows."""
+    import torch
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    nq, n = w.queries.n, w.db.n
+    qlen = w.queries.lengths.astype(np.float64)
+    tlen = w.db.lengths.astype(np.float64)
+    hits = hits_dev.cpu().numpy()
+    if float(w.cells) <= max_cells:
+        qi = np.repeat(np.arange(nq, dtype=np.int64), n)
+        ti = np.tile(np.arange(n, dtype=np.int64), nq)
+        what = "every pair"
+    else:
+        qi = [np.arange(nq, dtype=np.int64)]
+        ti = [hits[:, 0, 1].astype(np.int64)]
+        budget = max_cells - float((qlen[qi[0]] * tlen[ti[0]]).sum())
+        k = max(0, int(budget / (qlen.mean() * tlen.mean())))
+        qi.append(rng.integers(0, nq, k))
+        ti.append(rng.integers(0, n, k))
+        qi, ti = np.concatenate(qi), np.concatenate(ti)
+        what = f"each query's best hit and {k} random pairs"
+    cells = float((qlen[qi] * tlen[ti]).sum())
+    threads = oracle.default_threads()
+    t0 = time.perf_counter()
+    want = oracle.score_pairs(w.queries, w.db, qi, ti, w.matrix, w.gap_open, w.gap_extend, threads=threads)
+    dt = time.perf_counter() - t0
+    got = scores_dev[torch.from_numpy(qi).to(scores_dev.device), torch.from_numpy(ti).to(scores_dev.device)]
+    exact = bool(np.array_equal(got.cpu().numpy().astype(np.int64), want))
+    # top-k of the rows checked in full (small workloads) or the best hit's score (others)
+    if what == "every pair":
+        for q in range(nq):
+            s_, i_ = oracle.top_k(want[q * n:(q + 1) * n], w.top_k)
+            exact &= bool(np.array_equal((hits[q, :, 0] & 0xffffffff).astype(np.int32).astype(np.int64), s_))
+            exact &= bool(np.array_equal(hits[q, :, 1], i_))
+    return {"pairs": int(len(qi)), "what": what, "cells": cells, "oracle_s": dt, "cores": threads,
+            "bit_exact_vs_gpu": exact}
+
+
+def run_sub_records(args, names, db_main, w_main, rate_dpx: float, sms: int, dev: int) -> dict:
+    import torch
+    import paper_2203_11100_gb300 as swdb
+    out = {}
+    stream = torch.cuda.Stream(device=dev)
+    for name in names:
+        warm, steps = SUB_DEFAULTS[name]
+        if args.sub_warmup >= 0:
+            warm = args.sub_warmup
+        if args.sub_steps > 0:
+            steps = args.sub_steps
+        if name == "batched_512q":
+            w = synth.make_workload(name, seed=synth.SEED, db=w_main.db)
+            db, own = db_main, False
+            forms = [("batched", swdb.SW_MODE_BATCHED), ("plain", swdb.SW_MODE_PLAIN)]
+        else:
+            w = synth.make_workload(name, seed=synth.SEED)
+            db, own = swdb.Database(w.db.residues, w.db.offsets, len(synth.ALPHABET), device=dev), True
+            forms = [("plain", swdb.SW_MODE_PLAIN)]
+        q_dev = torch.from_numpy(w.queries.residues).to(f"cuda:{dev}")
+        scores = torch.empty((w.queries.n, w.db.n), dtype=torch.int32, device=f"cuda:{dev}")
+        hits = torch.empty((w.queries.n, w.top_k, 2), dtype=torch.int64, device=f"cuda:{dev}")
+        for form, mode in forms:
+            kw = dict(mode=mode)
+
+            def step():
+                return swdb.sw_search(db.handle, q_dev, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend,
+                                      w.top_k, scores, hits, stats=True, stream=stream.cuda_stream, **kw)
+
+            ms, st_all, clk = timed_steps(step, steps, warm, stream, dev)
+            mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+            cells = float(w.cells)
+            if name == "long_4q_50k":
+                roof = kernel_roofline(st_all, "long", "k_intra_i16x2", DPX_OPS_PER_CELL, rate_dpx, sms, mhz,
+                                       " (intra-task kernel: long sequences, on the side stream)")
+                roof["inter_task"] = kernel_roofline(st_all, "inter", "k_inter_i16x2", DPX_OPS_PER_CELL,
+                                                     rate_dpx, sms, mhz)
+            elif form == "batched":
+                roof = kernel_roofline(st_all, "inter", "k_batch_i16x2", BATCH_OPS_PER_CELL, rate_dpx, sms, mhz,
+                                       " (query pairs: one ready int16x2 profile word per row, no permute)")
+                roof["frac_of_plain_kernel_roofline"] = roof["achieved"] / (rate_dpx * sms * mhz * 1e6 /
+                                                                            DPX_OPS_PER_CELL / 1e9)
+            else:
+                roof = kernel_roofline(st_all, "inter", "k_inter_i16x2", DPX_OPS_PER_CELL, rate_dpx, sms, mhz)
+            rec = {"workload": name, "form": form, "value": cells * steps / (ms * 1e-3) / 1e9, "unit": UNIT,
+                   "steps": steps, "warmup": warm, "ms_per_step": ms / steps, "cells_per_step": cells,
+                   "queries": w.queries.n, "query_residues": int(w.queries.lengths.sum()), "db_seqs": w.db.n,
+                   "db_residues": int(w.db.lengths.sum()), "roofline": roof, "clocks": clk,
+                   "gpu_launches": sum(s["launches"] for s in st_all),
+                   "kernel_ms_per_step": {k: sum(s[k + "_ms"] for s in st_all) / steps
+                                          for k in ("inter", "rescore", "intra", "other")},
+                   "long_sequences": st_all[0]["long_sequences"],
+                   "rescored_per_step": sum(s["rescored"] for s in st_all) / steps,
+                   "launch": {k: v for k, v in kw.items() if k != "mode"} or "library choice per query"}
+            if not args.no_cpu_baseline:
+                rec["oracle_sample"] = oracle_sample(w, scores, hits, synth.SEED + 31 + len(out),
+                                                     max_cells=4e10 if name == "batched_512q" else 1e10)
+            out[f"{name}/{form}"] = rec
+        del scores, hits, q_dev
+        if own:
+            db.close()
     return out
 
 

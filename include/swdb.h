@@ -418,6 +418,60 @@ int sw_align_mode(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, i
 int sw_search_no_alloc(const sw_db *db, const uint8_t *query, int32_t m, const int32_t *matrix,
                        int32_t gap_open, int32_t gap_extend, int32_t *scores, void *stream);
 
+/*
+ * Database sharding over several GPUs (host-side steps; no device memory).
+ * The paper leaves multi-GPU execution to future work (Section 5), and SW#db
+ * spreads its search over GPU(s) (Section 2.3).  Every (query, sequence)
+ * score is independent, so the database splits into shards that separate
+ * GPUs search with the full query batch (one sw_db_load per shard, on its
+ * own device), each keeping its own top-k; the one exchange step is a
+ * gather of the shards' k best per query and the merge below.
+ *
+ * sw_shard_plan: partition n_seqs sequences (offsets as for sw_db_load, host
+ * pointer, n_seqs + 1 entries) into n_shards shards of balanced residue
+ * counts, each with sequences of every length range: sequences are dealt
+ * longest first (ties in the caller's order), each to the shard with the
+ * fewest residues so far (ties to the lower shard).  The largest and the
+ * smallest shard then differ by at most the longest sequence's residues.
+ * Outputs (host, caller-allocated): members[n_seqs] lists shard 0's
+ * sequences (the caller's indices) in increasing order, then shard 1's, and
+ * so on; member_offsets[n_shards + 1] delimits them.  Shard s's local
+ * sequence j is the caller's sequence members[member_offsets[s] + j], so a
+ * shard's local order is the caller's order.
+ * Errors: SW_ERR_INVALID_ARG (NULL pointer, n_shards < 1, bad offsets).
+ */
+int sw_shard_plan(const int64_t *offsets, int64_t n_seqs, int32_t n_shards, int64_t *members,
+                  int64_t *member_offsets);
+
+/*
+ * sw_hits_merge: the top-k of an unsharded search from the shards' top-k.
+ *   shard_hits  host, [n_shards][n_q][top_k]: shard s's hits as sw_search
+ *               returned them for its own database (db_index local to the
+ *               shard, {-1, -1} padding when the shard holds fewer than
+ *               top_k sequences)
+ *   members, member_offsets   the partition from sw_shard_plan
+ *   hits_out    host, [n_q][top_k]: score descending, then the caller's
+ *               database index ascending; {-1, -1} padding
+ * Exact: a sequence outside its shard's k best has k better sequences in
+ * that shard, so the merged list equals the unsharded search's top-k, ties
+ * included.  Errors: SW_ERR_INVALID_ARG (NULL pointer, bad count, a shard
+ * index outside its shard; nothing is written then).
+ */
+int sw_hits_merge(const sw_hit *shard_hits, const int64_t *members, const int64_t *member_offsets,
+                  int32_t n_shards, int32_t n_q, int32_t top_k, sw_hit *hits_out);
+
+/*
+ * sw_scores_scatter: one shard's score rows into the unsharded table.
+ *   shard_scores  host, [n_q][n_members] as sw_search returned them for the shard
+ *   members       host, the shard's n_members caller indices (its slice of
+ *                 sw_shard_plan's members)
+ *   scores_out    host, [n_q][n_seqs]; row q, column members[j] receives
+ *                 shard_scores[q][j]; other columns are left as they are
+ * Errors: SW_ERR_INVALID_ARG (NULL pointer, bad count, index >= n_seqs).
+ */
+int sw_scores_scatter(const int32_t *shard_scores, const int64_t *members, int64_t n_members, int32_t n_q,
+                      int64_t n_seqs, int32_t *scores_out);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char *sw_last_error(void);
 

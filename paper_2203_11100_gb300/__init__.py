@@ -24,6 +24,7 @@ from .binding import (  # noqa: F401
     SW_PREC_I32,
     SwError,
     Database,
+    ShardedDatabase,
     load_library,
     library_path,
     sw_align,
@@ -31,12 +32,15 @@ from .binding import (  # noqa: F401
     sw_db_free,
     sw_db_get_info,
     sw_db_load,
+    sw_hits_merge,
     sw_last_error,
     sw_probe_alu_rate,
     sw_probe_wait_timeout,
     sw_search,
     sw_search_no_alloc,
     sw_search_workspace_size,
+    sw_scores_scatter,
+    sw_shard_plan,
     sw_top_k,
     sw_version,
 )

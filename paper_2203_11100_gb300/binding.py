@@ -99,6 +99,12 @@ def load_library():
     lib.sw_align_mode.argtypes = [vp, vp, vp, i32, vp, vp, i64, vp, i32, i32, i32, vp, vp, i64,
                                   ctypes.POINTER(SwAlignStats), vp]
     lib.sw_align_mode.restype = ctypes.c_int
+    lib.sw_shard_plan.argtypes = [vp, i64, i32, vp, vp]
+    lib.sw_hits_merge.argtypes = [vp, vp, vp, i32, i32, i32, vp]
+    lib.sw_scores_scatter.argtypes = [vp, vp, i64, i32, i64, vp]
+    for name in ("sw_align", "sw_align_ops_capacity", "sw_probe_wait_timeout", "sw_shard_plan", "sw_hits_merge",
+                 "sw_scores_scatter"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("sw_db_load", "sw_db_free", "sw_db_get_info", "sw_search_workspace_size", "sw_search",
                  "sw_top_k", "sw_probe_alu_rate", "sw_search_no_alloc"):
         getattr(lib, name).restype = ctypes.c_int
@@ -328,6 +334,107 @@ def sw_align(handle, queries, q_offsets, pair_query, pair_target, matrix, gap_op
                                         ctypes.byref(st) if stats else None, stream))
     sd = {f: getattr(st, f) for f, _ in SwAlignStats._fields_} if stats else None
     return aln, ops[:cap], sd
+
+
+def sw_shard_plan(offsets, n_shards: int):
+    """Partition a database (offsets, host) into n_shards residue-balanced,
+    length-stratified shards.  Returns (members int64 [n_seqs], member_offsets
+    int64 [n_shards + 1]); shard s is members[member_offsets[s]:member_offsets[s+1]]
+    (the caller's indices, increasing)."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    n = len(offsets) - 1
+    members = np.zeros(max(n, 1), dtype=np.int64)
+    moff = np.zeros(int(n_shards) + 1 if n_shards > 0 else 1, dtype=np.int64)
+    _check(load_library().sw_shard_plan(offsets.ctypes.data, n, int(n_shards), members.ctypes.data, moff.ctypes.data))
+    return members[:n], moff
+
+
+def sw_hits_merge(shard_hits, members, member_offsets, top_k: int) -> np.ndarray:
+    """Merge shards' top-k lists (HIT_DTYPE [n_shards, n_q, top_k], shard-local
+    indices) into the unsharded top-k (HIT_DTYPE [n_q, top_k], caller's indices)."""
+    shard_hits = np.ascontiguousarray(shard_hits, dtype=HIT_DTYPE)
+    members = np.ascontiguousarray(members, dtype=np.int64)
+    moff = np.ascontiguousarray(member_offsets, dtype=np.int64)
+    n_shards, n_q = shard_hits.shape[0], shard_hits.shape[1]
+    if shard_hits.shape[2] != top_k or len(moff) != n_shards + 1:
+        raise ValueError("shard_hits must be [n_shards, n_q, top_k] and member_offsets n_shards + 1 long")
+    out = np.zeros((n_q, top_k), dtype=HIT_DTYPE)
+    _check(load_library().sw_hits_merge(shard_hits.ctypes.data if shard_hits.size else None,
+                                        members.ctypes.data if members.size else None, moff.ctypes.data,
+                                        n_shards, n_q, int(top_k), out.ctypes.data if out.size else None))
+    return out
+
+
+def sw_scores_scatter(shard_scores, members, scores_out) -> None:
+    """Write one shard's score rows (int32 [n_q, n_members]) into the columns
+    `members` of the unsharded table scores_out (int32 [n_q, n_seqs], host)."""
+    shard_scores = np.ascontiguousarray(shard_scores, dtype=np.int32)
+    members = np.ascontiguousarray(members, dtype=np.int64)
+    if not (isinstance(scores_out, np.ndarray) and scores_out.dtype == np.int32 and scores_out.flags.c_contiguous):
+        raise TypeError("scores_out must be a C-contiguous int32 numpy array")
+    n_q, n_seqs = scores_out.shape
+    if shard_scores.shape != (n_q, len(members)):
+        raise ValueError("shard_scores must be [n_q, len(members)]")
+    _check(load_library().sw_scores_scatter(shard_scores.ctypes.data if shard_scores.size else None,
+                                            members.ctypes.data if members.size else None, len(members), n_q,
+                                            n_seqs, scores_out.ctypes.data if scores_out.size else None))
+
+
+class ShardedDatabase:
+    """A database split into residue-balanced shards (sw_shard_plan), one
+    resident handle per shard; shard s lives on devices[s % len(devices)].
+    search() runs the full query batch on every shard and merges: top-k by
+    sw_hits_merge, score rows by sw_scores_scatter.  Results equal an
+    unsharded search's, ties included."""
+
+    def __init__(self, residues, offsets, alphabet_size: int, n_shards: int, devices=(0,)):
+        residues = np.ascontiguousarray(residues, dtype=np.uint8)
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        self.n_seqs = len(offsets) - 1
+        self.members, self.member_offsets = sw_shard_plan(offsets, n_shards)
+        self.shards = []
+        try:
+            for s in range(n_shards):
+                idx = self.members[self.member_offsets[s]:self.member_offsets[s + 1]]
+                lens = offsets[idx + 1] - offsets[idx]
+                off = np.zeros(len(idx) + 1, dtype=np.int64)
+                np.cumsum(lens, out=off[1:])
+                res = (np.concatenate([residues[offsets[i]:offsets[i + 1]] for i in idx]) if len(idx)
+                       else np.zeros(0, np.uint8))
+                self.shards.append(Database(res, off, alphabet_size, device=devices[s % len(devices)]))
+        except Exception:
+            self.close()
+            raise
+
+    def shard_members(self, s: int) -> np.ndarray:
+        return self.members[self.member_offsets[s]:self.member_offsets[s + 1]]
+
+    def search(self, queries, q_offsets, matrix, gap_open: int, gap_extend: int, top_k: int = 10,
+               want_scores: bool = True, **kw):
+        """Returns (scores [n_q, n_seqs] int32 or None, hits [n_q, top_k] HIT_DTYPE)."""
+        nq = len(q_offsets) - 1
+        scores = np.empty((nq, self.n_seqs), dtype=np.int32) if want_scores else None
+        shard_hits = np.empty((len(self.shards), nq, max(top_k, 0)), dtype=HIT_DTYPE)
+        for s, d in enumerate(self.shards):
+            sc, h, _ = d.search(queries, q_offsets, matrix, gap_open, gap_extend, top_k=top_k,
+                                want_scores=want_scores, **kw)
+            if top_k > 0:
+                shard_hits[s] = h
+            if want_scores:
+                sw_scores_scatter(sc, self.shard_members(s), scores)
+        hits = sw_hits_merge(shard_hits, self.members, self.member_offsets, top_k) if top_k > 0 else None
+        return scores, hits
+
+    def close(self):
+        for d in getattr(self, "shards", []):
+            d.close()
+        self.shards = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Database:

@@ -220,9 +220,11 @@ WORKLOADS = {
 }
 
 
-def make_workload(name: str, seed: int = SEED, db_scale: float = 1.0) -> Workload:
+def make_workload(name: str, seed: int = SEED, db_scale: float = 1.0, db: SeqSet | None = None) -> Workload:
     """Build a named workload.  db_scale < 1 shrinks the database count
-    (used to make bounded samples of a workload; the full size is 1.0)."""
+    (used to make bounded samples of a workload; the full size is 1.0).
+    For batched_512q, db may pass the already generated database of
+    swissprot_like_20q (same seed and scale) instead of generating it again."""
     mat = blosum62()
     if name == "db2k_q100":
         rng = np.random.default_rng(seed + 1)
@@ -250,10 +252,10 @@ def make_workload(name: str, seed: int = SEED, db_scale: float = 1.0) -> Workloa
         q = seqset_from_lengths(rng, [5000, 10000, 20000, 35000])
         return Workload(name, q, db, mat, 10, 1, 10)
     if name == "batched_512q":
-        base = make_workload("swissprot_like_20q", seed, db_scale)
+        base_db = db if db is not None else make_workload("swissprot_like_20q", seed, db_scale).db
         rng = np.random.default_rng(seed + 4)
         q = seqset_from_lengths(rng, rng.integers(50, 5001, 512))
-        return Workload(name, q, base.db, mat, 10, 1, 10)
+        return Workload(name, q, base_db, mat, 10, 1, 10)
     raise KeyError(name)
 
 

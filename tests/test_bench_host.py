@@ -71,3 +71,44 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"] == "swissprot_like_20q"
+
+
+def test_sub_records_only_for_the_default_single_gpu_line():
+    b = _bench()
+    one = b.Dist(init=False)
+    assert b.sub_record_names(b.parse_args([]), one) == ["db2k_q100", "long_4q_50k", "batched_512q"]
+    assert b.sub_record_names(b.parse_args(["--sub-records", "none"]), one) == []
+    assert b.sub_record_names(b.parse_args(["--mode", "batched"]), one) == []
+    assert b.sub_record_names(b.parse_args(["--db-scale", "0.5"]), one) == []
+    assert b.sub_record_names(b.parse_args(["--sub-records", "long_4q_50k"]), one) == ["long_4q_50k"]
+    two = b.Dist(init=False)
+    two.world = 2
+    assert b.sub_record_names(b.parse_args([]), two) == []
+    with pytest.raises(SystemExit):
+        b.sub_record_names(b.parse_args(["--sub-records", "nope"]), one)
+
+
+def test_oracle_sample_flags_a_wrong_score():
+    """The sub-records' oracle check: exact scores and hits pass, one changed
+    score fails (CPU tensors stand in for the device buffers)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+    b = _bench()
+    w = synth.make_workload("db2k_q100", db_scale=0.05)
+    want = oracle.all_scores(w.queries, w.db, w.matrix, w.gap_open, w.gap_extend)
+    hits = np.zeros((w.queries.n, w.top_k, 2), np.int64)
+    for q in range(w.queries.n):
+        s_, i_ = oracle.top_k(want[q], w.top_k)
+        hits[q, :, 0] = s_ & 0xffffffff
+        hits[q, :, 1] = i_
+    scores = torch.from_numpy(want.astype(np.int32))
+    rec = b.oracle_sample(w, scores, torch.from_numpy(hits), 1, max_cells=1e12)
+    assert rec["bit_exact_vs_gpu"] and rec["what"] == "every pair" and rec["pairs"] == w.db.n
+    scores[0, 3] += 1
+    assert not b.oracle_sample(w, scores, torch.from_numpy(hits), 1, max_cells=1e12)["bit_exact_vs_gpu"]
+    # a bounded sample of a larger workload: each query's best hit plus random pairs
+    rec = b.oracle_sample(w, torch.from_numpy(want.astype(np.int32)), torch.from_numpy(hits), 1, max_cells=1e6)
+    assert rec["bit_exact_vs_gpu"] and rec["what"].startswith("each query's best hit")

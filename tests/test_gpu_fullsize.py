@@ -93,6 +93,52 @@ def test_long_queries_full_size(gpu):
     np.testing.assert_array_equal(s[qi, ti].astype(np.int64), want)
 
 
+def test_db2k_q100_in_full(gpu):
+    """The small plain workload (1 x 100 vs 2,000 sequences) in full: every
+    score and the top-10 equal the oracle's, in the bench's configuration."""
+    w = synth.make_workload("db2k_q100")
+    with gpu.Database(w.db.residues, w.db.offsets, len(synth.ALPHABET)) as d:
+        s, h, _ = d.search(w.queries.residues, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend,
+                           top_k=w.top_k, stats=True)
+    want = oracle.all_scores(w.queries, w.db, w.matrix, w.gap_open, w.gap_extend)
+    np.testing.assert_array_equal(s.astype(np.int64), want)
+    ws, wi = oracle.top_k(want[0], w.top_k)
+    np.testing.assert_array_equal(h[0]["score"], ws)
+    np.testing.assert_array_equal(h[0]["db_index"], wi)
+
+
+def test_batched_512_queries_full_size(gpu):
+    """512 queries (50..5,000) against the full 565,000-sequence database in
+    the batched form, checked against the oracle on a stratified sample:
+    every top-k hit, every rescored pair, 100 pairs among the 100 longest
+    targets and 10,000 random pairs; the hits are the best entries of the
+    returned score table."""
+    w = synth.make_workload("batched_512q")
+    rng = np.random.default_rng(73)
+    with gpu.Database(w.db.residues, w.db.offsets, len(synth.ALPHABET)) as d:
+        s, h, st = d.search(w.queries.residues, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend,
+                            top_k=w.top_k, mode=gpu.SW_MODE_BATCHED, stats=True)
+    assert st["mode_used"] == gpu.SW_MODE_BATCHED and st["long_sequences"] > 0
+    assert (s >= 0).all()
+    for q in range(w.queries.n):
+        _hits_consistent(s[q], h[q], w.top_k)
+    qi = [np.repeat(np.arange(w.queries.n), w.top_k)]
+    ti = [h["db_index"].reshape(-1)]
+    sat = np.argwhere(s >= 32767 - int(w.matrix.max()))          # pairs the int32 rescore produced
+    qi.append(sat[:, 0])
+    ti.append(sat[:, 1])
+    longest = np.argsort(w.db.lengths)[::-1][:100]
+    qi.append(rng.integers(0, w.queries.n, 100))
+    ti.append(longest)
+    qi.append(rng.integers(0, w.queries.n, 10_000))
+    ti.append(rng.integers(0, w.db.n, 10_000))
+    qi = np.concatenate(qi).astype(np.int64)
+    ti = np.concatenate(ti).astype(np.int64)
+    assert st["rescored"] == len(sat)
+    want = oracle.score_pairs(w.queries, w.db, qi, ti, w.matrix, w.gap_open, w.gap_extend)
+    np.testing.assert_array_equal(s[qi, ti].astype(np.int64), want)
+
+
 def test_batched_512_queries_sampled(gpu):
     w = synth.make_workload("batched_512q", db_scale=0.1)
     rng = np.random.default_rng(72)
