@@ -15,9 +15,13 @@ experiment (Section 4.1) with seeded synthetic residues.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun each rank scores its own batch of queries (a distinct seed)
-against its own copy of the database: independent problems, no collective on
-the data path ("weak" scaling); rank 0 prints one JSON line.
+Under torchrun (N > 1) the database is sharded: every rank loads one
+residue-balanced, length-stratified shard (sw_shard_plan) on its own GPU and
+scores the whole query batch against it; the one exchange step all-gathers
+each shard's top-k and merges them (sw_hits_merge).  The total work is fixed
+("strong" scaling); rank 0 prints one JSON line.  --multi replicas instead
+gives every rank its own query batch against a full copy of the database
+(independent problems, "weak" scaling).
 """
 from __future__ import annotations
 
@@ -72,6 +76,9 @@ def parse_args(argv=None):
     p.add_argument("--mode", choices=["plain", "batched"], default="plain",
                    help="plain: one inter-task launch per query (the paper's form); "
                         "batched: all queries in one persistent launch")
+    p.add_argument("--autotune", choices=["auto", "on", "off"], default="auto",
+                   help="measure the launch tuning (shape rate tables, cutoff, form) on this GPU and database "
+                        "before timing: auto = for the batched form and the serving loop")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--serve", action="store_true",
                    help="serving benchmark: Poisson request stream against a resident database "
@@ -95,6 +102,9 @@ def parse_args(argv=None):
                         "plain forms), 'none', or 'auto' (all of them on one GPU for the default workload)")
     p.add_argument("--sub-steps", type=int, default=0, help="timed steps of every sub-record (0 = per workload)")
     p.add_argument("--sub-warmup", type=int, default=-1, help="warm-up steps of every sub-record (-1 = per workload)")
+    p.add_argument("--multi", choices=["shard", "replicas"], default="shard",
+                   help="with N > 1 ranks: shard the database (strong scaling, the default) or run "
+                        "independent replicas with their own queries (weak scaling)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-cells", type=float, default=6e10,
                    help="cells of the oracle's bounded sample (about 10-20 s on 16 cores)")
@@ -105,19 +115,33 @@ def parse_args(argv=None):
 # distributed helpers (torchrun); single-process runs skip them
 
 class Dist:
+    """Rank, world and device of this process.  Each local rank takes GPU
+    local_rank (modulo the GPUs visible, so more ranks than GPUs share them
+    round-robin); the process group is NCCL when every local rank has a GPU
+    of its own, else gloo."""
+
     def __init__(self, backend: str | None = None, init: bool = True):
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.rank = int(os.environ.get("RANK", "0"))
         self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.local_world = int(os.environ.get("LOCAL_WORLD_SIZE", str(self.world)))
         self.pg = None
+        self.backend = None
+        self.device = self.local_rank
+        try:
+            import torch
+            n_dev = torch.cuda.device_count() if torch.cuda.is_available() else 0
+        except Exception:
+            n_dev = 0
+        if n_dev > 0:
+            self.device = self.local_rank % n_dev
         if self.world > 1 and init:
             import torch.distributed as dist
             if backend is None:
-                import torch
-                backend = "nccl" if torch.cuda.is_available() else "gloo"
+                backend = "nccl" if n_dev >= self.local_world else "gloo"
             if backend == "nccl":
                 import torch
-                torch.cuda.set_device(self.local_rank)
+                torch.cuda.set_device(self.device)
             dist.init_process_group(backend=backend)
             self.pg = dist
             self.backend = backend
@@ -305,7 +329,7 @@ def run_ours(args, dist: Dist):
     import torch
     import paper_2203_11100_gb300 as swdb
 
-    dev = dist.local_rank
+    dev = dist.device
     torch.cuda.set_device(dev)
     swdb.load_library()
     seed = synth.SEED + 7919 * dist.rank
@@ -328,6 +352,11 @@ def run_ours(args, dist: Dist):
               long_cutoff=args.long_cutoff,
               mode=swdb.SW_MODE_BATCHED if args.mode == "batched" else swdb.SW_MODE_PLAIN,
               alignment=ALIGNMENTS[args.alignment])
+    tuned = None
+    if want_autotune(args, args.mode == "batched") and args.alignment == "local":
+        tuned = tune(db, w, forms=(args.mode,))
+        if not args.long_cutoff:
+            kw["long_cutoff"] = tuned["params"]["long_cutoff"]
 
     def step(stats=True):
         return swdb.sw_search(db.handle, q_dev, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend, w.top_k,
@@ -420,7 +449,8 @@ def run_ours(args, dist: Dist):
                              f"{db.info()['device_bytes'] / 1e6:.0f} MB > 129 MB), no flush",
                        "parallelism": f"{dist.world} independent GPU(s)",
                        "cuda_graph": "captured once, replayed every step (roofline achieved = whole step)"
-                                     if args.graph else "no"},
+                                     if args.graph else "no",
+                       "autotune": tuned if tuned else "off (the library's measured shape tables)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
                          "frac": achieved / peak if peak else None,
                          "traffic": traffic,
@@ -460,6 +490,26 @@ SUB_DEFAULTS = {            # (warm-up, timed steps) per workload
     "long_4q_50k": (3, 5),
     "batched_512q": (1, 3),     # 38-45 s per step: one warm-up step allocates and settles
 }
+
+
+def want_autotune(args, default: bool) -> bool:
+    return args.autotune == "on" or (args.autotune == "auto" and default)
+
+
+def tune(db, w, forms=("plain", "batched"), sample_queries: int = 8, cutoffs=(2048, 3072, 6144)) -> dict:
+    """Run the autotuner for this database and batch (outside any timed
+    region) and summarise what it chose and measured."""
+    from paper_2203_11100_gb300 import autotune
+    params = autotune.autotune(db, w.queries.residues, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend,
+                               top_k=w.top_k, sample_queries=sample_queries, cutoffs=cutoffs, repeats=2,
+                               forms=forms, force=True, cache_path=None)
+    r = autotune.last_result()
+    fmt = lambda rows: [{"lanes": l, "rows": rr, "gcups": round(g, 1)} for l, rr, g in rows]
+    return {"params": params, "plain_shapes": fmt(r["tuning"]["plain"]), "batched_shapes": fmt(r["tuning"]["batched"]),
+            "tried": r["tried"], "tune_seconds": r["tune_seconds"],
+            "how": "shape rates: median CUDA-event kernel rate of a 3,072-residue query cut from the batch "
+                   f"(pairs of them for the batched kernel); cutoff and form: median whole-search time of "
+                   f"{sample_queries} queries spread over the batch's lengths"}
 
 
 def sub_record_names(args, dist) -> list:
@@ -569,10 +619,13 @@ def run_sub_records(args, names, db_main, w_main, rate_dpx: float, sms: int, dev
             warm = args.sub_warmup
         if args.sub_steps > 0:
             steps = args.sub_steps
+        tuned = None
         if name == "batched_512q":
             w = synth.make_workload(name, seed=synth.SEED, db=w_main.db)
             db, own = db_main, False
             forms = [("batched", swdb.SW_MODE_BATCHED), ("plain", swdb.SW_MODE_PLAIN)]
+            if want_autotune(args, True):
+                tuned = tune(db, w)      # both forms use the measured tables and the chosen cutoff
         else:
             w = synth.make_workload(name, seed=synth.SEED)
             db, own = swdb.Database(w.db.residues, w.db.offsets, len(synth.ALPHABET), device=dev), True
@@ -582,6 +635,8 @@ def run_sub_records(args, names, db_main, w_main, rate_dpx: float, sms: int, dev
         hits = torch.empty((w.queries.n, w.top_k, 2), dtype=torch.int64, device=f"cuda:{dev}")
         for form, mode in forms:
             kw = dict(mode=mode)
+            if tuned:
+                kw["long_cutoff"] = tuned["params"]["long_cutoff"]
 
             def step():
                 return swdb.sw_search(db.handle, q_dev, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend,
@@ -611,7 +666,8 @@ def run_sub_records(args, names, db_main, w_main, rate_dpx: float, sms: int, dev
                                           for k in ("inter", "rescore", "intra", "other")},
                    "long_sequences": st_all[0]["long_sequences"],
                    "rescored_per_step": sum(s["rescored"] for s in st_all) / steps,
-                   "launch": {k: v for k, v in kw.items() if k != "mode"} or "library choice per query"}
+                   "launch": {k: v for k, v in kw.items() if k != "mode"} or "library choice per query",
+                   "autotune": tuned if tuned else "off (the library's measured shape tables)"}
             if not args.no_cpu_baseline:
                 rec["oracle_sample"] = oracle_sample(w, scores, hits, synth.SEED + 31 + len(out),
                                                      max_cells=4e10 if name == "batched_512q" else 1e10)
@@ -619,6 +675,127 @@ def run_sub_records(args, names, db_main, w_main, rate_dpx: float, sms: int, dev
         del scores, hits, q_dev
         if own:
             db.close()
+        elif tuned:
+            swdb.sw_db_set_tuning(db.handle, None)
+    return out
+
+
+def run_sharded(args, dist: Dist):
+    """The database sharded over the ranks (one shard per GPU), every query
+    against every shard, then the top-k exchange: an all-gather of each
+    shard's n_q x top_k hits and the merge into the unsharded top-k on rank 0.
+    One step = the whole workload (all queries x the whole database): strong
+    scaling.  Rank 0 checks the merged hits' best entries against the oracle."""
+    import torch
+    import paper_2203_11100_gb300 as swdb
+    from paper_2203_11100_gb300 import multigpu
+
+    dev = dist.device
+    torch.cuda.set_device(dev)
+    swdb.load_library()
+    w = synth.make_workload(args.workload, seed=synth.SEED, db_scale=args.db_scale)
+    members, moff = swdb.sw_shard_plan(w.db.offsets, dist.world)
+    mine = members[moff[dist.rank]:moff[dist.rank + 1]]
+    lens = w.db.lengths[mine]
+    off = np.zeros(len(mine) + 1, np.int64)
+    np.cumsum(lens, out=off[1:])
+    res = np.concatenate([w.db.seq(int(i)) for i in mine]) if len(mine) else np.zeros(0, np.uint8)
+    db = swdb.Database(res, off, len(synth.ALPHABET), device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    nq = w.queries.n
+    q_dev = torch.from_numpy(w.queries.residues).to(f"cuda:{dev}")
+    scores = torch.empty((nq, max(len(mine), 1)), dtype=torch.int32, device=f"cuda:{dev}")
+    hits = torch.empty((nq, w.top_k, 2), dtype=torch.int64, device=f"cuda:{dev}")
+    kw = dict(mode=swdb.SW_MODE_BATCHED if args.mode == "batched" else swdb.SW_MODE_PLAIN)
+    merged = [None]
+
+    def step():
+        with torch.cuda.stream(stream):
+            st = swdb.sw_search(db.handle, q_dev, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend, w.top_k,
+                                scores, hits, stats=True, stream=stream.cuda_stream, **kw)
+            if dist.pg is not None:
+                local = hits if dist.backend == "nccl" else hits.cpu()
+                merged[0] = multigpu.exchange_hits(dist.pg, local, members, moff, w.top_k, dst=0)
+            else:
+                merged[0] = swdb.sw_hits_merge(multigpu.tensor_to_hits(hits)[None], members, moff, w.top_k)
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    st_all = [step() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    local_ms = ev0.elapsed_time(ev1)
+    t_ms = dist.max(local_ms)
+    cells_step = float(w.cells)
+    gcups = cells_step * args.steps / (t_ms * 1e-3) / 1e9
+    shard_cells = dist.sum(float(w.queries.lengths.sum()) * float(lens.sum()))
+
+    # end to end: queries from pinned host memory, each shard's hits back to
+    # the host, the exchange and the merge
+    q_host = torch.from_numpy(w.queries.residues).pin_memory()
+    h_host = torch.empty((nq, w.top_k, 2), dtype=torch.int64).pin_memory()
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        swdb.sw_search(db.handle, q_host, w.queries.offsets, w.matrix, w.gap_open, w.gap_extend, w.top_k, None,
+                       h_host, **kw)
+        if dist.pg is not None:
+            multigpu.exchange_hits(dist.pg, h_host.to(f"cuda:{dev}") if dist.backend == "nccl" else h_host,
+                                   members, moff, w.top_k, dst=0)
+        else:
+            swdb.sw_hits_merge(multigpu.tensor_to_hits(h_host)[None], members, moff, w.top_k)
+    torch.cuda.synchronize()
+    e2e_ms = dist.max((time.perf_counter() - t0) * 1e3)
+    out = None
+    if dist.rank == 0:
+        rate_dpx, sms = swdb.sw_probe_alu_rate(dev, 0)
+        mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+        roof = kernel_roofline(st_all, "inter", "k_inter_i16x2", DPX_OPS_PER_CELL, rate_dpx, sms, mhz,
+                               " (rank 0's shard)")
+        check = None
+        if not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            h = merged[0]
+            qi = np.arange(nq, dtype=np.int64)
+            ti = h[:, 0]["db_index"].astype(np.int64)
+            want = oracle.score_pairs(w.queries, w.db, qi, ti, w.matrix, w.gap_open, w.gap_extend)
+            check = {"pairs": int(nq), "what": "each query's merged best hit (caller's index)",
+                     "bit_exact_vs_gpu": bool(np.array_equal(want, h[:, 0]["score"].astype(np.int64)))}
+        out = {"metric": METRIC, "value": gcups, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+               "scaling": "strong", "vs_baseline": None, "dtype": "i16x2", "data": "synthetic",
+               "config": {"workload": args.workload, "queries": nq, "db_seqs": w.db.n,
+                          "db_residues": int(w.db.lengths.sum()), "cells_per_step": cells_step,
+                          "shard_residues": [int(w.db.lengths[members[moff[r]:moff[r + 1]]].sum())
+                                             for r in range(dist.world)],
+                          "matrix": "BLOSUM62", "gap_open": w.gap_open, "gap_extend": w.gap_extend,
+                          "top_k": w.top_k, "mode": args.mode,
+                          "parallelism": f"database sharded over {dist.world} GPU(s) (residue-balanced, "
+                                         "length-stratified); top-k all-gather + merge on rank 0",
+                          "l2": "inputs larger than L2, no flush" if int(lens.sum()) > 129e6 else
+                                "shard layout may fit L2; each launch streams it once per query"},
+               "roofline": roof, "clocks": clk,
+               "gpu_launches": sum(s["launches"] for s in st_all), "shard_cells_all_ranks": shard_cells,
+               "merged_hits_check": check,
+               "e2e": {"value": cells_step * args.e2e_steps / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+                       "h2d_bytes_per_step": int(w.queries.residues.nbytes) * dist.world,
+                       "d2h_bytes_per_step": int(nq * w.top_k * 16) * dist.world,
+                       "ms_per_step": e2e_ms / args.e2e_steps}}
+    db.close()
     return out
 
 
@@ -629,7 +806,7 @@ def run_serving(args, dist: Dist):
     import paper_2203_11100_gb300 as swdb
     from paper_2203_11100_gb300.serve import SearchServer
 
-    dev = dist.local_rank
+    dev = dist.device
     torch.cuda.set_device(dev)
     swdb.load_library()
     dbs = synth.serving_database(db_scale=args.serve_db_scale)
@@ -640,8 +817,17 @@ def run_serving(args, dist: Dist):
     residues = int(dbs.lengths.sum())
     clocks = ClockSampler(dev)
 
+    launch = {}
+    tuned = None
+    if want_autotune(args, True):
+        sample = synth.Workload("serving sample", synth.seqset_from_list([reqs.seq(i) for i in range(64)]), dbs, S,
+                                10, 1, 10)
+        tuned = tune(db, sample, forms=("batched",))
+        launch = {"long_cutoff": tuned["params"]["long_cutoff"]}
+
     def new_server():
-        return SearchServer(db, S, 10, 1, top_k=10, max_batch=args.serve_max_batch, streams=3, max_query_len=8000)
+        return SearchServer(db, S, 10, 1, top_k=10, max_batch=args.serve_max_batch, streams=3, max_query_len=8000,
+                            launch=launch)
 
     # warm-up: one batch through a server
     srv = new_server()
@@ -707,7 +893,7 @@ def run_serving(args, dist: Dist):
                        "db_fraction_of_20M": args.serve_db_scale, "requests_saturation": n_req,
                        "request_lengths": "lognormal mean 400, 30..8000", "matrix": "BLOSUM62",
                        "gap_open": 10, "gap_extend": 1, "top_k": 10, "max_batch": args.serve_max_batch,
-                       "streams": 3},
+                       "streams": 3, "autotune": tuned if tuned else "off"},
             "serving": {"saturation_rate_per_s": sat_rate, "saturation_p50_ms": sat["p50_ms"],
                         "saturation_p99_ms": sat["p99_ms"], "points": points,
                         "plain_one_launch_per_query_gcups": sat_cells / plain_s / 1e9},
@@ -723,7 +909,7 @@ def run_sweep(args, dist: Dist):
     import torch
     import paper_2203_11100_gb300 as swdb
 
-    dev = dist.local_rank
+    dev = dist.device
     torch.cuda.set_device(dev)
     swdb.load_library()
     w = synth.make_workload(args.workload, seed=synth.SEED, db_scale=args.db_scale)
@@ -784,7 +970,7 @@ def run_align(args, dist: Dist):
     import torch
     import paper_2203_11100_gb300 as swdb
 
-    dev = dist.local_rank
+    dev = dist.device
     torch.cuda.set_device(dev)
     swdb.load_library()
     w = synth.make_workload(args.workload, seed=synth.SEED, db_scale=args.db_scale)
@@ -965,7 +1151,10 @@ def main(argv=None):
         out = run_sweep(args, dist)
     else:
         dist = Dist()
-        out = run_ours(args, dist)
+        if dist.world > 1 and args.multi == "shard":
+            out = run_sharded(args, dist)
+        else:
+            out = run_ours(args, dist)
     if out is not None and dist.rank == 0:
         print(json.dumps(out), flush=True)
     dist.close()

@@ -197,6 +197,51 @@ typedef struct {
 
 int sw_db_get_info(const sw_db *db, sw_db_info *out);
 
+/*
+ * Launch tuning of one database handle (no counterpart in the paper, whose
+ * SW#db picks blocks and threads from fixed per-architecture tables,
+ * Section 3.2, and whose results depend on the work-group size, Section
+ * 4.2).  sw_search picks, per query, the launch shape of the inter-task
+ * kernel (plain form) or of the batched kernel (batched form: per query
+ * pair) with the least predicted time, ceil(m / (lanes*rows)) * lanes*rows
+ * / gcups, from a table of shapes and their cell rates; the library's
+ * tables hold rates measured on GB300.  An autotuner that measures the rates
+ * on the caller's own GPU and database installs its tables here, with the
+ * inter/intra-task length cutoff, the intra-task rows per lane and the form
+ * that SW_MODE_AUTO takes; sw_search options that are set explicitly still
+ * override them.  Tuning never changes scores, only launch shapes.
+ */
+typedef struct {
+    int32_t lanes;            /* lanes per subwarp: with rows_per_lane, a shape sw_search
+                                 accepts in opts for that form */
+    int32_t rows_per_lane;
+    float gcups;              /* measured cell updates per second / 1e9, > 0 */
+} sw_shape_rate;              /* 12 bytes */
+
+#define SW_TUNING_MAX_SHAPES 16
+typedef struct {
+    int32_t n_plain;          /* entries of plain[] in use (0: the library's table) */
+    int32_t n_batched;        /* entries of batched[] in use (0: the library's table) */
+    sw_shape_rate plain[SW_TUNING_MAX_SHAPES];    /* inter-task kernel, plain form */
+    sw_shape_rate batched[SW_TUNING_MAX_SHAPES];  /* batched kernel */
+    int64_t long_cutoff;      /* default of opts->long_cutoff (0: the library's, 3072) */
+    int32_t long_rows_per_lane; /* default of opts->long_rows_per_lane (0: library choice) */
+    int32_t mode;             /* what SW_MODE_AUTO means: 0 or SW_MODE_PLAIN = plain,
+                                 SW_MODE_BATCHED = batched */
+} sw_tuning;                  /* 408 bytes */
+
+/* Install a tuning on the handle (copied), or NULL to go back to the
+ * library's tables.  Do not call it while a search on the handle is in
+ * flight or being captured.  Errors: SW_ERR_INVALID_ARG (NULL handle, a
+ * count outside 0..SW_TUNING_MAX_SHAPES, a shape the form does not support,
+ * a rate that is not a positive finite number, long_rows_per_lane other
+ * than 0, 8, 16 or 32, an unknown mode). */
+int sw_db_set_tuning(sw_db *db, const sw_tuning *tuning);
+
+/* The handle's tuning, the library's tables when none is installed (with
+ * n_plain and n_batched giving their sizes). */
+int sw_db_get_tuning(const sw_db *db, sw_tuning *out);
+
 /* Device workspace (bytes) sw_search needs for these queries and options,
  * written to *bytes.  q_offsets is a host pointer (n_q+1 entries). */
 int sw_search_workspace_size(const sw_db *db, const int64_t *q_offsets, int32_t n_q,

@@ -31,7 +31,9 @@ from .binding import (  # noqa: F401
     sw_align_ops_capacity,
     sw_db_free,
     sw_db_get_info,
+    sw_db_get_tuning,
     sw_db_load,
+    sw_db_set_tuning,
     sw_hits_merge,
     sw_last_error,
     sw_probe_alu_rate,

@@ -1,25 +1,40 @@
 """Autotuner for the search's launch parameters.
 
-It picks, for one GPU, database and kind of query batch:
+The paper's SW#db takes its launch shape from fixed per-architecture tables
+(Section 3.2) and its GCUPS depend on the work-group size (Section 4.2).
+Here the library picks, per query (plain form) or per query pair (batched
+form), the launch shape -- lanes per subwarp, which sets the sequences per
+256-thread block, and query rows per lane -- with the least predicted time
+ceil(m / (lanes*rows)) * lanes*rows / rate, from a table of shapes and
+their cell rates.  This module measures that table on the caller's GPU and
+database and installs it on the handle (sw_db_set_tuning), together with:
 
 - the lane packing: sequence pairs in the int16x2 halves with one launch per
-  query (the plain form), or query pairs with one persistent launch (the
-  batched form);
-- the subwarp width (lanes), which sets the sequences per 256-thread block;
-- the query rows held per lane;
+  query (the plain form), or query pairs with one persistent launch for the
+  whole batch (the batched form) -- what SW_MODE_AUTO then means;
 - the length above which database sequences go to the intra-task kernel.
 
-Each candidate is timed on a bounded sample of the batch (queries spread
-over its length range) against the whole resident database, with the
-library's own CUDA-event kernel timings.  The winner is cached in a JSON file
-keyed by GPU name, SM count, database size and the batch's length profile, so
-the next batch of the same kind reuses it.  The launch parameters never change
-the scores; only the time does.
+Measurements use the library's own CUDA-event kernel times (the median of
+several repeats after a warm-up):
+
+- shape rates: a query of 3,072 residues taken from the batch itself (a
+  whole number of strips of every shape, so no padding enters the rate)
+  against the whole resident database, one search per candidate shape,
+  rate = the scoring kernel's cells / its event time;
+- cutoff and form: the whole search of a sample of the batch (queries spread
+  over its length range), bracketed by CUDA events on its stream.
+
+The result is cached in a JSON file keyed by GPU, database, substitution
+matrix, penalties, the arithmetic the library chose, library version and the
+batch's length profile, so the next batch of the same kind reuses it.  The
+launch parameters never change the scores; only the time does.
 """
 from __future__ import annotations
 
+import hashlib
 import json
 import os
+import statistics
 import time
 
 import numpy as np
@@ -28,12 +43,10 @@ from . import binding
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "swdb", "autotune.json")
 
-CANDIDATES = (
-    [{"mode": binding.SW_MODE_PLAIN, "lanes": 0, "rows_per_lane": 0}]
-    + [{"mode": binding.SW_MODE_BATCHED, "lanes": l, "rows_per_lane": r} for l, r in
-       [(8, 16), (8, 24), (8, 32), (16, 24), (16, 32)]]
-)
-CUTOFFS = (2048, 3072, 6144)
+PLAIN_SHAPES = ((8, 16), (16, 16), (32, 16), (8, 24), (8, 32), (16, 32), (32, 32))
+BATCH_SHAPES = ((8, 16), (8, 24), (8, 32), (16, 16), (16, 24), (16, 32))
+CUTOFFS = (2048, 3072, 6144, 12288)
+RATE_ROWS = 3072          # a whole number of strips of every candidate shape
 
 
 def _device_key(device: int) -> str:
@@ -49,6 +62,11 @@ def _batch_key(db_info: dict, lengths: np.ndarray) -> str:
             f"|nq{nq_bucket}|len{q[0]}-{q[1]}-{q[2]}")
 
 
+def _search_key(matrix, gap_open: int, gap_extend: int, precision: int) -> str:
+    h = hashlib.sha256(np.ascontiguousarray(matrix, dtype=np.int32).tobytes()).hexdigest()[:16]
+    return f"S{h}|o{int(gap_open)}e{int(gap_extend)}|prec{int(precision)}|{binding.sw_version()}"
+
+
 def _sample(queries, offsets, k: int):
     """Up to k queries spread over the length range (by length rank)."""
     lens = np.diff(offsets)
@@ -61,15 +79,80 @@ def _sample(queries, offsets, k: int):
     return res, off
 
 
+def _probe_queries(queries, n: int, rows: int = RATE_ROWS):
+    """n queries of `rows` residues cut from the batch's own residues (tiled
+    when the batch is shorter)."""
+    src = np.ascontiguousarray(queries, dtype=np.uint8)
+    if len(src) == 0:
+        src = np.zeros(1, np.uint8)
+    reps = -(-(n * rows) // len(src))
+    res = np.tile(src, reps)[:n * rows].copy()
+    return res, np.arange(n + 1, dtype=np.int64) * rows
+
+
+def _median_rate(db, q_res, q_off, matrix, o, e, stream, repeats: int, **kw) -> float:
+    """Median over repeats of the scoring kernel's own cell rate (GCUPS) in
+    one search, after a warm-up search."""
+    import torch
+    q_dev = torch.from_numpy(q_res).cuda(db.device)
+    call = lambda: binding.sw_search(db.handle, q_dev, q_off, matrix, o, e, 0, None, None, stats=True,
+                                     stream=stream.cuda_stream, **kw)
+    call()
+    rates = []
+    for _ in range(repeats):
+        st = call()
+        if st["inter_ms"] <= 0 or st["inter_cells"] <= 0:
+            continue
+        rates.append(st["inter_cells"] / (st["inter_ms"] * 1e-3) / 1e9)
+    return statistics.median(rates) if rates else 0.0
+
+
+def _median_search_ms(db, q_res, q_off, matrix, o, e, top_k, stream, repeats: int, **kw) -> float:
+    """Median over repeats of a whole search's time (CUDA events on its stream)."""
+    import torch
+    q_dev = torch.from_numpy(q_res).cuda(db.device)
+    n = db.n_seqs
+    scores = torch.empty((len(q_off) - 1, max(n, 1)), dtype=torch.int32, device=q_dev.device)
+    hits = torch.empty((len(q_off) - 1, max(top_k, 1), 2), dtype=torch.int64, device=q_dev.device)
+
+    def call():
+        binding.sw_search(db.handle, q_dev, q_off, matrix, o, e, top_k, scores, hits if top_k else None,
+                          stream=stream.cuda_stream, **kw)
+
+    call()
+    times = []
+    for _ in range(repeats):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        call()
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    return statistics.median(times)
+
+
 def autotune(db, queries, q_offsets, matrix, gap_open: int, gap_extend: int, top_k: int = 10,
              sample_queries: int = 16, cache_path: str | None = DEFAULT_CACHE, force: bool = False,
-             candidates=CANDIDATES, cutoffs=CUTOFFS) -> dict:
-    """Return the fastest launch parameters (keyword arguments of sw_search)
-    for this kind of batch, measuring them if the cache has no entry."""
+             repeats: int = 3, plain_shapes=PLAIN_SHAPES, batch_shapes=BATCH_SHAPES, cutoffs=CUTOFFS,
+             forms=("plain", "batched")) -> dict:
+    """Measure (or take from the cache) this batch kind's launch tuning,
+    install it on db's handle, and return the sw_search keyword arguments
+    it implies ({"mode": ..., "long_cutoff": ...}).  The handle keeps the
+    tuning (shape tables, cutoff, and the form SW_MODE_AUTO takes) until it
+    is replaced; see sw_db_set_tuning.  last_result() returns the measured
+    tables and the candidates tried."""
+    import torch
     queries = np.ascontiguousarray(queries, dtype=np.uint8)
     q_offsets = np.ascontiguousarray(q_offsets, dtype=np.int64)
     info = db.info()
-    key = _device_key(db.device) + "|" + _batch_key(info, np.diff(q_offsets))
+    stream = torch.cuda.Stream(device=db.device)
+    # which arithmetic the library takes for this matrix and these penalties
+    probe_res, probe_off = _probe_queries(queries, 1, rows=64)
+    prec = binding.sw_search(db.handle, probe_res, probe_off, matrix, gap_open, gap_extend, 0, None, None,
+                             stats=True)["precision_used"]
+    key = "|".join([_device_key(db.device), _batch_key(info, np.diff(q_offsets)),
+                    _search_key(matrix, gap_open, gap_extend, prec), ",".join(forms)])
     cache = {}
     if cache_path and os.path.exists(cache_path):
         try:
@@ -77,30 +160,62 @@ def autotune(db, queries, q_offsets, matrix, gap_open: int, gap_extend: int, top
         except Exception:
             cache = {}
     if not force and key in cache:
-        return dict(cache[key]["params"])
+        entry = cache[key]
+        binding.sw_db_set_tuning(db.handle, entry["tuning"])
+        _LAST.clear()
+        _LAST.update(entry, cached=True)
+        return dict(entry["params"])
 
-    s_res, s_off = _sample(queries, q_offsets, sample_queries)
-    cells = int(np.diff(s_off).sum()) * info["residues"]
-    results = []
-    for cand in candidates:
-        for cut in cutoffs:
-            params = dict(cand, long_cutoff=cut)
+    t_start = time.perf_counter()
+    binding.sw_db_set_tuning(db.handle, None)
+    tuning = {"plain": [], "batched": [], "long_cutoff": 0, "long_rows_per_lane": 0, "mode": 0}
+    if prec == binding.SW_PREC_I16:
+        one_res, one_off = _probe_queries(queries, 1)
+        for (l, r) in plain_shapes:
             try:
-                binding.sw_search(db.handle, s_res, s_off, matrix, gap_open, gap_extend, top_k, None, None,
-                                  stats=True, **params)                 # warm-up (and plan validation)
-                t0 = time.perf_counter()
-                st = binding.sw_search(db.handle, s_res, s_off, matrix, gap_open, gap_extend, top_k, None, None,
-                                       stats=True, **params)
-                dt = time.perf_counter() - t0
+                g = _median_rate(db, one_res, one_off, matrix, gap_open, gap_extend, stream, repeats,
+                                 mode=binding.SW_MODE_PLAIN, lanes=l, rows_per_lane=r)
             except binding.SwError:
                 continue
-            results.append((dt, params, st))
-    if not results:
+            if g > 0:
+                tuning["plain"].append((l, r, g))
+        if "batched" in forms:
+            two_res, two_off = _probe_queries(queries, 2)
+            for (l, r) in batch_shapes:
+                try:
+                    g = _median_rate(db, two_res, two_off, matrix, gap_open, gap_extend, stream, repeats,
+                                     mode=binding.SW_MODE_BATCHED, lanes=l, rows_per_lane=r)
+                except binding.SwError:
+                    continue
+                if g > 0:
+                    tuning["batched"].append((l, r, g))
+    binding.sw_db_set_tuning(db.handle, tuning)
+
+    # the cutoff and the form, on a sample of the batch with the measured tables
+    s_res, s_off = _sample(queries, q_offsets, sample_queries)
+    tried = []
+    mode_of = {"plain": binding.SW_MODE_PLAIN, "batched": binding.SW_MODE_BATCHED}
+    for form in forms:
+        if form == "batched" and prec != binding.SW_PREC_I16:
+            continue
+        for cut in cutoffs:
+            try:
+                ms = _median_search_ms(db, s_res, s_off, matrix, gap_open, gap_extend, top_k, stream, repeats,
+                                       mode=mode_of[form], long_cutoff=cut)
+            except binding.SwError:
+                continue
+            tried.append({"form": form, "long_cutoff": cut, "ms": ms})
+    if not tried:
         raise RuntimeError("no candidate launch configuration ran")
-    results.sort(key=lambda r: r[0])
-    best_dt, best, _ = results[0]
-    entry = {"params": best, "gcups": cells / best_dt / 1e9, "sample_cells": cells,
-             "tried": [{"params": p, "gcups": cells / d / 1e9} for d, p, _ in results]}
+    best = min(tried, key=lambda x: x["ms"])
+    tuning["long_cutoff"] = best["long_cutoff"]
+    tuning["mode"] = mode_of[best["form"]]
+    binding.sw_db_set_tuning(db.handle, tuning)
+    cells = int(np.diff(s_off).sum()) * info["residues"]
+    params = {"mode": tuning["mode"], "long_cutoff": tuning["long_cutoff"]}
+    entry = {"params": params, "tuning": tuning, "sample_cells": cells,
+             "sample_gcups": cells / (best["ms"] * 1e-3) / 1e9 if best["ms"] > 0 else 0.0,
+             "tried": tried, "tune_seconds": time.perf_counter() - t_start}
     if cache_path:
         os.makedirs(os.path.dirname(cache_path), exist_ok=True)
         cache[key] = entry
@@ -108,4 +223,15 @@ def autotune(db, queries, q_offsets, matrix, gap_open: int, gap_extend: int, top
         with open(tmp, "w") as f:
             json.dump(cache, f, indent=1)
         os.replace(tmp, cache_path)
-    return dict(best)
+    _LAST.clear()
+    _LAST.update(entry, cached=False)
+    return dict(params)
+
+
+_LAST: dict = {}
+
+
+def last_result() -> dict:
+    """The measured (or cached) entry of the last autotune() call: params,
+    tuning tables, sample GCUPS, the candidates tried and the time spent."""
+    return dict(_LAST)

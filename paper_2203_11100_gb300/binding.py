@@ -60,6 +60,19 @@ class SwAlignStats(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class SwShapeRate(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int32), ("rows_per_lane", ctypes.c_int32), ("gcups", ctypes.c_float)]
+
+
+SW_TUNING_MAX_SHAPES = 16
+
+
+class SwTuning(ctypes.Structure):
+    _fields_ = [("n_plain", ctypes.c_int32), ("n_batched", ctypes.c_int32),
+                ("plain", SwShapeRate * SW_TUNING_MAX_SHAPES), ("batched", SwShapeRate * SW_TUNING_MAX_SHAPES),
+                ("long_cutoff", ctypes.c_int64), ("long_rows_per_lane", ctypes.c_int32), ("mode", ctypes.c_int32)]
+
+
 class SwDbInfo(ctypes.Structure):
     _fields_ = [("n_seqs", ctypes.c_int64), ("residues", ctypes.c_int64), ("max_length", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("alphabet_size", ctypes.c_int32), ("device", ctypes.c_int32)]
@@ -99,11 +112,13 @@ def load_library():
     lib.sw_align_mode.argtypes = [vp, vp, vp, i32, vp, vp, i64, vp, i32, i32, i32, vp, vp, i64,
                                   ctypes.POINTER(SwAlignStats), vp]
     lib.sw_align_mode.restype = ctypes.c_int
+    lib.sw_db_set_tuning.argtypes = [vp, ctypes.POINTER(SwTuning)]
+    lib.sw_db_get_tuning.argtypes = [vp, ctypes.POINTER(SwTuning)]
     lib.sw_shard_plan.argtypes = [vp, i64, i32, vp, vp]
     lib.sw_hits_merge.argtypes = [vp, vp, vp, i32, i32, i32, vp]
     lib.sw_scores_scatter.argtypes = [vp, vp, i64, i32, i64, vp]
     for name in ("sw_align", "sw_align_ops_capacity", "sw_probe_wait_timeout", "sw_shard_plan", "sw_hits_merge",
-                 "sw_scores_scatter"):
+                 "sw_scores_scatter", "sw_db_set_tuning", "sw_db_get_tuning"):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("sw_db_load", "sw_db_free", "sw_db_get_info", "sw_search_workspace_size", "sw_search",
                  "sw_top_k", "sw_probe_alu_rate", "sw_search_no_alloc"):
@@ -176,6 +191,37 @@ def sw_db_get_info(handle) -> dict:
     info = SwDbInfo()
     _check(load_library().sw_db_get_info(handle, ctypes.byref(info)))
     return {f: getattr(info, f) for f, _ in SwDbInfo._fields_}
+
+
+def sw_db_set_tuning(handle, tuning: dict | None) -> None:
+    """Install a launch tuning on a handle, or None for the library's tables.
+    tuning: {"plain": [(lanes, rows, gcups), ...], "batched": [...],
+    "long_cutoff": int, "long_rows_per_lane": int, "mode": int} (keys optional)."""
+    if tuning is None:
+        _check(load_library().sw_db_set_tuning(handle, None))
+        return
+    t = SwTuning()
+    for key, arr, count in (("plain", t.plain, "n_plain"), ("batched", t.batched, "n_batched")):
+        rows = list(tuning.get(key, []))
+        if len(rows) > SW_TUNING_MAX_SHAPES:
+            raise ValueError(f"at most {SW_TUNING_MAX_SHAPES} {key} shapes")
+        for i, (l, r, g) in enumerate(rows):
+            arr[i].lanes, arr[i].rows_per_lane, arr[i].gcups = int(l), int(r), float(g)
+        setattr(t, count, len(rows))
+    t.long_cutoff = int(tuning.get("long_cutoff", 0))
+    t.long_rows_per_lane = int(tuning.get("long_rows_per_lane", 0))
+    t.mode = int(tuning.get("mode", 0))
+    _check(load_library().sw_db_set_tuning(handle, ctypes.byref(t)))
+
+
+def sw_db_get_tuning(handle) -> dict:
+    """The handle's active tuning (the library's tables when none is installed)."""
+    t = SwTuning()
+    _check(load_library().sw_db_get_tuning(handle, ctypes.byref(t)))
+    return {"plain": [(t.plain[i].lanes, t.plain[i].rows_per_lane, float(t.plain[i].gcups)) for i in range(t.n_plain)],
+            "batched": [(t.batched[i].lanes, t.batched[i].rows_per_lane, float(t.batched[i].gcups))
+                        for i in range(t.n_batched)],
+            "long_cutoff": int(t.long_cutoff), "long_rows_per_lane": int(t.long_rows_per_lane), "mode": int(t.mode)}
 
 
 def _opts(precision, mode, long_cutoff, lanes, rows_per_lane, workspace, flags=0, long_rows_per_lane=0,

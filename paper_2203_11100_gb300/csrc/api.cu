@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <chrono>
+#include <iterator>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -74,6 +75,8 @@ struct sw_db {
     cudaGraphExec_t graph_exec = nullptr;   // last captured search (SW_FLAG_GRAPH)
     std::string graph_key;
     std::mutex mu;
+    sw_tuning tuning{};                     // installed by sw_db_set_tuning (counts 0: library tables)
+    int64_t tuning_version = 0;             // bumped by every sw_db_set_tuning
 
     DbView view() const {
         DbView v;
@@ -164,9 +167,22 @@ struct ShapeRate {
 };
 constexpr ShapeRate kShapes[] = {{8, 16, 5000.0}, {16, 16, 5300.0}, {8, 24, 5680.0}, {8, 32, 5900.0}, {16, 32, 5700.0}};
 
-void choose_shape(int64_t m, int *lanes, int *rows) {
+using ShapeTable = std::vector<ShapeRate>;
+
+// The handle's active tables: its tuning's when installed, else the library's.
+ShapeTable plain_shapes(const sw_db *db) {
+    if (db->tuning.n_plain > 0) {
+        ShapeTable t;
+        for (int i = 0; i < db->tuning.n_plain; ++i)
+            t.push_back({db->tuning.plain[i].lanes, db->tuning.plain[i].rows_per_lane, double(db->tuning.plain[i].gcups)});
+        return t;
+    }
+    return ShapeTable(std::begin(kShapes), std::end(kShapes));
+}
+
+void choose_shape(const ShapeTable &table, int64_t m, int *lanes, int *rows) {
     double best = 1e300;
-    for (const ShapeRate &c : kShapes) {
+    for (const ShapeRate &c : table) {
         const int64_t tr = int64_t(c.lanes) * c.rows;
         const double t = double((m + tr - 1) / tr * tr) / c.gcups;
         if (t < best) {
@@ -206,12 +222,23 @@ constexpr int32_t kMode16Cols = 4096;
 
 constexpr ShapeRate kBatchShapes[] = {{8, 16, 5000.0}, {8, 24, 5850.0}, {8, 32, 5850.0}};
 
-int choose_batch_shape(int64_t m) {
+ShapeTable batch_shapes(const sw_db *db) {
+    if (db->tuning.n_batched > 0) {
+        ShapeTable t;
+        for (int i = 0; i < db->tuning.n_batched; ++i)
+            t.push_back({db->tuning.batched[i].lanes, db->tuning.batched[i].rows_per_lane,
+                         double(db->tuning.batched[i].gcups)});
+        return t;
+    }
+    return ShapeTable(std::begin(kBatchShapes), std::end(kBatchShapes));
+}
+
+int choose_batch_shape(const ShapeTable &table, int64_t m) {
     double best = 1e300;
     int arg = 0;
-    for (int i = 0; i < int(sizeof(kBatchShapes) / sizeof(kBatchShapes[0])); ++i) {
-        const int64_t tr = int64_t(kBatchShapes[i].lanes) * kBatchShapes[i].rows;
-        const double t = double((m + tr - 1) / tr * tr) / kBatchShapes[i].gcups;
+    for (int i = 0; i < int(table.size()); ++i) {
+        const int64_t tr = int64_t(table[size_t(i)].lanes) * table[size_t(i)].rows;
+        const double t = double((m + tr - 1) / tr * tr) / table[size_t(i)].gcups;
         if (t < best) {
             best = t;
             arg = i;
@@ -221,6 +248,7 @@ int choose_batch_shape(int64_t m) {
 }
 
 struct Plan {
+    ShapeTable plain_table, batch_table;   // the handle's active rate tables
     int precision = SW_PREC_I16;
     int mode = SW_MODE_PLAIN;
     bool auto_shape = true;          // int16x2 kernel: shape chosen per query ...
@@ -284,6 +312,8 @@ int64_t mode16_first_pair(const sw_db *db, const Plan &p, int32_t m, int tr, int
 int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int32_t *matrix,
               int32_t o, int32_t e, const sw_search_opts *opts, Plan *plan) {
     Plan p;
+    p.plain_table = plain_shapes(db);
+    p.batch_table = batch_shapes(db);
     for (int32_t i = 0; i < n_q; ++i) {
         const int64_t m = q_offsets[i + 1] - q_offsets[i];
         if (m < 0) return fail(SW_ERR_INVALID_ARG, "q_offsets must be non-decreasing");
@@ -397,7 +427,9 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
     const int mode = opts ? opts->mode : SW_MODE_AUTO;
     if (mode < 0 || mode > SW_MODE_BATCHED) return fail(SW_ERR_INVALID_ARG, "unknown mode");
     // The batched kernel is int16x2 only; an int32 search runs in the plain form.
-    p.mode = (mode == SW_MODE_BATCHED && p.precision == SW_PREC_I16) ? SW_MODE_BATCHED : SW_MODE_PLAIN;
+    // SW_MODE_AUTO takes the handle's tuned form (plain unless tuned otherwise)
+    const int want_mode = mode == SW_MODE_AUTO ? db->tuning.mode : mode;
+    p.mode = (want_mode == SW_MODE_BATCHED && p.precision == SW_PREC_I16) ? SW_MODE_BATCHED : SW_MODE_PLAIN;
 
     int lanes = opts && opts->lanes ? opts->lanes : 8;
     int rows = opts && opts->rows_per_lane ? opts->rows_per_lane : 16;
@@ -426,7 +458,7 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
             p.min_tr = 1 << 30;
             for (int32_t i = 0; i < n_q; ++i) {
                 int l = 8, r = 16;
-                choose_shape(q_offsets[i + 1] - q_offsets[i], &l, &r);
+                choose_shape(p.plain_table, q_offsets[i + 1] - q_offsets[i], &l, &r);
                 p.min_tr = std::min(p.min_tr, l * r);
             }
             if (n_q == 0) p.min_tr = 128;
@@ -442,11 +474,14 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
     // first) whose length exceeds the cutoff are scored by a separate launch
     // with wide subwarps on a second stream, concurrently with the rest, so a
     // handful of very long sequences do not set the length of the main launch.
-    const int64_t cutoff = opts && opts->long_cutoff ? opts->long_cutoff : 3072;
-    if (opts && opts->long_rows_per_lane) {
-        if (opts->long_rows_per_lane == 8) { p.rows_long = 8; p.warps_long = 4; }
-        else if (opts->long_rows_per_lane == 16) { p.rows_long = 16; p.warps_long = 4; }
-        else if (opts->long_rows_per_lane == 32) { p.rows_long = 32; p.warps_long = 2; }
+    const int64_t cutoff = opts && opts->long_cutoff ? opts->long_cutoff
+                                                     : (db->tuning.long_cutoff ? db->tuning.long_cutoff : 3072);
+    const int32_t long_rows = opts && opts->long_rows_per_lane ? opts->long_rows_per_lane
+                                                               : db->tuning.long_rows_per_lane;
+    if (long_rows) {
+        if (long_rows == 8) { p.rows_long = 8; p.warps_long = 4; }
+        else if (long_rows == 16) { p.rows_long = 16; p.warps_long = 4; }
+        else if (long_rows == 32) { p.rows_long = 32; p.warps_long = 2; }
         else return fail(SW_ERR_UNSUPPORTED, "long_rows_per_lane must be 8, 16 or 32");
     }
     int64_t nlb = 0;
@@ -456,7 +491,7 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
     for (int64_t b = 0; b < nlb; ++b) p.long_residues += db->h_bundle_res[size_t(b)];
     p.n_long = std::min<int64_t>(nlb * kBundleSeqs, db->n_seqs);
     p.long_codes_bytes = nlb < db->n_bundles ? db->h_bundle_off[size_t(nlb)] : db->codes_bytes;
-    if (!(opts && opts->long_rows_per_lane)) {
+    if (!long_rows) {
         // Few (long pair, query) tasks: the launch is bound by the serial
         // column chain of the longest sequences, which shares its SMs with the
         // concurrent inter-task launch, so 16 rows per lane (a shorter step)
@@ -486,12 +521,12 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
         // shape is chosen per query), so that a workspace sized for queries of
         // the maximum length also fits any batch of shorter ones.
         const int sms = std::max(1, db->sm_count);
-        const int n_shapes = p.auto_shape ? int(sizeof(kShapes) / sizeof(kShapes[0])) : 1;
+        const int n_shapes = p.auto_shape ? int(p.plain_table.size()) : 1;
         int min_tr = 1 << 30;
         p.inter_min_lanes = 32;
         for (int sh = 0; sh < n_shapes; ++sh) {
-            const int l = p.auto_shape ? kShapes[sh].lanes : p.lanes;
-            const int r = p.auto_shape ? kShapes[sh].rows : p.rows;
+            const int l = p.auto_shape ? p.plain_table[size_t(sh)].lanes : p.lanes;
+            const int r = p.auto_shape ? p.plain_table[size_t(sh)].rows : p.rows;
             p.inter_min_lanes = std::min(p.inter_min_lanes, l);
             p.inter_grid_max = std::max(p.inter_grid_max, inter_slots(l, r, sms));
             min_tr = std::min(min_tr, l * r);
@@ -517,17 +552,17 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
             pb.push_back(i + 1 < idx.size() ? idx[i + 1] : -1);
         }
         // Group the pairs by launch shape (each group keeps longest-first order).
-        const int n_shapes = p.auto_shape ? int(sizeof(kBatchShapes) / sizeof(kBatchShapes[0])) : 1;
+        const int n_shapes = p.auto_shape ? int(p.batch_table.size()) : 1;
         p.batch_max_m = idx.empty() ? 0 : int32_t(q_offsets[idx[0] + 1] - q_offsets[idx[0]]);
         p.batch_scratch = p.batch_max_m > 128;   // any multi-pass pair, in any shape
         for (int sh = 0; sh < n_shapes; ++sh) {
-            const int gl = p.auto_shape ? kBatchShapes[sh].lanes : p.lanes;
-            const int gr = p.auto_shape ? kBatchShapes[sh].rows : p.rows;
+            const int gl = p.auto_shape ? p.batch_table[size_t(sh)].lanes : p.lanes;
+            const int gr = p.auto_shape ? p.batch_table[size_t(sh)].rows : p.rows;
             Plan::BatchGroup g{gl, gr, int32_t(p.qp_a.size()), 0, 0};
             int64_t gmax = 0;
             for (size_t i = 0; i < pa.size(); ++i) {
                 const int64_t m = q_offsets[pa[i] + 1] - q_offsets[pa[i]];
-                if (p.auto_shape && choose_batch_shape(m) != sh) continue;
+                if (p.auto_shape && choose_batch_shape(p.batch_table, m) != sh) continue;
                 p.qp_a.push_back(pa[i]);
                 p.qp_b.push_back(pb[i]);
                 gmax = std::max(gmax, m);
@@ -544,7 +579,7 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
         // Size the per-slot scratch for the widest grid any shape could use, so a
         // workspace sized for one batch fits every batch of the same length bound.
         if (p.auto_shape)
-            for (const ShapeRate &c : kBatchShapes)
+            for (const ShapeRate &c : p.batch_table)
                 p.batch_grid = std::max(p.batch_grid, batch_slots(c.lanes, c.rows, std::max(1, db->sm_count)));
         p.batch_seq_begin = p.long_end_pair * 2;
         p.batch_max_cols = p.batch_seq_begin < db->n_sorted
@@ -865,6 +900,48 @@ int sw_db_get_info(const sw_db *db, sw_db_info *out) {
     out->device_bytes = db->codes_bytes + db->n_bundles * 12 + db->n_sorted * 12;
     out->alphabet_size = db->A;
     out->device = db->device;
+    return SW_OK;
+}
+
+int sw_db_set_tuning(sw_db *db, const sw_tuning *t) {
+    g_last_error.clear();
+    if (!db) return fail(SW_ERR_INVALID_ARG, "db is NULL");
+    if (t) {
+        if (t->n_plain < 0 || t->n_plain > SW_TUNING_MAX_SHAPES || t->n_batched < 0 ||
+            t->n_batched > SW_TUNING_MAX_SHAPES)
+            return fail(SW_ERR_INVALID_ARG, "shape count outside 0..SW_TUNING_MAX_SHAPES");
+        auto bad_rate = [](float g) { return !(g > 0.0f) || !(g < 1e30f); };
+        for (int i = 0; i < t->n_plain; ++i) {
+            if (!inter_config_supported(t->plain[i].lanes, t->plain[i].rows_per_lane))
+                return fail(SW_ERR_INVALID_ARG, "a plain-form shape the inter-task kernel does not support");
+            if (bad_rate(t->plain[i].gcups)) return fail(SW_ERR_INVALID_ARG, "a shape rate is not positive and finite");
+        }
+        for (int i = 0; i < t->n_batched; ++i) {
+            if (!batch_config_supported(t->batched[i].lanes, t->batched[i].rows_per_lane))
+                return fail(SW_ERR_INVALID_ARG, "a batched-form shape the batched kernel does not support");
+            if (bad_rate(t->batched[i].gcups)) return fail(SW_ERR_INVALID_ARG, "a shape rate is not positive and finite");
+        }
+        if (t->long_rows_per_lane != 0 && t->long_rows_per_lane != 8 && t->long_rows_per_lane != 16 &&
+            t->long_rows_per_lane != 32)
+            return fail(SW_ERR_INVALID_ARG, "long_rows_per_lane must be 0, 8, 16 or 32");
+        if (t->mode < SW_MODE_AUTO || t->mode > SW_MODE_BATCHED) return fail(SW_ERR_INVALID_ARG, "unknown mode");
+    }
+    std::lock_guard<std::mutex> lock(db->mu);
+    if (t) db->tuning = *t;
+    else db->tuning = sw_tuning{};
+    ++db->tuning_version;
+    return SW_OK;
+}
+
+int sw_db_get_tuning(const sw_db *db, sw_tuning *out) {
+    g_last_error.clear();
+    if (!db || !out) return fail(SW_ERR_INVALID_ARG, "NULL argument");
+    *out = db->tuning;
+    const ShapeTable pt = plain_shapes(db), bt = batch_shapes(db);
+    out->n_plain = int32_t(pt.size());
+    out->n_batched = int32_t(bt.size());
+    for (size_t i = 0; i < pt.size(); ++i) out->plain[i] = {pt[i].lanes, pt[i].rows, float(pt[i].gcups)};
+    for (size_t i = 0; i < bt.size(); ++i) out->batched[i] = {bt[i].lanes, bt[i].rows, float(bt[i].gcups)};
     return SW_OK;
 }
 
@@ -1189,7 +1266,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
             ia.pair_begin = plan.long_end_pair;
             ia.pair_end = n_pairs;
             int lanes = plan.lanes, rows = plan.rows;
-            if (plan.auto_shape) choose_shape(m, &lanes, &rows);
+            if (plan.auto_shape) choose_shape(plan.plain_table, m, &lanes, &rows);
             last_lanes = lanes;
             last_rows = rows;
             // persistent grid, per-slot boundary scratch (stays in L2)
@@ -1252,6 +1329,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
                                 hits_out != nullptr, plan.rows_long, plan.warps_long, plan.alignment};
         put(ints, sizeof ints);
         put(&plan.long_end_pair, sizeof plan.long_end_pair);
+        put(&db->tuning_version, sizeof db->tuning_version);
         if (n_q > 0) put(q_offsets, sizeof(int64_t) * size_t(n_q + 1));
         put(matrix, sizeof(int32_t) * size_t(db->A) * size_t(db->A));
         if (!(db->graph_exec && db->graph_key == key)) {
@@ -1284,7 +1362,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
                     last_rows = plan.mode16_rows.back();
                 }
             } else if (plan.precision == SW_PREC_I16 && plan.mode == SW_MODE_PLAIN && plan.auto_shape && n_q > 0) {
-                choose_shape(q_offsets[n_q] - q_offsets[n_q - 1], &last_lanes, &last_rows);
+                choose_shape(plan.plain_table, q_offsets[n_q] - q_offsets[n_q - 1], &last_lanes, &last_rows);
             }
         }
         SW_CUDA_TRY(cudaGraphLaunch(db->graph_exec, st));

@@ -133,3 +133,21 @@ def test_wait_probe_rejects_bad_arguments_on_host(lib):
     assert "spin_iters" in binding.sw_last_error()
     assert lib.sw_probe_wait_timeout(0, 1 << 26, ctypes.byref(st), ctypes.byref(ms)) == 1
     assert lib.sw_probe_wait_timeout(0, 1000, None, ctypes.byref(ms)) == 1
+
+
+def test_tuning_struct_size_matches_the_header(tmp_path):
+    import subprocess
+    from paper_2203_11100_gb300 import binding
+    src = tmp_path / "tsize.c"
+    src.write_text('#include <stdio.h>\n#include "swdb.h"\nint main(void) {\n'
+                   '  printf("%zu %zu\\n", sizeof(sw_tuning), sizeof(sw_shape_rate));\n  return 0;\n}\n')
+    exe = tmp_path / "tsize"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert got == [ctypes.sizeof(binding.SwTuning), ctypes.sizeof(binding.SwShapeRate)] == [408, 12]
+
+
+def test_tuning_rejects_bad_tables_on_host(lib):
+    from paper_2203_11100_gb300 import binding
+    assert lib.sw_db_set_tuning(None, None) == 1
+    assert "db is NULL" in binding.sw_last_error()

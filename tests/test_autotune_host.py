@@ -20,3 +20,26 @@ def test_batch_key_depends_on_shape():
     k2 = autotune._batch_key(info, np.array([1000, 2000, 3000]))
     k3 = autotune._batch_key(info, np.array([100, 200, 300]))
     assert k1 != k2 and k1 == k3
+
+
+def test_search_key_separates_matrix_penalties_and_precision(monkeypatch):
+    from paper_2203_11100_gb300 import binding
+    monkeypatch.setattr(binding, "sw_version", lambda: "v")
+    S = np.eye(4, dtype=np.int32)
+    T = S.copy()
+    T[0, 1] = 2
+    k = autotune._search_key(S, 10, 1, 1)
+    assert k == autotune._search_key(S.copy(), 10, 1, 1)
+    assert k != autotune._search_key(T, 10, 1, 1)
+    assert k != autotune._search_key(S, 10, 2, 1)
+    assert k != autotune._search_key(S, 11, 1, 1)
+    assert k != autotune._search_key(S, 10, 1, 2)
+
+
+def test_probe_queries_are_whole_strips_of_the_batch():
+    res = np.arange(100, dtype=np.uint8) % 20
+    q, off = autotune._probe_queries(res, 2)
+    assert off.tolist() == [0, autotune.RATE_ROWS, 2 * autotune.RATE_ROWS]
+    assert len(q) == 2 * autotune.RATE_ROWS and np.array_equal(q[:100], res)
+    for lanes, rows in autotune.PLAIN_SHAPES + autotune.BATCH_SHAPES:
+        assert autotune.RATE_ROWS % (lanes * rows) == 0

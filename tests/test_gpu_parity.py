@@ -360,6 +360,9 @@ def test_graph_capture_and_replay(gpu, mode):
 
 
 def test_autotune_picks_and_caches(gpu, tmp_path):
+    """The autotuner measures the shape tables, cutoff and form, installs them
+    on the handle, caches them, and the tuned searches (explicit parameters
+    and SW_MODE_AUTO) still equal the oracle."""
     from paper_2203_11100_gb300 import autotune
     rng = np.random.default_rng(61)
     db = synth.seqset_from_lengths(rng, synth.lognormal_lengths(rng, 3000, 360.0, 2, 5000))
@@ -368,13 +371,48 @@ def test_autotune_picks_and_caches(gpu, tmp_path):
     cache = tmp_path / "tune.json"
     with gpu.Database(db.residues, db.offsets, 24) as d:
         params = autotune.autotune(d, qs.residues, qs.offsets, S, 10, 1, sample_queries=4, cache_path=str(cache),
-                                   cutoffs=(1024, 3072))
-        assert cache.exists()
-        assert set(params) == {"mode", "lanes", "rows_per_lane", "long_cutoff"}
+                                   cutoffs=(1024, 3072), repeats=2)
+        first = autotune.last_result()
+        assert cache.exists() and not first["cached"]
+        assert set(params) == {"mode", "long_cutoff"} and params["long_cutoff"] in (1024, 3072)
+        tuned = gpu.sw_db_get_tuning(d.handle)
+        assert len(tuned["plain"]) == len(autotune.PLAIN_SHAPES)
+        assert len(tuned["batched"]) == len(autotune.BATCH_SHAPES)
+        assert all(g > 0 for _, _, g in tuned["plain"] + tuned["batched"])
+        assert tuned["mode"] == params["mode"] and tuned["long_cutoff"] == params["long_cutoff"]
+        gpu.sw_db_set_tuning(d.handle, None)
+        assert gpu.sw_db_get_tuning(d.handle)["long_cutoff"] == 0
         again = autotune.autotune(d, qs.residues, qs.offsets, S, 10, 1, cache_path=str(cache))
-        assert again == params
+        assert again == params and autotune.last_result()["cached"]
+        assert gpu.sw_db_get_tuning(d.handle) == tuned                 # reinstalled from the cache
         scores, _, _ = d.search(qs.residues, qs.offsets, S, 10, 1, top_k=0, **params)
-    np.testing.assert_array_equal(scores, oracle.all_scores(qs, db, S, 10, 1))
+        auto, _, st = d.search(qs.residues, qs.offsets, S, 10, 1, top_k=0, stats=True)   # SW_MODE_AUTO
+        assert st["mode_used"] == params["mode"]
+    want = oracle.all_scores(qs, db, S, 10, 1)
+    np.testing.assert_array_equal(scores, want)
+    np.testing.assert_array_equal(auto, want)
+
+
+def test_tuned_tables_drive_the_shape_choice(gpu):
+    """A table with one plain shape makes every query of a search use it; a
+    shape the kernel does not support is rejected; scores stay exact."""
+    rng = np.random.default_rng(62)
+    db = _db(rng, 500, 1, 700)
+    qs = synth.seqset_from_lengths(rng, [90, 700, 2000])
+    S = synth.blosum62()
+    with gpu.Database(db.residues, db.offsets, 24) as d:
+        gpu.sw_db_set_tuning(d.handle, {"plain": [(16, 32, 1000.0)], "batched": [(8, 24, 1000.0)]})
+        scores, _, st = d.search(qs.residues, qs.offsets, S, 10, 1, top_k=0, stats=True, mode=gpu.SW_MODE_PLAIN)
+        assert (st["lanes_used"], st["rows_per_lane_used"]) == (16, 32)
+        sb, _, stb = d.search(qs.residues, qs.offsets, S, 10, 1, top_k=0, stats=True, mode=gpu.SW_MODE_BATCHED)
+        assert (stb["lanes_used"], stb["rows_per_lane_used"]) == (8, 24)
+        with pytest.raises(gpu.SwError):
+            gpu.sw_db_set_tuning(d.handle, {"plain": [(8, 40, 1000.0)]})
+        with pytest.raises(gpu.SwError):
+            gpu.sw_db_set_tuning(d.handle, {"plain": [(8, 16, -1.0)]})
+    want = oracle.all_scores(qs, db, S, 10, 1)
+    np.testing.assert_array_equal(scores, want)
+    np.testing.assert_array_equal(sb, want)
 
 
 @pytest.mark.parametrize("mode", ["plain", "batched"])
