@@ -412,6 +412,7 @@ def run_ours(args, dist: Dist):
     if dist.rank == 0:
         rate_dpx, sms = swdb.sw_probe_alu_rate(dev, 0)
         rate_cells, _ = swdb.sw_probe_alu_rate(dev, 1)
+        rate_u8x4, _ = swdb.sw_probe_alu_rate(dev, 2)
         mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
         local = args.alignment == "local"
         packed = local or st0["precision_used"] == swdb.SW_PREC_I16
@@ -459,6 +460,8 @@ def run_ours(args, dist: Dist):
                                        f"{mhz:.0f} MHz (median under load) / {ops_per_cell} ops per cell"
                                        + basis_note,
                          "register_only_ceiling_gcups": ceiling,
+                         "probe_cells_per_sm_cycle": {"int16x2_shipped_sequence": rate_cells,
+                                                      "int8x4_byte_simd": rate_u8x4},
                          "avg_launch_ms": inter_ms / max(inter_launches, 1)},
             "cpu_baseline": cb,
             "e2e": {"value": e2e_gcups, "unit": UNIT, "h2d_bytes_per_step": int(w.queries.residues.nbytes),
@@ -496,7 +499,7 @@ def want_autotune(args, default: bool) -> bool:
     return args.autotune == "on" or (args.autotune == "auto" and default)
 
 
-def tune(db, w, forms=("plain", "batched"), sample_queries: int = 8, cutoffs=(2048, 3072, 6144)) -> dict:
+def tune(db, w, forms=("plain", "batched"), sample_queries: int = 8, cutoffs=(0, 2048, 6144)) -> dict:
     """Run the autotuner for this database and batch (outside any timed
     region) and summarise what it chose and measured."""
     from paper_2203_11100_gb300 import autotune

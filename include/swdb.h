@@ -114,7 +114,12 @@ typedef struct {
     int32_t precision;        /* sw_precision */
     int32_t mode;             /* sw_mode */
     int64_t long_cutoff;      /* database sequences longer than this are scored by the
-                                 intra-task kernel; 0 = library default, <0 = never */
+                                 intra-task kernel; <0 = never; 0 = the handle's tuning, else
+                                 the library default: the longest length n <= 3072 (at
+                                 least 768) at which one sequence pair holds no more than
+                                 1/S of the residues of the sequences up to n, S the
+                                 resident subwarps of the default launch shape (a pair
+                                 scored by one subwarp then never outlasts the launch) */
     int32_t lanes;            /* lanes per database-sequence pair in the inter-task kernel
                                  (4, 8, 16 or 32); 0 = chosen per query by the library */
     int32_t rows_per_lane;    /* query rows held per lane (16, 24 or 32; 8 with 32 lanes);
@@ -299,7 +304,11 @@ int sw_top_k(const int32_t *scores, int64_t n_rows, int64_t n_cols, int32_t top_
  * SM and counts SM cycles with clock64.
  *   mode 0: packed int16x2 DPX add-max operations per SM cycle
  *   mode 1: cell updates per SM cycle of the inter-task kernel's own
- *           instruction sequence, from registers (no memory traffic)
+ *           instruction sequence as it ships (32 rows per lane; operands in
+ *           registers, profile words from shared memory, no global traffic)
+ *   mode 2: cell updates per SM cycle of the same recurrence in unsigned
+ *           saturating byte SIMD, four sequences per 32-bit word (the
+ *           int8x4 lane packing, measured rather than built)
  * Writes the rate to *per_sm_cycle and the SM count to *sm_count.
  */
 int sw_probe_alu_rate(int device, int32_t mode, double *per_sm_cycle, int32_t *sm_count);

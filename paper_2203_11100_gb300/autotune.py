@@ -45,7 +45,7 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "swdb", "autotun
 
 PLAIN_SHAPES = ((8, 16), (16, 16), (32, 16), (8, 24), (8, 32), (16, 32), (32, 32))
 BATCH_SHAPES = ((8, 16), (8, 24), (8, 32), (16, 16), (16, 24), (16, 32))
-CUTOFFS = (2048, 3072, 6144, 12288)
+CUTOFFS = (0, 1024, 2048, 3072, 6144)   # 0: the library's balanced default for this database
 RATE_ROWS = 3072          # a whole number of strips of every candidate shape
 
 

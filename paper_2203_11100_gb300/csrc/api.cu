@@ -75,6 +75,7 @@ struct sw_db {
     cudaGraphExec_t graph_exec = nullptr;   // last captured search (SW_FLAG_GRAPH)
     std::string graph_key;
     std::mutex mu;
+    int64_t default_cutoff = 3072;          // long-sequence cutoff when neither opts nor tuning set one
     sw_tuning tuning{};                     // installed by sw_db_set_tuning (counts 0: library tables)
     int64_t tuning_version = 0;             // bumped by every sw_db_set_tuning
 
@@ -141,6 +142,32 @@ void free_db_device(sw_db *db) {
 }
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Default length above which database sequences leave the inter-task launch
+// for the intra-task one.  In the inter-task kernel a subwarp scores one
+// pair through ceil(m / (lanes*rows)) strips, one after another, so a pair
+// of n columns keeps its subwarp busy for a time proportional to m * n,
+// while the launch's throughput spreads the m * R cells of the R residues it
+// holds over S resident subwarps: when one pair holds more than 1/S of the
+// work, the launch waits on it.  Both sides scale with m, so the balance
+// point depends only on the database: the longest bundle length n <= 3072
+// with n * 2S <= R(n), the residues of the bundles of length <= n (2S:
+// sequence pairs count two sequences per subwarp), S = 2 CTAs x 32
+// subwarps per SM of the default 8-lane shape, and not below 768.
+// Bundles are sorted longest first.
+int64_t balanced_long_cutoff(const std::vector<int32_t> &bundle_len, const std::vector<int64_t> &bundle_res,
+                             int sms) {
+    constexpr int64_t kMaxCutoff = 3072, kMinCutoff = 768;
+    const int64_t slots2 = int64_t(std::max(1, sms)) * 2 * (kCtaThreads / 8) * 2;
+    int64_t suffix = 0;
+    for (int64_t r : bundle_res) suffix += r;
+    for (size_t b = 0; b < bundle_len.size(); ++b) {
+        const int64_t L = bundle_len[b];
+        if (L <= kMaxCutoff && (L <= kMinCutoff || L * slots2 <= suffix)) return std::max(L, kMinCutoff);
+        suffix -= bundle_res[b];
+    }
+    return kMinCutoff;
+}
 
 // Workspace carve-out: a bump allocator over one device buffer.
 struct Carver {
@@ -475,7 +502,8 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
     // with wide subwarps on a second stream, concurrently with the rest, so a
     // handful of very long sequences do not set the length of the main launch.
     const int64_t cutoff = opts && opts->long_cutoff ? opts->long_cutoff
-                                                     : (db->tuning.long_cutoff ? db->tuning.long_cutoff : 3072);
+                                                     : (db->tuning.long_cutoff ? db->tuning.long_cutoff
+                                                                               : db->default_cutoff);
     const int32_t long_rows = opts && opts->long_rows_per_lane ? opts->long_rows_per_lane
                                                                : db->tuning.long_rows_per_lane;
     if (long_rows) {
@@ -833,6 +861,7 @@ int sw_db_load(const uint8_t *residues, const int64_t *offsets, int64_t n_seqs, 
     db->codes_bytes = off;
     db->h_bundle_res.assign(size_t(db->n_bundles), 0);
     for (int64_t t = 0; t < n_seqs; ++t) db->h_bundle_res[size_t(t / kBundleSeqs)] += db->h_len[size_t(t)];
+    db->default_cutoff = balanced_long_cutoff(db->h_bundle_len, db->h_bundle_res, db->sm_count);
     std::vector<uint8_t> codes(size_t(std::max<int64_t>(off, 1)), uint8_t(kPadCode));
     for (int64_t s = 0; s < n_seqs; ++s) {
         const int64_t b = s / kBundleSeqs;
@@ -1457,7 +1486,7 @@ int sw_probe_wait_timeout(int device, int64_t spin_iters, int32_t *status_out, d
 
 int sw_probe_alu_rate(int device, int32_t mode, double *per_sm_cycle, int32_t *sm_count) {
     g_last_error.clear();
-    if (!per_sm_cycle || !sm_count || (mode != 0 && mode != 1)) return fail(SW_ERR_INVALID_ARG, "bad argument");
+    if (!per_sm_cycle || !sm_count || mode < 0 || mode > 2) return fail(SW_ERR_INVALID_ARG, "bad argument");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();
@@ -1482,8 +1511,7 @@ int sw_probe_alu_rate(int device, int32_t mode, double *per_sm_cycle, int32_t *s
         if (err == cudaSuccess) err = cudaDeviceSynchronize();
         if (err == cudaSuccess) err = cudaMemcpy(&c, cycles, sizeof c, cudaMemcpyDeviceToHost);
         if (err == cudaSuccess && c > 0) {
-            // mode 0: 64 DPX ops per thread-iteration; mode 1: 16 rows x 2 cells.
-            const double per_thread = mode == 0 ? 64.0 : 32.0;
+            const double per_thread = probe_work_per_iteration(mode);
             const double work = double(grid) * kCtaThreads * double(iters) * per_thread;
             best = std::max(best, work / (double(c) * sms));
         }

@@ -238,6 +238,7 @@ bool i32_config_supported(int lanes, int rows);
 cudaError_t launch_probe(int mode, int grid, int iters, unsigned long long *cycles, uint32_t *sink,
                          cudaStream_t s);
 int probe_blocks_per_sm(int mode);
+double probe_work_per_iteration(int mode);
 cudaError_t launch_modes_i32(const ModeArgs &a, int grid, cudaStream_t s);   // grid capped by the items
 int modes_slots(int sms);            // resident CTAs of the modes kernel
 int32_t modes_strip_rows();
