@@ -87,6 +87,11 @@ def parse_args(argv=None):
                    help="fraction of the 20M-sequence serving database (0.1 = 2M sequences)")
     p.add_argument("--serve-requests", type=int, default=96)
     p.add_argument("--serve-max-batch", type=int, default=16)
+    p.add_argument("--serve-point-requests", type=int, default=0,
+                   help="requests per Poisson load point (0 = half of --serve-requests)")
+    p.add_argument("--serve-check", type=int, default=8,
+                   help="served requests whose hits are checked against the oracle's scores and against a plain "
+                        "search of the same query")
     p.add_argument("--graph", action="store_true",
                    help="capture the search into a CUDA graph on the first call and replay it")
     p.add_argument("--alignment", choices=["local", "global", "semiglobal", "overlap"], default="local",
@@ -843,8 +848,7 @@ def run_serving(args, dist: Dist):
     srv = new_server()
     t0 = time.perf_counter()
     futs = [srv.submit(reqs.seq(i)) for i in range(n_req)]
-    for f in futs:
-        f.result(timeout=RESULT_TIMEOUT_S)
+    served = [f.result(timeout=RESULT_TIMEOUT_S) for f in futs]
     sat_s = time.perf_counter() - t0
     sat = srv.stats()
     srv.close()
@@ -856,7 +860,7 @@ def run_serving(args, dist: Dist):
     base = n_req
     for frac in (0.5, 0.8, 0.95):
         rate = frac * sat_rate
-        count = max(16, n_req // 2)
+        count = args.serve_point_requests or max(16, n_req // 2)
         gaps = rng.exponential(1.0 / rate, count)
         srv = new_server()
         t_start = time.perf_counter()
@@ -886,6 +890,25 @@ def run_serving(args, dist: Dist):
     t0 = time.perf_counter()
     swdb.sw_search(db.handle, q_dev, q_off, S, 10, 1, 10, None, hits, mode=swdb.SW_MODE_PLAIN, stats=True)
     plain_s = time.perf_counter() - t0
+    # served results: the same hits as the plain search of the same query, and
+    # every hit's score equal to the oracle's score of that pair
+    check = None
+    if args.serve_check > 0:
+        import oracle
+        from paper_2203_11100_gb300 import multigpu
+        oracle.build()
+        k = min(args.serve_check, n_req)
+        plain = multigpu.tensor_to_hits(hits[:k])
+        same = all(np.array_equal(served[i]["score"], plain[i]["score"]) and
+                   np.array_equal(served[i]["db_index"], plain[i]["db_index"]) for i in range(k))
+        qi = np.repeat(np.arange(k, dtype=np.int64), 10)
+        ti = np.concatenate([served[i]["db_index"] for i in range(k)]).astype(np.int64)
+        qs = synth.SeqSet(reqs.residues, reqs.offsets)
+        t0 = time.perf_counter()
+        want = oracle.score_pairs(qs, dbs, qi, ti, S, 10, 1)
+        got = np.concatenate([served[i]["score"] for i in range(k)]).astype(np.int64)
+        check = {"requests": k, "hits_equal_plain_search": bool(same), "hit_scores_equal_oracle":
+                 bool(np.array_equal(want, got)), "oracle_pairs": int(len(qi)), "oracle_s": time.perf_counter() - t0}
     db.close()
     value = sat_cells / sat_s / 1e9
     return {"metric": "GCUPS (served: continuous batching, database resident in HBM)", "value": value,
@@ -899,7 +922,8 @@ def run_serving(args, dist: Dist):
                        "streams": 3, "autotune": tuned if tuned else "off"},
             "serving": {"saturation_rate_per_s": sat_rate, "saturation_p50_ms": sat["p50_ms"],
                         "saturation_p99_ms": sat["p99_ms"], "points": points,
-                        "plain_one_launch_per_query_gcups": sat_cells / plain_s / 1e9},
+                        "plain_one_launch_per_query_gcups": sat_cells / plain_s / 1e9,
+                        "served_check": check},
             "clocks": clk}
 
 

@@ -770,6 +770,15 @@ struct LaunchTimer {
 // Read-only facts of a loaded database, for entry points defined in other
 // translation units.
 namespace swdb {
+int high_launch_priority() {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return greatest;
+}
+
 bool db_describe(const sw_db *db, DbView *view, int *device, int32_t *alphabet, int64_t *codes_bytes) {
     if (!db) return false;
     *view = db->view();
@@ -1087,6 +1096,11 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
     const int64_t list_stride = std::max<int64_t>(n_pairs, 1);
     const bool split = plan.precision == SW_PREC_I16 && plan.long_end_pair > 0 && n_q > 0 && db->n_seqs > 0;
     const int32_t n_qp = int32_t(plan.qp_a.size());
+    // While the long sequences run on the side stream, the main-stream launches
+    // take a higher priority: their CTAs are dispatched as soon as SMs free up
+    // instead of queuing behind every pending intra-task CTA (the intra-task
+    // CTAs already running, the longest tasks first, are not preempted).
+    const int main_priority = split && !plan.long_inter ? high_launch_priority() : 0;
 
     // Host-to-device inputs first: they stay outside any captured graph.
     if (!plan.mode_entries.empty())
@@ -1272,7 +1286,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
             ba.tile_counter = d_tiles + (gi & 3);
             last_lanes = g.lanes;
             last_rows = g.rows;
-            TIMED(LaunchTimer::INTER, launch_batch_i16x2(ba, g.lanes, g.rows, g.grid, st));
+            TIMED(LaunchTimer::INTER, launch_batch_i16x2(ba, g.lanes, g.rows, g.grid, st, main_priority));
         }
     }
 
@@ -1304,7 +1318,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
             ia.slot_stride = int64_t(kCtaThreads / lanes) * plan.inter_max_cols;
             ia.chunk_counter = d_chunks + qi;
             const int slots = inter_slots(lanes, rows, std::max(1, db->sm_count));
-            TIMED(LaunchTimer::INTER, launch_inter_i16x2(ia, lanes, rows, st, slots));
+            TIMED(LaunchTimer::INTER, launch_inter_i16x2(ia, lanes, rows, st, slots, main_priority));
         } else {
             const int tr32 = plan.lanes32 * plan.rows32;
             const int32_t m_pad = int32_t(round_up(m, tr32));

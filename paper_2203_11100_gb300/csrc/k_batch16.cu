@@ -271,9 +271,10 @@ size_t batch_smem() {
 }
 
 template <int T, int R>
-cudaError_t launch_tr(const BatchArgs &a, int grid, cudaStream_t s) {
+cudaError_t launch_tr(const BatchArgs &a, int grid, cudaStream_t s, int priority) {
     const size_t smem = batch_smem<T, R>();   // attribute set by batch_slots at planning
-    k_batch_i16x2<T, R><<<grid, kCtaThreads, smem, s>>>(a);
+    const cudaError_t e = launch_with_priority(k_batch_i16x2<T, R>, dim3(grid), dim3(kCtaThreads), smem, s, priority, a);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -309,14 +310,14 @@ int batch_slots(int lanes, int rows, int sms) {
     }
 }
 
-cudaError_t launch_batch_i16x2(const BatchArgs &a, int lanes, int rows, int grid, cudaStream_t s) {
+cudaError_t launch_batch_i16x2(const BatchArgs &a, int lanes, int rows, int grid, cudaStream_t s, int priority) {
     switch (lanes * 100 + rows) {
-        case 816: return launch_tr<8, 16>(a, grid, s);
-        case 824: return launch_tr<8, 24>(a, grid, s);
-        case 832: return launch_tr<8, 32>(a, grid, s);
-        case 1624: return launch_tr<16, 24>(a, grid, s);
-        case 1616: return launch_tr<16, 16>(a, grid, s);
-        case 1632: return launch_tr<16, 32>(a, grid, s);
+        case 816: return launch_tr<8, 16>(a, grid, s, priority);
+        case 824: return launch_tr<8, 24>(a, grid, s, priority);
+        case 832: return launch_tr<8, 32>(a, grid, s, priority);
+        case 1624: return launch_tr<16, 24>(a, grid, s, priority);
+        case 1616: return launch_tr<16, 16>(a, grid, s, priority);
+        case 1632: return launch_tr<16, 32>(a, grid, s, priority);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -331,14 +331,17 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_inter_i16x2(
 }
 
 template <int T, int R>
-cudaError_t launch_tr(const InterArgs &a, cudaStream_t s, int grid_slots) {
+cudaError_t launch_tr(const InterArgs &a, cudaStream_t s, int grid_slots, int priority) {
     constexpr int PAIRS_PER_CTA = kCtaThreads / T;
     const int64_t pairs = a.pair_end - a.pair_begin;
     if (pairs <= 0) return cudaSuccess;
     const int64_t chunks = (pairs + PAIRS_PER_CTA - 1) / PAIRS_PER_CTA;
     if (grid_slots > 0) {
         if (!a.chunk_counter) return cudaErrorInvalidValue;
-        k_inter_i16x2<T, R, true><<<unsigned(std::min<int64_t>(grid_slots, chunks)), kCtaThreads, 0, s>>>(a);
+        const cudaError_t e = launch_with_priority(k_inter_i16x2<T, R, true>,
+                                                   dim3(unsigned(std::min<int64_t>(grid_slots, chunks))),
+                                                   dim3(kCtaThreads), 0, s, priority, a);
+        if (e != cudaSuccess) return e;
     } else {
         k_inter_i16x2<T, R, false><<<unsigned(chunks), kCtaThreads, 0, s>>>(a);
     }
@@ -363,17 +366,18 @@ bool inter_config_supported(int lanes, int rows) {
     }
 }
 
-cudaError_t launch_inter_i16x2(const InterArgs &a, int lanes, int rows, cudaStream_t s, int grid_slots) {
+cudaError_t launch_inter_i16x2(const InterArgs &a, int lanes, int rows, cudaStream_t s, int grid_slots,
+                               int priority) {
     switch (lanes * 100 + rows) {
-        case 416: return launch_tr<4, 16>(a, s, grid_slots);
-        case 816: return launch_tr<8, 16>(a, s, grid_slots);
-        case 824: return launch_tr<8, 24>(a, s, grid_slots);
-        case 1616: return launch_tr<16, 16>(a, s, grid_slots);
-        case 3208: return launch_tr<32, 8>(a, s, grid_slots);
-        case 3216: return launch_tr<32, 16>(a, s, grid_slots);
-        case 832: return launch_tr<8, 32>(a, s, grid_slots);
-        case 1632: return launch_tr<16, 32>(a, s, grid_slots);
-        case 3232: return launch_tr<32, 32>(a, s, grid_slots);
+        case 416: return launch_tr<4, 16>(a, s, grid_slots, priority);
+        case 816: return launch_tr<8, 16>(a, s, grid_slots, priority);
+        case 824: return launch_tr<8, 24>(a, s, grid_slots, priority);
+        case 1616: return launch_tr<16, 16>(a, s, grid_slots, priority);
+        case 3208: return launch_tr<32, 8>(a, s, grid_slots, priority);
+        case 3216: return launch_tr<32, 16>(a, s, grid_slots, priority);
+        case 832: return launch_tr<8, 32>(a, s, grid_slots, priority);
+        case 1632: return launch_tr<16, 32>(a, s, grid_slots, priority);
+        case 3232: return launch_tr<32, 32>(a, s, grid_slots, priority);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace swdb {
 
 // Residue code used for padding past the end of a sequence.  Its profile
@@ -218,17 +220,41 @@ struct Mode16Args {
     int32_t *scores;            // row of this query, original database order
 };
 
+// Launch a kernel with an execution priority (cudaLaunchAttributePriority;
+// 0 = the stream's own).  Among CTAs waiting for an SM, the GPU dispatches
+// those of higher-priority launches first; CTAs already running are not
+// preempted.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_with_priority(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                 int priority, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = priority;
+    cfg.attrs = attr;
+    cfg.numAttrs = priority != 0 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// The highest launch priority of the current device (numerically smallest).
+int high_launch_priority();
+
 // Launchers (return cudaGetLastError() after the launch).
 // grid_slots > 0 launches a persistent grid of that many CTAs (slot-layout
 // scratch); 0 launches one CTA per chunk of pairs (per-pair scratch).
-cudaError_t launch_inter_i16x2(const InterArgs &a, int lanes, int rows, cudaStream_t s, int grid_slots = 0);
+cudaError_t launch_inter_i16x2(const InterArgs &a, int lanes, int rows, cudaStream_t s, int grid_slots = 0,
+                               int priority = 0);
 bool inter_config_supported(int lanes, int rows);
 int inter_slots(int lanes, int rows, int sms);   // resident CTAs of a persistent grid
 cudaError_t launch_intra_i16x2(const IntraArgs &a, int warps, int rows, cudaStream_t s);
 int intra_rows_per_superpass(int warps, int rows);
 cudaError_t prepare_intra_i16x2(int warps, int rows);   // kernel attributes; call before any capture
 bool intra_config_supported(int warps, int rows);
-cudaError_t launch_batch_i16x2(const BatchArgs &a, int lanes, int rows, int grid, cudaStream_t s);
+cudaError_t launch_batch_i16x2(const BatchArgs &a, int lanes, int rows, int grid, cudaStream_t s, int priority = 0);
 bool batch_config_supported(int lanes, int rows);
 int batch_slots(int lanes, int rows, int sms);   // resident CTAs of the persistent grid (sets attributes)
 cudaError_t launch_profile32(const uint8_t *query, int32_t m, int32_t m_pad, const int32_t *matrix_host,
