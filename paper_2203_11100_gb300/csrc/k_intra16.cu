@@ -22,7 +22,16 @@
 //   columns: a bounded producer/consumer pipeline with acquire/release
 //   flags, so the warps advance as a wavefront of their own.  Between
 //   super-passes the last warp's bottom row goes through global scratch
-//   (staged back with cp.async) and a CTA barrier.
+//   (one contiguous row per pair, staged back with cp.async) and a CTA
+//   barrier.
+// * Steady columns (every lane inside the sequence) run in groups of four
+//   with no per-column bookkeeping: lane 0's inputs (the column's codes and
+//   the boundary value from the ring, the staging buffer or the top row) are
+//   read by every lane as one broadcast load and taken by lane 0 with a
+//   select, the ring's waits and releases happen in the fixed groups where a
+//   chunk starts or ends, and the input and output addresses advance once
+//   per group.  The first 32 columns (lanes starting) and the last ones
+//   (lanes finishing, a partly filled chunk) take a general per-column path.
 // * Every wait is bounded: if a flag does not arrive within the spin limit
 //   the kernel records SW_ERR_TIMEOUT in a status word, tells the other
 //   warps to stop waiting, and finishes without hanging.
@@ -95,6 +104,7 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
     int *empty = full + P * NW;                                               // [P][NW] chunks read from link w
     int *abort_flag = empty + P * NW;
     __shared__ uint32_t red[P * NW];
+    __shared__ uint2 top4[4];          // the top row's inputs B(H-o), B(F) = B(-o), for broadcast reads
 
     const int warp = threadIdx.x >> 5;
     const int pl = warp / NW;          // pipeline (pair) within the CTA
@@ -116,19 +126,23 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
         empty[threadIdx.x] = 0;
     }
     if (threadIdx.x == 0) *abort_flag = 0;
+    if (threadIdx.x < 4) top4[threadIdx.x] = make_uint2(pack2(32768 - a.gap_open), pack2(32768 - a.gap_open));
 
     const int64_t pair = a.pair_begin + group * P + pl;
     const bool valid = pair < a.pair_end;
     int Lp = 0;
     const uint2 *cptr = nullptr;
-    uint2 *gbnd2 = nullptr;              // this pair's global boundary, [column/4][slot][column%4]
+    uint2 *gbnd2 = nullptr;              // this pair's global boundary row, one entry per column
     if (valid) {
         const int64_t b = pair / kBundlePairs;
         const int slot = int(pair % kBundlePairs);
         Lp = (a.db.len[2 * pair] + 3) & ~3;
         const int64_t off = a.db.bundle_off[b];
         cptr = reinterpret_cast<const uint2 *>(a.db.codes + off) + slot;
-        if (a.boundary) gbnd2 = a.boundary + int64_t(q) * a.boundary_stride + off / 2 + slot * 4;
+        // the bundle's region holds 8 * bundle_len entries: pair slot s owns
+        // [s * bundle_len, (s + 1) * bundle_len)
+        if (a.boundary)
+            gbnd2 = a.boundary + int64_t(q) * a.boundary_stride + off / 2 + int64_t(slot) * a.db.bundle_len[b];
     }
 
     const int o = a.gap_open;
@@ -192,26 +206,66 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
         // pub_h: B(Ho) of this lane's bottom row; pub_f: B(F) of the next lane's top row
         uint32_t pub_h = BNEG_O2, pub_f = BNEG_O2, pub_c = 0;
         uint2 quad = make_uint2(0, 0), quad_next = make_uint2(0, 0);
-        const uint4 *gsrc = reinterpret_cast<const uint4 *>(gbnd2);
-        if (k == 0) {
-            quad_next = __ldg(cptr);
-            if (from_global) {
-                cp_async16(stg + 0, gsrc);
-                cp_async16(stg + 2, gsrc + 1);
-                cp_async_commit();
-                if (4 < Lp) {
-                    cp_async16(stg + 4, gsrc + kBundlePairs * 2);
-                    cp_async16(stg + 6, gsrc + kBundlePairs * 2 + 1);
-                }
-                cp_async_commit();
+        const uint4 *gsrc = reinterpret_cast<const uint4 *>(gbnd2);   // 2 uint4 per 4 columns
+        quad_next = __ldg(cptr);         // every lane: one broadcast load
+        if (k == 0 && from_global) {
+            cp_async16(stg + 0, gsrc);
+            cp_async16(stg + 2, gsrc + 1);
+            cp_async_commit();
+            if (4 < Lp) {
+                cp_async16(stg + 4, gsrc + 2);
+                cp_async16(stg + 6, gsrc + 3);
             }
+            cp_async_commit();
         }
         const int steps = Lp + T - 1;
-        // One column step; STEADY: every lane inside the sequence (s >= 31 and
-        // s + 3 < Lp), U = s % 4 at compile time (see k_inter16.cu).
-        auto step = [&](const int s, auto steady_c, auto u_c) {
-            constexpr bool STEADY = decltype(steady_c)::value;
-            constexpr int U = decltype(u_c)::value;
+
+        // The cell work of one column step for this lane's R rows, given the
+        // top-row inputs (hin, fin) and the column's residue codes cin.
+        auto cells = [&](const uint32_t hin, const uint32_t fin, const uint32_t cin) {
+            const int ta = int(cin & 0xffu), tb = int((cin >> 8) & 0xffu);
+            const uint4 *pa = reinterpret_cast<const uint4 *>(prof + ta * SLOT + k * 16);
+            const uint4 *pb = reinterpret_cast<const uint4 *>(prof + tb * SLOT + k * 16);
+            uint32_t wa[R / 4], wb[R / 4];
+#pragma unroll
+            for (int v = 0; v < R / 16; ++v) {
+                const uint4 x = pa[v * T];
+                const uint4 y = pb[v * T];
+                wa[4 * v + 0] = x.x; wa[4 * v + 1] = x.y; wa[4 * v + 2] = x.z; wa[4 * v + 3] = x.w;
+                wb[4 * v + 0] = y.x; wb[4 * v + 1] = y.y; wb[4 * v + 2] = y.z; wb[4 * v + 3] = y.w;
+            }
+            if (R % 16) {                     // last group of 8 rows: an 8-byte load
+                const uint2 x = *reinterpret_cast<const uint2 *>(pa + (R / 16) * T);
+                const uint2 y = *reinterpret_cast<const uint2 *>(pb + (R / 16) * T);
+                wa[R / 4 - 2] = x.x; wa[R / 4 - 1] = x.y;
+                wb[R / 4 - 2] = y.x; wb[R / 4 - 1] = y.y;
+            }
+            uint32_t f = fin;
+            uint32_t d = hd;
+            uint32_t yprev = 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const uint32_t pr = prmt(wa[r / 4], wb[r / 4], pair_sel(r % 4));
+                const uint32_t e_r = __viaddmax_u16x2(E[r], ADD_NEG_E, Ho[r]);
+                const uint32_t x = __viaddmax_u16x2(d, pr, e_r);
+                const uint32_t y = __vimax3_u16x2(f, x, BZERO2);
+                const uint32_t ho = y - OO;
+                f = __viaddmax_u16x2(f, ADD_NEG_E, ho);
+                d = Ho[r];
+                E[r] = e_r;
+                Ho[r] = ho;
+                if (r & 1) mx = __vimax3_u16x2(mx, yprev, y);
+                yprev = y;
+            }
+            hd = hin;
+            pub_h = Ho[R - 1];
+            pub_f = f;
+            pub_c = cin;
+        };
+
+        // One column step with every check (lanes starting or finishing, a
+        // chunk boundary at any column): the ramp and the tail.
+        auto step = [&](const int s) {
             const int j31 = s - (T - 1);
             // Flow control (warp-uniform): wait for the producer's chunk before
             // lane 0 enters it, and for ring space before lane 31 starts writing one.
@@ -222,9 +276,9 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
             uint32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1, T);
             uint32_t cin = __shfl_up_sync(0xffffffffu, pub_c, 1, T);
             const int j = s - k;
-            const bool act = STEADY || ((j >= 0) && (j < Lp));
+            const bool act = (j >= 0) && (j < Lp);
             if (k == 0 && act) {
-                const int s3 = STEADY ? U : (s & 3);
+                const int s3 = s & 3;
                 if (s3 == 0) {
                     quad = quad_next;
                     if (s + 4 < Lp) quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
@@ -242,7 +296,7 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
                     fin = bv.y;
                     if (s3 == 3) {
                         if (s + 5 < Lp) {
-                            const uint4 *g = gsrc + size_t((s >> 2) + 2) * (kBundlePairs * 2);
+                            const uint4 *g = gsrc + size_t((s >> 2) + 2) * 2;
                             cp_async16(stg + ((s >> 2) & 1) * 4, g);
                             cp_async16(stg + ((s >> 2) & 1) * 4 + 2, g + 1);
                         }
@@ -254,49 +308,12 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
                 }
             }
             if (act) {
-                const int ta = int(cin & 0xffu), tb = int((cin >> 8) & 0xffu);
-                const uint4 *pa = reinterpret_cast<const uint4 *>(prof + ta * SLOT + k * 16);
-                const uint4 *pb = reinterpret_cast<const uint4 *>(prof + tb * SLOT + k * 16);
-                uint32_t wa[R / 4], wb[R / 4];
-#pragma unroll
-                for (int v = 0; v < R / 16; ++v) {
-                    const uint4 x = pa[v * T];
-                    const uint4 y = pb[v * T];
-                    wa[4 * v + 0] = x.x; wa[4 * v + 1] = x.y; wa[4 * v + 2] = x.z; wa[4 * v + 3] = x.w;
-                    wb[4 * v + 0] = y.x; wb[4 * v + 1] = y.y; wb[4 * v + 2] = y.z; wb[4 * v + 3] = y.w;
-                }
-                if (R % 16) {                     // last group of 8 rows: an 8-byte load
-                    const uint2 x = *reinterpret_cast<const uint2 *>(pa + (R / 16) * T);
-                    const uint2 y = *reinterpret_cast<const uint2 *>(pb + (R / 16) * T);
-                    wa[R / 4 - 2] = x.x; wa[R / 4 - 1] = x.y;
-                    wb[R / 4 - 2] = y.x; wb[R / 4 - 1] = y.y;
-                }
-                uint32_t f = fin;
-                uint32_t d = hd;
-                uint32_t yprev = 0;
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const uint32_t pr = prmt(wa[r / 4], wb[r / 4], pair_sel(r % 4));
-                    const uint32_t e_r = __viaddmax_u16x2(E[r], ADD_NEG_E, Ho[r]);
-                    const uint32_t x = __viaddmax_u16x2(d, pr, e_r);
-                    const uint32_t y = __vimax3_u16x2(f, x, BZERO2);
-                    const uint32_t ho = y - OO;
-                    f = __viaddmax_u16x2(f, ADD_NEG_E, ho);
-                    d = Ho[r];
-                    E[r] = e_r;
-                    Ho[r] = ho;
-                    if (r & 1) mx = __vimax3_u16x2(mx, yprev, y);
-                    yprev = y;
-                }
-                hd = hin;
-                pub_h = Ho[R - 1];
-                pub_f = f;
-                pub_c = cin;
+                cells(hin, fin, cin);
                 if (k == T - 1) {
                     if (to_ring)
-                        ring_out[(g_out % D) * C + (j31 % C)] = make_uint2(Ho[R - 1], f);
+                        ring_out[(g_out % D) * C + (j31 % C)] = make_uint2(pub_h, pub_f);
                     else if (to_global)
-                        gbnd2[size_t(j31 >> 2) * (kBundlePairs * 4) + (j31 & 3)] = make_uint2(Ho[R - 1], f);
+                        gbnd2[j31] = make_uint2(pub_h, pub_f);
                 }
             }
             // Release a consumed chunk (lane 0 has used its last column) and
@@ -311,17 +328,84 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
                 ++g_out;
             }
         };
-        using FalseC = std::integral_constant<bool, false>;
-        using TrueC = std::integral_constant<bool, true>;
+
+        // One steady column step (every lane inside the sequence), U = s % 4:
+        // lane 0 takes its inputs from the broadcast loads ib[U] (boundary
+        // value) and quad (codes); lane 31 writes its bottom row to ob[U].
+        auto sstep = [&](const uint2 *ib, uint2 *ob, auto u_c) {
+            constexpr int U = decltype(u_c)::value;
+            uint32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1, T);
+            uint32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1, T);
+            uint32_t cin = __shfl_up_sync(0xffffffffu, pub_c, 1, T);
+            const uint2 v = ib[U];
+            const uint32_t wd = (U & 2) ? quad.y : quad.x;
+            const uint32_t c0 = (U & 1) ? (wd >> 16) : (wd & 0xffffu);
+            const bool lane0 = k == 0;
+            hin = lane0 ? v.x : hin;
+            fin = lane0 ? v.y : fin;
+            cin = lane0 ? c0 : cin;
+            cells(hin, fin, cin);
+            if (ob != nullptr && k == T - 1) ob[U] = make_uint2(pub_h, pub_f);
+        };
+        using U0 = std::integral_constant<int, 0>;
+        using U1 = std::integral_constant<int, 1>;
+        using U2 = std::integral_constant<int, 2>;
+        using U3 = std::integral_constant<int, 3>;
+
         int s = 0;
-        for (; s < 32 && s < steps; ++s) step(s, FalseC(), std::integral_constant<int, -1>());
+        for (; s < T && s < steps; ++s) step(s);
+        // Steady groups of four columns: s % 4 == 0, s >= 32 (lane 31 started),
+        // s + 3 < Lp (lane 0 inside).  A ring chunk starts at s % 64 == 0 (wait
+        // for it) and ends at s % 64 == 63 or at the last column (release it);
+        // lane 31, 31 columns behind, ends an output chunk at s % 64 == 30
+        // (publish it) and starts the next at s % 64 == 31 (wait for space):
+        // both fall in the group at s % 64 == 28.  Lane 31's last partial chunk
+        // ends at s = Lp + 30, in the tail.
         for (; s + 3 < Lp; s += 4) {
-            step(s, TrueC(), std::integral_constant<int, 0>());
-            step(s + 1, TrueC(), std::integral_constant<int, 1>());
-            step(s + 2, TrueC(), std::integral_constant<int, 2>());
-            step(s + 3, TrueC(), std::integral_constant<int, 3>());
+            const int g64 = s & (C - 1);
+            const uint2 *ib;
+            if (from_ring) {
+                if (g64 == 0) wait_flag(full_in, g_in + 1, abort_flag, a.status);
+                ib = ring_in + (g_in % D) * C + g64;
+            } else if (from_global) {
+                cp_async_wait1();                            // the group for columns s..s+3 has landed
+                ib = stg + ((s >> 2) & 1) * 4;
+            } else {
+                ib = top4;
+            }
+            quad = quad_next;
+            if (s + 4 < Lp) quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
+            uint2 *ob = nullptr;
+            if (to_ring) ob = ring_out + (g_out % D) * C + ((g64 - (T - 1)) & (C - 1));
+            else if (to_global) ob = gbnd2 + (s - (T - 1));
+            sstep(ib, ob, U0());
+            sstep(ib, ob, U1());
+            sstep(ib, ob, U2());
+            if (to_ring && g64 == 28) {
+                __syncwarp();
+                if (k == T - 1) st_release(full_out, g_out + 1);
+                ++g_out;
+                wait_flag(empty_out, g_out - D + 1, abort_flag, a.status);
+                ob = ring_out + (g_out % D) * C - 3;         // ob[3]: column 0 of the new chunk
+            }
+            sstep(ib, ob, U3());
+            if (from_global) {
+                if (k == 0 && s + 5 < Lp) {
+                    const uint4 *g = gsrc + size_t((s >> 2) + 2) * 2;
+                    cp_async16(stg + ((s >> 2) & 1) * 4, g);
+                    cp_async16(stg + ((s >> 2) & 1) * 4 + 2, g + 1);
+                }
+                cp_async_commit();
+            }
+            // lane 0 has used the chunk's last column (s % 64 == 63, or the
+            // sequence's last column: Lp is a multiple of 4, so the last steady
+            // group ends the sequence when Lp >= 36)
+            if (from_ring && (g64 == C - 4 || s + 4 == Lp)) {
+                if (k == 0) st_release(empty_in, g_in + 1);
+                ++g_in;
+            }
         }
-        for (; s < steps; ++s) step(s, FalseC(), std::integral_constant<int, -1>());
+        for (; s < steps; ++s) step(s);
     }
 
 #pragma unroll
