@@ -78,11 +78,13 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_inter_i16x2(
     __shared__ __align__(16) uint2 bstage[PAIRS_PER_CTA][8];
 
     __shared__ int sh_chunk;
+    __shared__ uint2 top4[4];            // the top row's inputs B(H-o), B(F) = B(-o), for broadcast reads
 
     const int tid = threadIdx.x;
     const int k = tid % T;               // lane within the subwarp
     const int sub = tid / T;             // subwarp within the CTA
     for (int i = tid; i < kProfRows * kProfRows; i += kCtaThreads) mat[i] = (&a.prof8[0][0])[i];
+    if (tid < 4) top4[tid] = make_uint2(pack2(32768 - a.gap_open), pack2(32768 - a.gap_open));
     const int n_chunks = int((a.pair_end - a.pair_begin + PAIRS_PER_CTA - 1) / PAIRS_PER_CTA);
 
   for (;;) {
@@ -184,33 +186,77 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_inter_i16x2(
         // global-load latency stays off the per-column critical path.
         uint2 quad = make_uint2(0, 0), quad_next = make_uint2(0, 0);
         uint2 *stg = bstage[sub];
-        if (k == 0 && Lp > 0) {
-            quad_next = __ldg(cptr);
-            if (pass > 0) {
-                cp_async16(stg + 0, bnd);
-                cp_async16(stg + 2, bnd + 1);
-                cp_async_commit();
-                if (4 < Lp) {
-                    cp_async16(stg + 4, bnd + gstride);
-                    cp_async16(stg + 6, bnd + gstride + 1);
-                }
-                cp_async_commit();
+        if (Lp > 0) quad_next = __ldg(cptr);     // every lane of the subwarp: one broadcast load
+        if (k == 0 && Lp > 0 && pass > 0) {
+            cp_async16(stg + 0, bnd);
+            cp_async16(stg + 2, bnd + 1);
+            cp_async_commit();
+            if (4 < Lp) {
+                cp_async16(stg + 4, bnd + gstride);
+                cp_async16(stg + 6, bnd + gstride + 1);
             }
+            cp_async_commit();
         }
 
-        // One column step of the subwarp.  STEADY: every lane of every subwarp
-        // of the warp is inside its sequence (no predicates) and U = s % 4 is a
-        // compile-time constant, so lane 0's code and boundary selects fold away.
-        auto step = [&](const int s, auto steady_c, auto u_c) {
-            constexpr bool STEADY = decltype(steady_c)::value;
-            constexpr int U = decltype(u_c)::value;
+        // Lane T-1's store of the strip's bottom row (H - o, F) at column jl;
+        // 4 consecutive columns fill one 32-byte sector.
+        auto bottom_index = [&](const int jl) -> size_t {
+            if (SLOTS) return size_t(jl);                           // per subwarp, [column]
+            return size_t(jl >> 2) * (gstride * 2) + (jl & 3);      // [column/4][slot][column%4]
+        };
+
+        // The cell work of one column step for this lane's R rows.
+        auto cells = [&](const uint32_t hin, const uint32_t fin, const uint32_t cin) {
+            const int ta = int(cin & 0xffu), tb = int((cin >> 8) & 0xffu);
+            const uint4 *pa = reinterpret_cast<const uint4 *>(prof + ta * SLOT + k * 16);
+            const uint4 *pb = reinterpret_cast<const uint4 *>(prof + tb * SLOT + k * 16);
+            uint32_t wa[R / 4], wb[R / 4];
+#pragma unroll
+            for (int v = 0; v < R / 16; ++v) {
+                const uint4 x = pa[v * T];
+                const uint4 y = pb[v * T];
+                wa[4 * v + 0] = x.x; wa[4 * v + 1] = x.y; wa[4 * v + 2] = x.z; wa[4 * v + 3] = x.w;
+                wb[4 * v + 0] = y.x; wb[4 * v + 1] = y.y; wb[4 * v + 2] = y.z; wb[4 * v + 3] = y.w;
+            }
+            if (R % 16) {                     // last group of 8 rows: an 8-byte load
+                const uint2 x = *reinterpret_cast<const uint2 *>(pa + (R / 16) * T);
+                const uint2 y = *reinterpret_cast<const uint2 *>(pb + (R / 16) * T);
+                wa[R / 4 - 2] = x.x; wa[R / 4 - 1] = x.y;
+                wb[R / 4 - 2] = y.x; wb[R / 4 - 1] = y.y;
+            }
+            uint32_t f = fin;                 // B(F) of this lane's top row
+            uint32_t d = hd;
+            uint32_t yprev = 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const uint32_t p = prmt(wa[r / 4], wb[r / 4], pair_sel(r % 4));
+                const uint32_t e_r = __viaddmax_u16x2(E[r], ADD_NEG_E, Ho[r]);
+                const uint32_t x = __viaddmax_u16x2(d, p, e_r);
+                const uint32_t y = __vimax3_u16x2(f, x, BZERO2);   // B(H)
+                const uint32_t ho = y - OO;                         // B(H - o), no borrow: y >= 0x8000
+                f = __viaddmax_u16x2(f, ADD_NEG_E, ho);           // B(F) of the row below
+                d = Ho[r];
+                E[r] = e_r;
+                Ho[r] = ho;
+                if (r & 1) mx = __vimax3_u16x2(mx, yprev, y);
+                yprev = y;
+            }
+            hd = hin;
+            pub_h = Ho[R - 1];
+            pub_f = f;
+            pub_c = cin;
+        };
+
+        // One column step of the subwarp with every check (lanes starting or
+        // finishing): the first and last columns.
+        auto step = [&](const int s) {
             uint32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1, T);
             uint32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1, T);
             uint32_t cin = __shfl_up_sync(0xffffffffu, pub_c, 1, T);
             const int j = s - k;
-            const bool act = STEADY || ((j >= 0) && (j < Lp));
+            const bool act = (j >= 0) && (j < Lp);
             if (k == 0 && act) {
-                const int s3 = STEADY ? U : (s & 3);
+                const int s3 = s & 3;
                 if (s3 == 0) {
                     quad = quad_next;
                     if (s + 4 < Lp) quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
@@ -236,66 +282,63 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_inter_i16x2(
                 }
             }
             if (act) {
-                const int ta = int(cin & 0xffu), tb = int((cin >> 8) & 0xffu);
-                const uint4 *pa = reinterpret_cast<const uint4 *>(prof + ta * SLOT + k * 16);
-                const uint4 *pb = reinterpret_cast<const uint4 *>(prof + tb * SLOT + k * 16);
-                uint32_t wa[R / 4], wb[R / 4];
-#pragma unroll
-                for (int v = 0; v < R / 16; ++v) {
-                    const uint4 x = pa[v * T];
-                    const uint4 y = pb[v * T];
-                    wa[4 * v + 0] = x.x; wa[4 * v + 1] = x.y; wa[4 * v + 2] = x.z; wa[4 * v + 3] = x.w;
-                    wb[4 * v + 0] = y.x; wb[4 * v + 1] = y.y; wb[4 * v + 2] = y.z; wb[4 * v + 3] = y.w;
-                }
-                if (R % 16) {                     // last group of 8 rows: an 8-byte load
-                    const uint2 x = *reinterpret_cast<const uint2 *>(pa + (R / 16) * T);
-                    const uint2 y = *reinterpret_cast<const uint2 *>(pb + (R / 16) * T);
-                    wa[R / 4 - 2] = x.x; wa[R / 4 - 1] = x.y;
-                    wb[R / 4 - 2] = y.x; wb[R / 4 - 1] = y.y;
-                }
-                uint32_t f = fin;                 // B(F) of this lane's top row
-                uint32_t d = hd;
-                uint32_t yprev = 0;
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const uint32_t p = prmt(wa[r / 4], wb[r / 4], pair_sel(r % 4));
-                    const uint32_t e_r = __viaddmax_u16x2(E[r], ADD_NEG_E, Ho[r]);
-                    const uint32_t x = __viaddmax_u16x2(d, p, e_r);
-                    const uint32_t y = __vimax3_u16x2(f, x, BZERO2);   // B(H)
-                    const uint32_t ho = y - OO;                         // B(H - o), no borrow: y >= 0x8000
-                    f = __viaddmax_u16x2(f, ADD_NEG_E, ho);           // B(F) of the row below
-                    d = Ho[r];
-                    E[r] = e_r;
-                    Ho[r] = ho;
-                    if (r & 1) mx = __vimax3_u16x2(mx, yprev, y);
-                    yprev = y;
-                }
-                hd = hin;
-                pub_h = Ho[R - 1];
-                pub_f = f;
-                pub_c = cin;
-                if (k == T - 1 && !last_pass) {   // 4 consecutive columns fill one 32-byte sector
-                    const int jl = s - (T - 1);
-                    reinterpret_cast<uint2 *>(bnd)[size_t(jl >> 2) * (gstride * 2) + (jl & 3)] =
-                        make_uint2(Ho[R - 1], f);
-                }
+                cells(hin, fin, cin);
+                if (k == T - 1 && !last_pass)
+                    reinterpret_cast<uint2 *>(bnd)[bottom_index(s - (T - 1))] = make_uint2(pub_h, pub_f);
             }
         };
-        using FalseC = std::integral_constant<bool, false>;
-        using TrueC = std::integral_constant<bool, true>;
+
+        // One steady column step (every lane of the warp inside its sequence),
+        // U = s % 4: lane 0 takes its codes from quad and its top-row inputs
+        // from the broadcast load ib[U] with selects instead of a branch.
+        auto sstep = [&](const int s, const uint2 *ib, auto u_c) {
+            constexpr int U = decltype(u_c)::value;
+            uint32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1, T);
+            uint32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1, T);
+            uint32_t cin = __shfl_up_sync(0xffffffffu, pub_c, 1, T);
+            const uint2 v = ib[U];
+            const uint32_t w = (U & 2) ? quad.y : quad.x;
+            const uint32_t c0 = (U & 1) ? (w >> 16) : (w & 0xffffu);
+            const bool lane0 = k == 0;
+            hin = lane0 ? v.x : hin;
+            fin = lane0 ? v.y : fin;
+            cin = lane0 ? c0 : cin;
+            cells(hin, fin, cin);
+            if (k == T - 1 && !last_pass)
+                reinterpret_cast<uint2 *>(bnd)[bottom_index(s + U - (T - 1))] = make_uint2(pub_h, pub_f);
+        };
+        using U0 = std::integral_constant<int, 0>;
+        using U1 = std::integral_constant<int, 1>;
+        using U2 = std::integral_constant<int, 2>;
+        using U3 = std::integral_constant<int, 3>;
         // Steady columns: s >= T-1 (every lane started) and s + 3 < Lmin (no lane
         // of any subwarp in the warp has finished), in groups of 4 aligned to s % 4 == 0.
         const int Lmin = __reduce_min_sync(0xffffffffu, Lp);
         const int s_steady = (T + 2) & ~3;
         int s = 0;
-        for (; s < s_steady && s < steps; ++s) step(s, FalseC(), std::integral_constant<int, -1>());
+        for (; s < s_steady && s < steps; ++s) step(s);
         for (; s + 3 < Lmin; s += 4) {
-            step(s, TrueC(), std::integral_constant<int, 0>());
-            step(s + 1, TrueC(), std::integral_constant<int, 1>());
-            step(s + 2, TrueC(), std::integral_constant<int, 2>());
-            step(s + 3, TrueC(), std::integral_constant<int, 3>());
+            quad = quad_next;
+            if (s + 4 < Lp) quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
+            const uint2 *ib = top4;
+            if (pass > 0) {
+                cp_async_wait1();                              // group s/4 has landed
+                ib = stg + ((s >> 2) & 1) * 4;
+            }
+            sstep(s, ib, U0());
+            sstep(s, ib, U1());
+            sstep(s, ib, U2());
+            sstep(s, ib, U3());
+            if (pass > 0) {                                    // fetch group s/4 + 2 into the freed half
+                if (k == 0 && s + 5 < Lp) {
+                    const uint4 *g = bnd + size_t((s >> 2) + 2) * gstride;
+                    cp_async16(stg + ((s >> 2) & 1) * 4, g);
+                    cp_async16(stg + ((s >> 2) & 1) * 4 + 2, g + 1);
+                }
+                cp_async_commit();
+            }
         }
-        for (; s < steps; ++s) step(s, FalseC(), std::integral_constant<int, -1>());
+        for (; s < steps; ++s) step(s);
     }
 
 #pragma unroll
