@@ -42,11 +42,13 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_batch_i16x2(
     __shared__ __align__(16) uint2 bstage[SPC][8];
     __shared__ int sh_tile;
     __shared__ int sh_mask[SPC / 2];
+    __shared__ uint2 top4[4];        // the top row's inputs B(H-o), B(F) = B(-o), for broadcast reads
 
     const int tid = threadIdx.x;
     const int k = tid % T;
     const int sub = tid / T;
     for (int i = tid; i < kProfRows * kProfRows; i += kCtaThreads) mat[i] = (&a.prof8[0][0])[i];
+    if (tid < 4) top4[tid] = make_uint2(pack2(32768 - a.gap_open), pack2(32768 - a.gap_open));
 
     const int o = a.gap_open;
     const uint32_t BNEG_O2 = pack2(32768 - o);
@@ -129,32 +131,60 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_batch_i16x2(
             uint2 quad = make_uint2(0, 0), quad_next = make_uint2(0, 0);
             uint2 *stg = bstage[sub];
             const uint4 *gsrc = reinterpret_cast<const uint4 *>(slot_scratch);
-            if (k == 0 && Lp > 0) {
-                quad_next = __ldg(cptr);
-                if (pass > 0) {
-                    cp_async16(stg + 0, gsrc);
-                    cp_async16(stg + 2, gsrc + 1);
-                    cp_async_commit();
-                    if (4 < Lp) {
-                        cp_async16(stg + 4, gsrc + 2);
-                        cp_async16(stg + 6, gsrc + 3);
-                    }
-                    cp_async_commit();
+            if (Lp > 0) quad_next = __ldg(cptr);     // every lane of the subwarp: one broadcast load
+            if (k == 0 && Lp > 0 && pass > 0) {
+                cp_async16(stg + 0, gsrc);
+                cp_async16(stg + 2, gsrc + 1);
+                cp_async_commit();
+                if (4 < Lp) {
+                    cp_async16(stg + 4, gsrc + 2);
+                    cp_async16(stg + 6, gsrc + 3);
                 }
+                cp_async_commit();
             }
             const int steps = Lw + T - 1;
-            // One column step; STEADY: all lanes of the warp inside their sequences,
-            // U = s % 4 known at compile time (see k_inter16.cu).
-            auto step = [&](const int s, auto steady_c, auto u_c) {
-                constexpr bool STEADY = decltype(steady_c)::value;
-                constexpr int U = decltype(u_c)::value;
+
+            // The cell work of one column step for this lane's R rows (both
+            // queries of the pair in the two halves; cin = the sequence's code).
+            auto cells = [&](const uint32_t hin, const uint32_t fin, const uint32_t cin) {
+                const uint4 *pp = reinterpret_cast<const uint4 *>(prof + cin * TR + k * 4);
+                uint32_t P[R];
+#pragma unroll
+                for (int v = 0; v < R / 4; ++v) {
+                    const uint4 x = pp[v * T];
+                    P[4 * v + 0] = x.x; P[4 * v + 1] = x.y; P[4 * v + 2] = x.z; P[4 * v + 3] = x.w;
+                }
+                uint32_t f = fin;
+                uint32_t d = hd;
+                uint32_t yprev = 0;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t e_r = __viaddmax_u16x2(E[r], ADD_NEG_E, Ho[r]);
+                    const uint32_t x = __viaddmax_u16x2(d, P[r], e_r);
+                    const uint32_t y = __vimax3_u16x2(f, x, BZERO2);
+                    const uint32_t ho = y - OO;
+                    f = __viaddmax_u16x2(f, ADD_NEG_E, ho);
+                    d = Ho[r];
+                    E[r] = e_r;
+                    Ho[r] = ho;
+                    if (r & 1) mx = __vimax3_u16x2(mx, yprev, y);
+                    yprev = y;
+                }
+                hd = hin;
+                pub_h = Ho[R - 1];
+                pub_f = f;
+                pub_c = cin;
+            };
+
+            // One column step with every check (lanes starting or finishing).
+            auto step = [&](const int s) {
                 uint32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1, T);
                 uint32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1, T);
                 uint32_t cin = __shfl_up_sync(0xffffffffu, pub_c, 1, T);
                 const int j = s - k;
-                const bool act = STEADY || ((j >= 0) && (j < Lp));
+                const bool act = (j >= 0) && (j < Lp);
                 if (k == 0 && act) {
-                    const int s3 = STEADY ? U : (s & 3);
+                    const int s3 = s & 3;
                     if (s3 == 0) {
                         quad = quad_next;
                         if (s + 4 < Lp) quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
@@ -180,49 +210,59 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_batch_i16x2(
                     }
                 }
                 if (act) {
-                    const uint4 *pp = reinterpret_cast<const uint4 *>(prof + cin * TR + k * 4);
-                    uint32_t P[R];
-#pragma unroll
-                    for (int v = 0; v < R / 4; ++v) {
-                        const uint4 x = pp[v * T];
-                        P[4 * v + 0] = x.x; P[4 * v + 1] = x.y; P[4 * v + 2] = x.z; P[4 * v + 3] = x.w;
-                    }
-                    uint32_t f = fin;
-                    uint32_t d = hd;
-                    uint32_t yprev = 0;
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const uint32_t e_r = __viaddmax_u16x2(E[r], ADD_NEG_E, Ho[r]);
-                        const uint32_t x = __viaddmax_u16x2(d, P[r], e_r);
-                        const uint32_t y = __vimax3_u16x2(f, x, BZERO2);
-                        const uint32_t ho = y - OO;
-                        f = __viaddmax_u16x2(f, ADD_NEG_E, ho);
-                        d = Ho[r];
-                        E[r] = e_r;
-                        Ho[r] = ho;
-                        if (r & 1) mx = __vimax3_u16x2(mx, yprev, y);
-                        yprev = y;
-                    }
-                    hd = hin;
-                    pub_h = Ho[R - 1];
-                    pub_f = f;
-                    pub_c = cin;
-                    if (k == T - 1 && !last_pass) slot_scratch[s - (T - 1)] = make_uint2(Ho[R - 1], f);
+                    cells(hin, fin, cin);
+                    if (k == T - 1 && !last_pass) slot_scratch[s - (T - 1)] = make_uint2(pub_h, pub_f);
                 }
             };
-            using FalseC = std::integral_constant<bool, false>;
-            using TrueC = std::integral_constant<bool, true>;
+
+            // One steady column step (every lane of the warp inside its
+            // sequence), U = s % 4: lane 0 takes its code from quad and its
+            // top-row inputs from the broadcast load ib[U] by select.
+            auto sstep = [&](const int s, const uint2 *ib, auto u_c) {
+                constexpr int U = decltype(u_c)::value;
+                uint32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1, T);
+                uint32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1, T);
+                uint32_t cin = __shfl_up_sync(0xffffffffu, pub_c, 1, T);
+                const uint2 v = ib[U];
+                const uint32_t wd = (U & 2) ? quad.y : quad.x;
+                const uint32_t c0 = (wd >> (16 * (U & 1) + 8 * h)) & 0xffu;
+                const bool lane0 = k == 0;
+                hin = lane0 ? v.x : hin;
+                fin = lane0 ? v.y : fin;
+                cin = lane0 ? c0 : cin;
+                cells(hin, fin, cin);
+                if (k == T - 1 && !last_pass) slot_scratch[s + U - (T - 1)] = make_uint2(pub_h, pub_f);
+            };
+            using U0 = std::integral_constant<int, 0>;
+            using U1 = std::integral_constant<int, 1>;
+            using U2 = std::integral_constant<int, 2>;
+            using U3 = std::integral_constant<int, 3>;
             const int Lmin = __reduce_min_sync(0xffffffffu, Lp);
             const int s_steady = (T + 2) & ~3;
             int s = 0;
-            for (; s < s_steady && s < steps; ++s) step(s, FalseC(), std::integral_constant<int, -1>());
+            for (; s < s_steady && s < steps; ++s) step(s);
             for (; s + 3 < Lmin; s += 4) {
-                step(s, TrueC(), std::integral_constant<int, 0>());
-                step(s + 1, TrueC(), std::integral_constant<int, 1>());
-                step(s + 2, TrueC(), std::integral_constant<int, 2>());
-                step(s + 3, TrueC(), std::integral_constant<int, 3>());
+                quad = quad_next;
+                if (s + 4 < Lp) quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
+                const uint2 *ib = top4;
+                if (pass > 0) {
+                    cp_async_wait1();                          // group s/4 has landed
+                    ib = stg + ((s >> 2) & 1) * 4;
+                }
+                sstep(s, ib, U0());
+                sstep(s, ib, U1());
+                sstep(s, ib, U2());
+                sstep(s, ib, U3());
+                if (pass > 0) {                                // fetch group s/4 + 2 into the freed half
+                    if (k == 0 && s + 5 < Lp) {
+                        const uint4 *g = gsrc + size_t((s >> 2) + 2) * 2;
+                        cp_async16(stg + ((s >> 2) & 1) * 4, g);
+                        cp_async16(stg + ((s >> 2) & 1) * 4 + 2, g + 1);
+                    }
+                    cp_async_commit();
+                }
             }
-            for (; s < steps; ++s) step(s, FalseC(), std::integral_constant<int, -1>());
+            for (; s < steps; ++s) step(s);
         }
 
 #pragma unroll
