@@ -514,8 +514,8 @@ def tune(db, w, forms=("plain", "batched"), sample_queries: int = 8, cutoffs=(0,
     r = autotune.last_result()
     fmt = lambda rows: [{"lanes": l, "rows": rr, "gcups": round(g, 1)} for l, rr, g in rows]
     return {"params": params, "plain_shapes": fmt(r["tuning"]["plain"]), "batched_shapes": fmt(r["tuning"]["batched"]),
-            "tried": r["tried"], "tune_seconds": r["tune_seconds"],
-            "how": "shape rates: median CUDA-event kernel rate of a 3,072-residue query cut from the batch "
+            "tried": r["tried"], "tune_seconds": r["tune_seconds"], "probe_rows": r.get("probe_rows"),
+            "how": "shape rates: median CUDA-event kernel rate of a probe query cut from the batch "
                    f"(pairs of them for the batched kernel); cutoff and form: median whole-search time of "
                    f"{sample_queries} queries spread over the batch's lengths"}
 
@@ -830,7 +830,7 @@ def run_serving(args, dist: Dist):
     if want_autotune(args, True):
         sample = synth.Workload("serving sample", synth.seqset_from_list([reqs.seq(i) for i in range(64)]), dbs, S,
                                 10, 1, 10)
-        tuned = tune(db, sample, forms=("batched",))
+        tuned = tune(db, sample, forms=("batched",), sample_queries=4)
         launch = {"long_cutoff": tuned["params"]["long_cutoff"]}
 
     def new_server():

@@ -20,7 +20,10 @@ several repeats after a warm-up):
 - shape rates: a query of 3,072 residues taken from the batch itself (a
   whole number of strips of every shape, so no padding enters the rate)
   against the whole resident database, one search per candidate shape,
-  rate = the scoring kernel's cells / its event time;
+  rate = the scoring kernel's cells / its event time; on a database so large
+  that one such search would exceed about 2e12 cells the query is halved (to
+  1,536 or 768 rows) and the shapes whose strip does not divide it are left
+  out;
 - cutoff and form: the whole search of a sample of the batch (queries spread
   over its length range), bracketed by CUDA events on its stream.
 
@@ -47,6 +50,15 @@ PLAIN_SHAPES = ((8, 16), (16, 16), (32, 16), (8, 24), (8, 32), (16, 32), (32, 32
 BATCH_SHAPES = ((8, 16), (8, 24), (8, 32), (16, 16), (16, 24), (16, 32))
 CUTOFFS = (0, 1024, 2048, 3072, 6144)   # 0: the library's balanced default for this database
 RATE_ROWS = 3072          # a whole number of strips of every candidate shape
+MAX_PROBE_CELLS = 2e12    # cells of one rate-probe search (about a third of a second)
+
+
+def probe_rows(residues: int) -> int:
+    """Rows of the rate-probe query for a database of this many residues."""
+    rows = RATE_ROWS
+    while rows > 768 and float(residues) * rows > MAX_PROBE_CELLS:
+        rows //= 2
+    return rows
 
 
 def _device_key(device: int) -> str:
@@ -169,8 +181,11 @@ def autotune(db, queries, q_offsets, matrix, gap_open: int, gap_extend: int, top
     t_start = time.perf_counter()
     binding.sw_db_set_tuning(db.handle, None)
     tuning = {"plain": [], "batched": [], "long_cutoff": 0, "long_rows_per_lane": 0, "mode": 0}
+    rows = probe_rows(info["residues"])
+    plain_shapes = [x for x in plain_shapes if rows % (x[0] * x[1]) == 0]
+    batch_shapes = [x for x in batch_shapes if rows % (x[0] * x[1]) == 0]
     if prec == binding.SW_PREC_I16:
-        one_res, one_off = _probe_queries(queries, 1)
+        one_res, one_off = _probe_queries(queries, 1, rows)
         for (l, r) in plain_shapes:
             try:
                 g = _median_rate(db, one_res, one_off, matrix, gap_open, gap_extend, stream, repeats,
@@ -180,7 +195,7 @@ def autotune(db, queries, q_offsets, matrix, gap_open: int, gap_extend: int, top
             if g > 0:
                 tuning["plain"].append((l, r, g))
         if "batched" in forms:
-            two_res, two_off = _probe_queries(queries, 2)
+            two_res, two_off = _probe_queries(queries, 2, rows)
             for (l, r) in batch_shapes:
                 try:
                     g = _median_rate(db, two_res, two_off, matrix, gap_open, gap_extend, stream, repeats,
@@ -213,7 +228,7 @@ def autotune(db, queries, q_offsets, matrix, gap_open: int, gap_extend: int, top
     binding.sw_db_set_tuning(db.handle, tuning)
     cells = int(np.diff(s_off).sum()) * info["residues"]
     params = {"mode": tuning["mode"], "long_cutoff": tuning["long_cutoff"]}
-    entry = {"params": params, "tuning": tuning, "sample_cells": cells,
+    entry = {"params": params, "tuning": tuning, "sample_cells": cells, "probe_rows": rows,
              "sample_gcups": cells / (best["ms"] * 1e-3) / 1e9 if best["ms"] > 0 else 0.0,
              "tried": tried, "tune_seconds": time.perf_counter() - t_start}
     if cache_path:

@@ -47,7 +47,10 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_batch_i16x2(
     const int tid = threadIdx.x;
     const int k = tid % T;
     const int sub = tid / T;
-    for (int i = tid; i < kProfRows * kProfRows; i += kCtaThreads) mat[i] = (&a.prof8[0][0])[i];
+    // staged transposed, [db code][query code]: the profile fill reads one db code
+    // against many query codes at once, which then fall in distinct banks
+    for (int i = tid; i < kProfRows * kProfRows; i += kCtaThreads)
+        mat[(i % kProfRows) * kProfRows + i / kProfRows] = (&a.prof8[0][0])[i];
     if (tid < 4) top4[tid] = make_uint2(pack2(32768 - a.gap_open), pack2(32768 - a.gap_open));
 
     const int o = a.gap_open;
@@ -111,11 +114,11 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_batch_i16x2(
                 int lo = -128, hi = -128;
                 if (row < ma) {
                     const int c = a.queries[qa0 + row];
-                    if (c < kProfRows) lo = mat[c * kProfRows + res];
+                    if (c < kProfRows) lo = mat[res * kProfRows + c];
                 }
                 if (row < mb) {
                     const int c = a.queries[qb0 + row];
-                    if (c < kProfRows) hi = mat[c * kProfRows + res];
+                    if (c < kProfRows) hi = mat[res * kProfRows + c];
                 }
                 prof[w] = (uint32_t(lo) & 0xffffu) | (uint32_t(hi) << 16);
             }

@@ -120,7 +120,10 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
     int32_t *scores = a.scores + int64_t(q) * a.db.n_seqs;
     int32_t *ovf_list = a.ovf_list + int64_t(q) * a.list_stride;
 
-    for (int i = threadIdx.x; i < kProfRows * kProfRows; i += NT) mat[i] = (&a.prof8[0][0])[i];
+    // staged transposed, [db code][query code]: the profile fill reads one db code
+    // against many query codes at once, which then fall in distinct banks
+    for (int i = threadIdx.x; i < kProfRows * kProfRows; i += NT)
+        mat[(i % kProfRows) * kProfRows + i / kProfRows] = (&a.prof8[0][0])[i];
     if (threadIdx.x < P * NW) {
         full[threadIdx.x] = 0;
         empty[threadIdx.x] = 0;
@@ -185,7 +188,7 @@ __global__ void __launch_bounds__(NW * P * 32, 2) k_intra_i16x2(const __grid_con
                 int v = -128;
                 if (row < m) {
                     const int qc = query[row];
-                    if (qc < kProfRows) v = mat[qc * kProfRows + res];
+                    if (qc < kProfRows) v = mat[res * kProfRows + qc];
                 }
                 word |= (uint32_t(uint8_t(int8_t(v)))) << (8 * c);
             }

@@ -87,7 +87,10 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_modes_i16x2(
     const int tid = threadIdx.x;
     const int k = tid % T;               // lane within the subwarp
     const int sub = tid / T;             // subwarp within the CTA
-    for (int i = tid; i < kProfRows * kProfRows; i += kCtaThreads) mat[i] = (&a.prof8[0][0])[i];
+    // staged transposed, [db code][query code]: the profile fill reads one db code
+    // against many query codes at once, which then fall in distinct banks
+    for (int i = tid; i < kProfRows * kProfRows; i += kCtaThreads)
+        mat[(i % kProfRows) * kProfRows + i / kProfRows] = (&a.prof8[0][0])[i];
     const int n_chunks = int((a.pair_end - a.pair_begin + PAIRS_PER_CTA - 1) / PAIRS_PER_CTA);
     const int o = a.gap_open;
     const int gmin = min(a.gap_open, a.gap_extend);
@@ -159,7 +162,7 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_modes_i16x2(
                             // device-resident queries are not validated on the host:
                             // codes outside the table score as padding
                             const int qc = a.query[row];
-                            if (qc < kProfRows) v = mat[qc * kProfRows + res_code];
+                            if (qc < kProfRows) v = mat[res_code * kProfRows + qc];
                         }
                     }
                     word |= (uint32_t(uint8_t(int8_t(v)))) << (8 * c);

@@ -43,3 +43,10 @@ def test_probe_queries_are_whole_strips_of_the_batch():
     assert len(q) == 2 * autotune.RATE_ROWS and np.array_equal(q[:100], res)
     for lanes, rows in autotune.PLAIN_SHAPES + autotune.BATCH_SHAPES:
         assert autotune.RATE_ROWS % (lanes * rows) == 0
+
+
+def test_probe_rows_shrink_for_huge_databases():
+    assert autotune.probe_rows(200_000_000) == 3072          # the default workload's database
+    assert autotune.probe_rows(1_000_000_000) == 1536
+    assert autotune.probe_rows(7_200_000_000) == 768          # the 20M-sequence serving database
+    assert autotune.probe_rows(10**12) == 768
