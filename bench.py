@@ -658,6 +658,9 @@ def run_sub_records(args, names, db_main, w_main, rate_dpx: float, sms: int, dev
                                        " (intra-task kernel: long sequences, on the side stream)")
                 roof["inter_task"] = kernel_roofline(st_all, "inter", "k_inter_i16x2", DPX_OPS_PER_CELL,
                                                      rate_dpx, sms, mhz)
+                # the two launches share the SMs for most of the step, so each one's
+                # event time includes the other's work: the whole step against the peak
+                roof["both_kernels_frac_of_peak"] = cells * steps / (ms * 1e-3) / 1e9 / roof["peak"]
             elif form == "batched":
                 roof = kernel_roofline(st_all, "inter", "k_batch_i16x2", BATCH_OPS_PER_CELL, rate_dpx, sms, mhz,
                                        " (query pairs: one ready int16x2 profile word per row, no permute)")

@@ -72,7 +72,9 @@ typedef enum {
 typedef enum {
     SW_MODE_AUTO = 0,    /* library choice */
     SW_MODE_PLAIN = 1,   /* one kernel launch per query (the paper's form) */
-    SW_MODE_BATCHED = 2  /* all queries in one persistent launch */
+    SW_MODE_BATCHED = 2  /* all queries in one persistent launch (two queries per int16x2
+                            word; a search with a single non-empty query, which has nothing
+                            to pair with, runs in the plain form) */
 } sw_mode;
 
 /* Which alignment score sw_search computes.  Section 2.2 defines the local
@@ -122,7 +124,8 @@ typedef struct {
                                  scored by one subwarp then never outlasts the launch) */
     int32_t lanes;            /* lanes per database-sequence pair in the inter-task kernel
                                  (4, 8, 16 or 32); 0 = chosen per query by the library */
-    int32_t rows_per_lane;    /* query rows held per lane (16, 24 or 32; 8 with 32 lanes);
+    int32_t rows_per_lane;    /* query rows held per lane (16, 24 or 32; 8 with 32 lanes; the
+                                 batched kernel: 16, 24 or 32 with 8 or 16 lanes);
                                  0 = chosen per query */
     void *workspace;          /* caller-owned device scratch, or NULL for the handle's own */
     size_t workspace_bytes;   /* size of workspace */
@@ -309,6 +312,8 @@ int sw_top_k(const int32_t *scores, int64_t n_rows, int64_t n_cols, int32_t top_
  *   mode 2: cell updates per SM cycle of the same recurrence in unsigned
  *           saturating byte SIMD, four sequences per 32-bit word (the
  *           int8x4 lane packing, measured rather than built)
+ *   mode 3: cell updates per SM cycle of the mode-1 sequence with two
+ *           columns per step (two F chains in flight per lane)
  * Writes the rate to *per_sm_cycle and the SM count to *sm_count.
  */
 int sw_probe_alu_rate(int device, int32_t mode, double *per_sm_cycle, int32_t *sm_count);

@@ -454,9 +454,15 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
     const int mode = opts ? opts->mode : SW_MODE_AUTO;
     if (mode < 0 || mode > SW_MODE_BATCHED) return fail(SW_ERR_INVALID_ARG, "unknown mode");
     // The batched kernel is int16x2 only; an int32 search runs in the plain form.
-    // SW_MODE_AUTO takes the handle's tuned form (plain unless tuned otherwise)
+    // SW_MODE_AUTO takes the handle's tuned form (plain unless tuned otherwise).
+    // The batched kernel packs two queries into the int16x2 halves: a search
+    // with a single non-empty query would leave half of every operation empty,
+    // so it runs in the plain form (sequence pairs) instead.
     const int want_mode = mode == SW_MODE_AUTO ? db->tuning.mode : mode;
-    p.mode = (want_mode == SW_MODE_BATCHED && p.precision == SW_PREC_I16) ? SW_MODE_BATCHED : SW_MODE_PLAIN;
+    int32_t nonempty_q = 0;
+    for (int32_t i = 0; i < n_q; ++i) nonempty_q += q_offsets[i + 1] > q_offsets[i];
+    p.mode = (want_mode == SW_MODE_BATCHED && p.precision == SW_PREC_I16 && nonempty_q >= 2) ? SW_MODE_BATCHED
+                                                                                              : SW_MODE_PLAIN;
 
     int lanes = opts && opts->lanes ? opts->lanes : 8;
     int rows = opts && opts->rows_per_lane ? opts->rows_per_lane : 16;
@@ -996,6 +1002,17 @@ int sw_search_workspace_size(const sw_db *db, const int64_t *q_offsets, int32_t 
     Buffers b;
     // Worst case: every buffer carved (host queries / outputs).
     *bytes = carve(db, p, n_q, top_k, false, false, false, nullptr, 0, &b);
+    if (p.mode == SW_MODE_BATCHED) {
+        // a later batch of these sizes with a single non-empty query runs in the
+        // plain form: cover that plan too
+        sw_search_opts plain_opts{};
+        if (opts) plain_opts = *opts;
+        plain_opts.mode = SW_MODE_PLAIN;
+        Plan pp;
+        rc = make_plan(db, q_offsets, n_q, zero.data(), 0, 0, &plain_opts, &pp);
+        if (rc) return rc;
+        *bytes = std::max(*bytes, carve(db, pp, n_q, top_k, false, false, false, nullptr, 0, &b));
+    }
     // Boundary scratch may be needed for either kernel family.
     if (!p.need_boundary) *bytes += size_t(db->codes_bytes) * 4 + 64 + 256;
     return SW_OK;
@@ -1500,7 +1517,7 @@ int sw_probe_wait_timeout(int device, int64_t spin_iters, int32_t *status_out, d
 
 int sw_probe_alu_rate(int device, int32_t mode, double *per_sm_cycle, int32_t *sm_count) {
     g_last_error.clear();
-    if (!per_sm_cycle || !sm_count || mode < 0 || mode > 2) return fail(SW_ERR_INVALID_ARG, "bad argument");
+    if (!per_sm_cycle || !sm_count || mode < 0 || mode > 3) return fail(SW_ERR_INVALID_ARG, "bad argument");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();

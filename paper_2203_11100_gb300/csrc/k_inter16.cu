@@ -407,7 +407,8 @@ int slots_tr(int sms) {
 
 bool inter_config_supported(int lanes, int rows) {
     switch (lanes * 100 + rows) {
-        case 416: case 816: case 1616: case 3216: case 824: case 832: case 1632: case 3232: case 3208: return true;
+        case 416: case 424: case 432: case 816: case 1616: case 3216: case 824: case 832: case 1632: case 3232:
+        case 3208: return true;
         default: return false;
     }
 }
@@ -416,6 +417,8 @@ cudaError_t launch_inter_i16x2(const InterArgs &a, int lanes, int rows, cudaStre
                                int priority) {
     switch (lanes * 100 + rows) {
         case 416: return launch_tr<4, 16>(a, s, grid_slots, priority);
+        case 424: return launch_tr<4, 24>(a, s, grid_slots, priority);
+        case 432: return launch_tr<4, 32>(a, s, grid_slots, priority);
         case 816: return launch_tr<8, 16>(a, s, grid_slots, priority);
         case 824: return launch_tr<8, 24>(a, s, grid_slots, priority);
         case 1616: return launch_tr<16, 16>(a, s, grid_slots, priority);
@@ -431,6 +434,8 @@ cudaError_t launch_inter_i16x2(const InterArgs &a, int lanes, int rows, cudaStre
 int inter_slots(int lanes, int rows, int sms) {
     switch (lanes * 100 + rows) {
         case 416: return slots_tr<4, 16>(sms);
+        case 424: return slots_tr<4, 24>(sms);
+        case 432: return slots_tr<4, 32>(sms);
         case 816: return slots_tr<8, 16>(sms);
         case 824: return slots_tr<8, 24>(sms);
         case 1616: return slots_tr<16, 16>(sms);

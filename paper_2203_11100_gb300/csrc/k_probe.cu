@@ -25,6 +25,10 @@
 #include "simd16.cuh"
 #include "swdb_internal.cuh"
 
+#ifndef PROBE2_ROWS
+#define PROBE2_ROWS 32
+#endif
+
 namespace swdb {
 namespace {
 
@@ -109,6 +113,73 @@ __global__ void k_probe_cells(int iters, uint32_t seed, unsigned long long *cycl
     if (mx == 0x12345678u) sink[0] = mx;
 }
 
+// The shipped sequence with two columns per step: column j's row r and
+// column j+1's row r are computed back to back, so two F chains (one per
+// column) are in flight instead of one; column j+1 reads E and H - o of
+// row r just after column j updated them, and its diagonal is column j's
+// H - o of the row above.
+template <int R>
+__global__ void k_probe_cells2(int iters, uint32_t seed, unsigned long long *cycles, uint32_t *sink) {
+    __shared__ uint4 tab[64];
+    if (threadIdx.x < 64) tab[threadIdx.x] = make_uint4(seed * 3u + threadIdx.x, seed ^ (threadIdx.x * 77u),
+                                                        seed + threadIdx.x * 5u, 0x7f7f0101u ^ threadIdx.x);
+    uint32_t E[R], Ho[R];
+    const uint32_t BNEG_O2 = 0x7ff67ff6u, ADD_NEG_E = 0xffffffffu, OO = 0x000a000au, BZERO2 = 0x80008000u;
+#pragma unroll
+    for (int r = 0; r < R; ++r) { E[r] = BNEG_O2 + r; Ho[r] = BNEG_O2 ^ (seed + r); }
+    uint32_t hin = seed | 0x80008000u, fin = BNEG_O2, hd = BNEG_O2, mx = BZERO2;
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int i = 0; i < iters; i += 2) {
+        uint32_t wa[R / 4], wb[R / 4], wc[R / 4], wd[R / 4];
+#pragma unroll
+        for (int v = 0; v < R / 16; ++v) {
+            const uint4 x = tab[(i + v) & 63];
+            const uint4 y = tab[(i + v + 17) & 63];
+            const uint4 z = tab[(i + v + 29) & 63];
+            const uint4 u = tab[(i + v + 41) & 63];
+            wa[4 * v + 0] = x.x; wa[4 * v + 1] = x.y; wa[4 * v + 2] = x.z; wa[4 * v + 3] = x.w;
+            wb[4 * v + 0] = y.x; wb[4 * v + 1] = y.y; wb[4 * v + 2] = y.z; wb[4 * v + 3] = y.w;
+            wc[4 * v + 0] = z.x; wc[4 * v + 1] = z.y; wc[4 * v + 2] = z.z; wc[4 * v + 3] = z.w;
+            wd[4 * v + 0] = u.x; wd[4 * v + 1] = u.y; wd[4 * v + 2] = u.z; wd[4 * v + 3] = u.w;
+        }
+        uint32_t f0 = fin, f1 = fin ^ 0x10001u;
+        uint32_t d0 = hd, d1 = hin;
+        uint32_t y0prev = 0, y1prev = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t p0 = prmt_p(wa[r / 4], wb[r / 4], pair_sel(r % 4));
+            const uint32_t p1 = prmt_p(wc[r / 4], wd[r / 4], pair_sel(r % 4));
+            // column j, row r
+            const uint32_t e0 = __viaddmax_u16x2(E[r], ADD_NEG_E, Ho[r]);
+            const uint32_t x0 = __viaddmax_u16x2(d0, p0, e0);
+            const uint32_t y0 = __vimax3_u16x2(f0, x0, BZERO2);
+            const uint32_t ho0 = y0 - OO;
+            f0 = __viaddmax_u16x2(f0, ADD_NEG_E, ho0);
+            d0 = Ho[r];
+            // column j + 1, row r
+            const uint32_t e1 = __viaddmax_u16x2(e0, ADD_NEG_E, ho0);
+            const uint32_t x1 = __viaddmax_u16x2(d1, p1, e1);
+            const uint32_t y1 = __vimax3_u16x2(f1, x1, BZERO2);
+            const uint32_t ho1 = y1 - OO;
+            f1 = __viaddmax_u16x2(f1, ADD_NEG_E, ho1);
+            d1 = ho0;
+            E[r] = e1;
+            Ho[r] = ho1;
+            if (r & 1) { mx = __vimax3_u16x2(mx, y0prev, y0); mx = __vimax3_u16x2(mx, y1prev, y1); }
+            y0prev = y0;
+            y1prev = y1;
+        }
+        hd = hin;
+        hin = Ho[R - 1];
+        fin = f0 ^ f1;
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    if (threadIdx.x == 0) atomicMax(cycles, (unsigned long long)(t1 - t0));
+    if (mx == 0x12345678u) sink[0] = mx;
+}
+
 // The recurrence in unsigned saturating byte SIMD: four database sequences
 // per 32-bit word, R rows held in registers (H for the diagonal, H - o for
 // the next column's E, and E).  Each sequence's profile row (four query rows
@@ -175,7 +246,8 @@ cudaError_t launch_probe(int mode, int grid, int iters, unsigned long long *cycl
                          cudaStream_t s) {
     if (mode == 0) k_probe_dpx<<<grid, kCtaThreads, 0, s>>>(iters, 12345u, cycles, sink);
     else if (mode == 1) k_probe_cells<32><<<grid, kCtaThreads, 0, s>>>(iters, 12345u, cycles, sink);
-    else k_probe_cells_u8x4<16><<<grid, kCtaThreads, 0, s>>>(iters, 12345u, cycles, sink);
+    else if (mode == 2) k_probe_cells_u8x4<16><<<grid, kCtaThreads, 0, s>>>(iters, 12345u, cycles, sink);
+    else k_probe_cells2<PROBE2_ROWS><<<grid, kCtaThreads, 0, s>>>(iters, 12345u, cycles, sink);
     return cudaGetLastError();
 }
 
@@ -183,12 +255,13 @@ int probe_blocks_per_sm(int mode) {
     int n = 0;
     if (mode == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_dpx, kCtaThreads, 0);
     else if (mode == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_cells<32>, kCtaThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_cells_u8x4<16>, kCtaThreads, 0);
+    else if (mode == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_cells_u8x4<16>, kCtaThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_probe_cells2<PROBE2_ROWS>, kCtaThreads, 0);
     return n;
 }
 
 // Work per thread and loop iteration of each probe mode: DPX operations
 // (mode 0) or cell updates (32 rows x 2 sequences; 16 rows x 4 sequences).
-double probe_work_per_iteration(int mode) { return mode == 0 ? 64.0 : (mode == 1 ? 64.0 : 64.0); }
+double probe_work_per_iteration(int mode) { return mode == 0 ? 64.0 : (mode == 3 ? 2.0 * PROBE2_ROWS : 64.0); }
 
 }  // namespace swdb

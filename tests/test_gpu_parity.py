@@ -13,7 +13,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-I16_SHAPES = [(4, 16), (8, 16), (16, 16), (32, 8), (32, 16), (8, 24), (8, 32), (16, 32), (32, 32)]
+I16_SHAPES = [(4, 16), (4, 24), (4, 32), (8, 16), (16, 16), (32, 8), (32, 16), (8, 24), (8, 32), (16, 32), (32, 32)]
 I32_SHAPES = [(8, 16), (16, 16), (32, 16), (32, 32)]
 
 
@@ -48,7 +48,7 @@ def test_int16x2_blosum62_shapes(gpu, lanes, rows):
     assert st["cells"] == int(qs.lengths.sum()) * int(db.lengths.sum())
 
 
-@pytest.mark.parametrize("lanes,rows", [(4, 16), (8, 16), (8, 24), (32, 32)])
+@pytest.mark.parametrize("lanes,rows", [(4, 16), (4, 32), (8, 16), (8, 24), (32, 32)])
 def test_int16x2_persistent_slots_reused(gpu, lanes, rows):
     """Far more sequence chunks than resident blocks: each block slot takes many
     chunks in turn and reuses its strip-boundary scratch for every pass of every
@@ -433,3 +433,26 @@ def test_workspace_bound_covers_mixed_batches(gpu, mode):
             scores = np.empty((qs.n, db.n), np.int32)
             gpu.sw_search(d.handle, qs.residues, qs.offsets, S, 10, 1, 0, scores_out=scores, workspace=ws, mode=m)
             np.testing.assert_array_equal(scores, oracle.all_scores(qs, db, S, 10, 1))
+
+
+def test_batched_single_query_runs_plain(gpu):
+    """A batched search with one non-empty query (nothing to pair it with) runs
+    in the plain form, exactly, and a workspace sized for the batched form of
+    that many queries still fits it."""
+    import torch
+    rng = np.random.default_rng(64)
+    db = _db(rng, 300, 1, 900)
+    S = synth.blosum62()
+    for lens in ([700], [0, 333, 0]):
+        qs = synth.seqset_from_lengths(rng, lens)
+        st = _check(gpu, qs, db, S, 10, 1, mode=gpu.SW_MODE_BATCHED)
+        assert st["mode_used"] == gpu.SW_MODE_PLAIN
+    with gpu.Database(db.residues, db.offsets, 24) as d:
+        off = np.array([0, 700], np.int64)
+        ws = torch.empty(gpu.sw_search_workspace_size(d.handle, off, 10, mode=gpu.SW_MODE_BATCHED),
+                         dtype=torch.uint8, device="cuda")
+        q = synth.seqset_from_lengths(rng, [700])
+        scores = np.empty((1, db.n), np.int32)
+        gpu.sw_search(d.handle, q.residues, q.offsets, S, 10, 1, 0, scores_out=scores, workspace=ws,
+                      mode=gpu.SW_MODE_BATCHED)
+    np.testing.assert_array_equal(scores, oracle.all_scores(q, db, S, 10, 1))

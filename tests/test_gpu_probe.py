@@ -14,5 +14,7 @@ def test_probe_modes(gpu):
     assert sms == sms1 == sms2 > 0
     assert dpx > 0 and cells16 > 0 and cells8 > 0
     assert cells16 <= dpx / 2.0 * 1.05
+    cells2, _ = gpu.sw_probe_alu_rate(0, 3)
+    assert 0 < cells2 <= dpx / 2.0 * 1.05
     with pytest.raises(gpu.SwError):
-        gpu.sw_probe_alu_rate(0, 3)
+        gpu.sw_probe_alu_rate(0, 4)
