@@ -310,6 +310,10 @@ struct Plan {
     int64_t total_m = 0;
     bool need_boundary = false;      // per-pair boundary (int32 rescore)
     int32_t sat_limit = 0;
+    int32_t smax_local = 0;          // max(S, 0): no H of a query of m rows exceeds min(m, longest) * smax_local
+    // the database is too small for the default shapes to fill the GPU: a query
+    // of one strip takes the shortest column step (32 lanes x 8 rows) instead
+    bool small_db = false;
     // plain form: persistent inter-task grid with per-slot boundary scratch
     int32_t inter_grid_max = 0;      // largest resident grid among the shapes used
     int32_t inter_min_lanes = 8;     // sets the most pairs per CTA
@@ -334,6 +338,19 @@ struct Plan {
 };
 
 int64_t mode16_first_pair(const sw_db *db, const Plan &p, int32_t m, int tr, int32_t o, int32_t e);
+
+// Launch shape of the inter-task kernel for a query of m rows (plain form,
+// shape chosen by the library): the table's least predicted time, except on a
+// database too small to fill the GPU with the default shapes, where a query of
+// one 256-row strip is latency-bound and takes the shortest column step.
+void query_shape(const Plan &p, int64_t m, int *lanes, int *rows) {
+    if (p.small_db && m <= kLongInterRows) {
+        *lanes = kLongInterLanes;
+        *rows = kLongInterRows / kLongInterLanes;
+        return;
+    }
+    choose_shape(p.plain_table, m, lanes, rows);
+}
 
 // Choose arithmetic and launch shapes for this call.
 int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int32_t *matrix,
@@ -450,6 +467,8 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
     if (want < 0 || want > SW_PREC_I32) return fail(SW_ERR_INVALID_ARG, "unknown precision");
     p.precision = (want == SW_PREC_I32 || !fits16) ? SW_PREC_I32 : SW_PREC_I16;
     p.sat_limit = 32767 - std::max(smax, 0);
+    p.smax_local = std::max(smax, 0);
+    p.small_db = db->n_sorted / 2 < int64_t(std::max(1, db->sm_count)) * (kCtaThreads / 8);
 
     const int mode = opts ? opts->mode : SW_MODE_AUTO;
     if (mode < 0 || mode > SW_MODE_BATCHED) return fail(SW_ERR_INVALID_ARG, "unknown mode");
@@ -491,7 +510,7 @@ int make_plan(const sw_db *db, const int64_t *q_offsets, int32_t n_q, const int3
             p.min_tr = 1 << 30;
             for (int32_t i = 0; i < n_q; ++i) {
                 int l = 8, r = 16;
-                choose_shape(p.plain_table, q_offsets[i + 1] - q_offsets[i], &l, &r);
+                query_shape(p, q_offsets[i + 1] - q_offsets[i], &l, &r);
                 p.min_tr = std::min(p.min_tr, l * r);
             }
             if (n_q == 0) p.min_tr = 128;
@@ -1326,7 +1345,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
             ia.pair_begin = plan.long_end_pair;
             ia.pair_end = n_pairs;
             int lanes = plan.lanes, rows = plan.rows;
-            if (plan.auto_shape) choose_shape(plan.plain_table, m, &lanes, &rows);
+            if (plan.auto_shape) query_shape(plan, m, &lanes, &rows);
             last_lanes = lanes;
             last_rows = rows;
             // persistent grid, per-slot boundary scratch (stays in L2)
@@ -1353,11 +1372,13 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
     }
     if (split) SW_CUDA_TRY(cudaStreamWaitEvent(st, db->ev_join, 0));
 
-    // (3) Exact int32 rescore of the sequences whose int16 maximum saturated.
+    // (3) Exact int32 rescore of the sequences whose int16 maximum saturated
+    //     (skipped for a query none of whose scores can reach the limit).
     if (plan.precision == SW_PREC_I16) {
         for (int32_t qi = 0; qi < n_q && db->n_seqs > 0; ++qi) {
             const int32_t m = int32_t(q_offsets[qi + 1] - q_offsets[qi]);
             if (m == 0) continue;
+            if (std::min<int64_t>(m, db->max_len) * plan.smax_local < plan.sat_limit) continue;
             const uint8_t *q = d_queries + q_offsets[qi];
             const int tr32 = plan.lanes32 * plan.rows32;
             const int32_t m_pad = int32_t(round_up(m, tr32));
@@ -1422,7 +1443,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
                     last_rows = plan.mode16_rows.back();
                 }
             } else if (plan.precision == SW_PREC_I16 && plan.mode == SW_MODE_PLAIN && plan.auto_shape && n_q > 0) {
-                choose_shape(plan.plain_table, q_offsets[n_q] - q_offsets[n_q - 1], &last_lanes, &last_rows);
+                query_shape(plan, q_offsets[n_q] - q_offsets[n_q - 1], &last_lanes, &last_rows);
             }
         }
         SW_CUDA_TRY(cudaGraphLaunch(db->graph_exec, st));
