@@ -188,30 +188,88 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_modes_i16x2(
             uint2 quad = make_uint2(0, 0), quad_next = make_uint2(0, 0);
             uint2 *stg = bstage[sub];
             constexpr int gstride = 2;                    // uint4 per 4-column group of the slot scratch
-            if (k == 0 && Lp > 0) {
-                quad_next = __ldg(cptr);
-                if (pass > 0) {
-                    cp_async16(stg + 0, bnd);
-                    cp_async16(stg + 2, bnd + 1);
-                    cp_async_commit();
-                    if (4 < Lp) {
-                        cp_async16(stg + 4, bnd + gstride);
-                        cp_async16(stg + 6, bnd + gstride + 1);
-                    }
-                    cp_async_commit();
+            if (Lp > 0) quad_next = __ldg(cptr);          // every lane of the subwarp: one broadcast load
+            if (k == 0 && Lp > 0 && pass > 0) {
+                cp_async16(stg + 0, bnd);
+                cp_async16(stg + 2, bnd + 1);
+                cp_async_commit();
+                if (4 < Lp) {
+                    cp_async16(stg + 4, bnd + gstride);
+                    cp_async16(stg + 6, bnd + gstride + 1);
                 }
+                cp_async_commit();
             }
 
-            auto step = [&](const int s, auto steady_c, auto u_c) {
-                constexpr bool STEADY = decltype(steady_c)::value;
-                constexpr int U = decltype(u_c)::value;
+            // The cell work of column j (0-based) for this lane's R rows, with the
+            // mode's bookkeeping of the last row and of column n.
+            auto cells = [&](const int j, const uint32_t hin, const uint32_t fin, const uint32_t cin) {
+                const int ta = int(cin & 0xffu), tb = int((cin >> 8) & 0xffu);
+                const uint4 *pa = reinterpret_cast<const uint4 *>(prof + ta * SLOT + k * 16);
+                const uint4 *pb = reinterpret_cast<const uint4 *>(prof + tb * SLOT + k * 16);
+                uint32_t wa[R / 4], wb[R / 4];
+#pragma unroll
+                for (int v = 0; v < R / 16; ++v) {
+                    const uint4 x = pa[v * T];
+                    const uint4 y = pb[v * T];
+                    wa[4 * v + 0] = x.x; wa[4 * v + 1] = x.y; wa[4 * v + 2] = x.z; wa[4 * v + 3] = x.w;
+                    wb[4 * v + 0] = y.x; wb[4 * v + 1] = y.y; wb[4 * v + 2] = y.z; wb[4 * v + 3] = y.w;
+                }
+                if (R % 16) {                             // last group of 8 rows: an 8-byte load
+                    const uint2 x = *reinterpret_cast<const uint2 *>(pa + (R / 16) * T);
+                    const uint2 y = *reinterpret_cast<const uint2 *>(pb + (R / 16) * T);
+                    wa[R / 4 - 2] = x.x; wa[R / 4 - 1] = x.y;
+                    wb[R / 4 - 2] = y.x; wb[R / 4 - 1] = y.y;
+                }
+                uint32_t f = fin;                         // B(F) of this lane's top row
+                uint32_t d = hd;
+                uint32_t ylast = 0;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t p = prmt(wa[r / 4], wb[r / 4], pair_sel(r % 4));
+                    const uint32_t e_r = __viaddmax_u16x2(E[r], ADD_NEG_E, Ho[r]);
+                    const uint32_t x = __viaddmax_u16x2(d, p, e_r);
+                    const uint32_t y = vmax2(f, x);                    // B(H)
+                    const uint32_t ho = y - OO;                         // B(H - o), no borrow
+                    f = __viaddmax_u16x2(f, ADD_NEG_E, ho);           // B(F) of the row below
+                    d = Ho[r];
+                    E[r] = e_r;
+                    Ho[r] = ho;
+                    if (r == R - 1) ylast = y;
+                }
+                if (LAST) {                               // lane T-1: ylast = B(H(m, j + 1))
+                    if (GLOBAL) {
+                        if (j == na - 1) res = (res & 0xffff0000u) | (ylast & 0xffffu);
+                        if (j == nb - 1) res = (res & 0xffffu) | (ylast & 0xffff0000u);
+                    } else {
+                        const uint32_t mask = (j < na ? 0xffffu : 0u) | (j < nb ? 0xffff0000u : 0u);
+                        res = vmax2(res, ylast & mask);
+                    }
+                }
+                if (OVERLAP && (j == na - 1 || j == nb - 1)) {   // column n of a half: its rows here
+                    uint32_t cm = Ho[0];
+#pragma unroll
+                    for (int r = 1; r < R; ++r) cm = vmax2(cm, Ho[r]);
+                    cm += OO;                             // B(H) = B(Ho) + o, no carry
+                    const uint32_t mask = (j == na - 1 ? 0xffffu : 0u) | (j == nb - 1 ? 0xffff0000u : 0u);
+                    mcol = vmax2(mcol, cm & mask);
+                }
+                hd = hin;
+                pub_h = Ho[R - 1];
+                pub_f = f;
+                pub_c = cin;
+                if (!LAST && k == T - 1)                  // 4 consecutive columns fill one 32-byte sector
+                    reinterpret_cast<uint2 *>(bnd)[size_t(j >> 2) * (gstride * 2) + (j & 3)] = make_uint2(pub_h, pub_f);
+            };
+
+            // One column step with every check (lanes starting or finishing).
+            auto step = [&](const int s) {
                 uint32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1, T);
                 uint32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1, T);
                 uint32_t cin = __shfl_up_sync(0xffffffffu, pub_c, 1, T);
                 const int j = s - k;                      // 0-based column (column number j + 1)
-                const bool act = STEADY || ((j >= 0) && (j < Lp));
+                const bool act = (j >= 0) && (j < Lp);
                 if (k == 0 && act) {
-                    const int s3 = STEADY ? U : (s & 3);
+                    const int s3 = s & 3;
                     if (s3 == 0) {
                         quad = quad_next;
                         if (s + 4 < Lp) quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
@@ -237,79 +295,65 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_modes_i16x2(
                         }
                     }
                 }
-                if (act) {
-                    const int ta = int(cin & 0xffu), tb = int((cin >> 8) & 0xffu);
-                    const uint4 *pa = reinterpret_cast<const uint4 *>(prof + ta * SLOT + k * 16);
-                    const uint4 *pb = reinterpret_cast<const uint4 *>(prof + tb * SLOT + k * 16);
-                    uint32_t wa[R / 4], wb[R / 4];
-#pragma unroll
-                    for (int v = 0; v < R / 16; ++v) {
-                        const uint4 x = pa[v * T];
-                        const uint4 y = pb[v * T];
-                        wa[4 * v + 0] = x.x; wa[4 * v + 1] = x.y; wa[4 * v + 2] = x.z; wa[4 * v + 3] = x.w;
-                        wb[4 * v + 0] = y.x; wb[4 * v + 1] = y.y; wb[4 * v + 2] = y.z; wb[4 * v + 3] = y.w;
-                    }
-                    if (R % 16) {                         // last group of 8 rows: an 8-byte load
-                        const uint2 x = *reinterpret_cast<const uint2 *>(pa + (R / 16) * T);
-                        const uint2 y = *reinterpret_cast<const uint2 *>(pb + (R / 16) * T);
-                        wa[R / 4 - 2] = x.x; wa[R / 4 - 1] = x.y;
-                        wb[R / 4 - 2] = y.x; wb[R / 4 - 1] = y.y;
-                    }
-                    uint32_t f = fin;                     // B(F) of this lane's top row
-                    uint32_t d = hd;
-                    uint32_t ylast = 0;
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const uint32_t p = prmt(wa[r / 4], wb[r / 4], pair_sel(r % 4));
-                        const uint32_t e_r = __viaddmax_u16x2(E[r], ADD_NEG_E, Ho[r]);
-                        const uint32_t x = __viaddmax_u16x2(d, p, e_r);
-                        const uint32_t y = vmax2(f, x);                // B(H)
-                        const uint32_t ho = y - OO;                             // B(H - o), no borrow
-                        f = __viaddmax_u16x2(f, ADD_NEG_E, ho);               // B(F) of the row below
-                        d = Ho[r];
-                        E[r] = e_r;
-                        Ho[r] = ho;
-                        if (r == R - 1) ylast = y;
-                    }
-                    if (LAST) {                           // lane T-1: ylast = B(H(m, j + 1))
-                        if (GLOBAL) {
-                            if (j == na - 1) res = (res & 0xffff0000u) | (ylast & 0xffffu);
-                            if (j == nb - 1) res = (res & 0xffffu) | (ylast & 0xffff0000u);
-                        } else {
-                            const uint32_t mask = (j < na ? 0xffffu : 0u) | (j < nb ? 0xffff0000u : 0u);
-                            res = vmax2(res, ylast & mask);
-                        }
-                    }
-                    if (OVERLAP && (j == na - 1 || j == nb - 1)) {   // column n of a half: its rows here
-                        uint32_t cm = Ho[0];
-#pragma unroll
-                        for (int r = 1; r < R; ++r) cm = vmax2(cm, Ho[r]);
-                        cm += OO;                         // B(H) = B(Ho) + o, no carry
-                        const uint32_t mask = (j == na - 1 ? 0xffffu : 0u) | (j == nb - 1 ? 0xffff0000u : 0u);
-                        mcol = vmax2(mcol, cm & mask);
-                    }
-                    hd = hin;
-                    pub_h = Ho[R - 1];
-                    pub_f = f;
-                    pub_c = cin;
-                    if (!LAST && k == T - 1) {            // 4 consecutive columns fill one 32-byte sector
-                        reinterpret_cast<uint2 *>(bnd)[size_t(j >> 2) * (gstride * 2) + (j & 3)] =
-                            make_uint2(Ho[R - 1], f);
-                    }
-                }
+                if (act) cells(j, hin, fin, cin);
             };
-            using FalseC = std::integral_constant<bool, false>;
-            using TrueC = std::integral_constant<bool, true>;
+
+            // One steady column step (every lane of the warp inside its pair),
+            // U = s % 4: lane 0 takes its code from quad and its top-row inputs
+            // from the running top row (first pass) or the broadcast load ib[U],
+            // by select instead of a branch.
+            auto sstep = [&](const int s, const uint2 *ib, auto u_c) {
+                constexpr int U = decltype(u_c)::value;
+                uint32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1, T);
+                uint32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1, T);
+                uint32_t cin = __shfl_up_sync(0xffffffffu, pub_c, 1, T);
+                const uint32_t w = (U & 2) ? quad.y : quad.x;
+                const uint32_t c0 = (U & 1) ? (w >> 16) : (w & 0xffffu);
+                uint32_t h0, f0;
+                if (pass == 0) {
+                    if (GLOBAL) top -= GM2;
+                    h0 = top;
+                    f0 = top;
+                } else {
+                    const uint2 v = ib[U];
+                    h0 = v.x;
+                    f0 = v.y;
+                }
+                const bool lane0 = k == 0;
+                hin = lane0 ? h0 : hin;
+                fin = lane0 ? f0 : fin;
+                cin = lane0 ? c0 : cin;
+                cells(s + U - k, hin, fin, cin);
+            };
+            using U0 = std::integral_constant<int, 0>;
+            using U1 = std::integral_constant<int, 1>;
+            using U2 = std::integral_constant<int, 2>;
+            using U3 = std::integral_constant<int, 3>;
             const int s_steady = (T + 2) & ~3;
             int s = 0;
-            for (; s < s_steady && s < steps; ++s) step(s, FalseC(), std::integral_constant<int, -1>());
+            for (; s < s_steady && s < steps; ++s) step(s);
             for (; s + 3 < Lmin; s += 4) {
-                step(s, TrueC(), std::integral_constant<int, 0>());
-                step(s + 1, TrueC(), std::integral_constant<int, 1>());
-                step(s + 2, TrueC(), std::integral_constant<int, 2>());
-                step(s + 3, TrueC(), std::integral_constant<int, 3>());
+                quad = quad_next;
+                if (s + 4 < Lp) quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
+                const uint2 *ib = stg;
+                if (pass > 0) {
+                    cp_async_wait1();                     // group s/4 has landed
+                    ib = stg + ((s >> 2) & 1) * 4;
+                }
+                sstep(s, ib, U0());
+                sstep(s, ib, U1());
+                sstep(s, ib, U2());
+                sstep(s, ib, U3());
+                if (pass > 0) {                           // fetch group s/4 + 2 into the freed half
+                    if (k == 0 && s + 5 < Lp) {
+                        const uint4 *g = bnd + size_t((s >> 2) + 2) * gstride;
+                        cp_async16(stg + ((s >> 2) & 1) * 4, g);
+                        cp_async16(stg + ((s >> 2) & 1) * 4 + 2, g + 1);
+                    }
+                    cp_async_commit();
+                }
             }
-            for (; s < steps; ++s) step(s, FalseC(), std::integral_constant<int, -1>());
+            for (; s < steps; ++s) step(s);
         };
         for (int pass = 0; pass + 1 < npass; ++pass) run_pass(pass, std::false_type());
         run_pass(npass - 1, std::true_type());
