@@ -207,11 +207,22 @@ ShapeTable plain_shapes(const sw_db *db) {
     return ShapeTable(std::begin(kShapes), std::end(kShapes));
 }
 
+// Rows the inter-task kernel computes for a query of m rows with this shape:
+// full strips of lanes*rows rows, then a last strip of the fewest rows per lane
+// (a multiple of 8) that cover the rest (k_inter16.cu).
+int64_t inter_padded_rows(int64_t m, int lanes, int rows) {
+    const int64_t tr = int64_t(lanes) * rows;
+    if (m <= 0) return 0;
+    const int64_t full = (m - 1) / tr;
+    const int64_t rest = m - full * tr;
+    const int64_t per_lane = std::min<int64_t>(rows, round_up((rest + lanes - 1) / lanes, 8));
+    return full * tr + lanes * per_lane;
+}
+
 void choose_shape(const ShapeTable &table, int64_t m, int *lanes, int *rows) {
     double best = 1e300;
     for (const ShapeRate &c : table) {
-        const int64_t tr = int64_t(c.lanes) * c.rows;
-        const double t = double((m + tr - 1) / tr * tr) / c.gcups;
+        const double t = double(inter_padded_rows(m, c.lanes, c.rows)) / c.gcups;
         if (t < best) {
             best = t;
             *lanes = c.lanes;

@@ -143,207 +143,229 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_inter_i16x2(
     const int npass = (a.m + TR - 1) / TR;
     uint32_t mx = BZERO2;                  // running max of B(H), both halves
 
-    for (int pass = 0; pass < npass; ++pass) {
-        __syncthreads();
-        // Profile strip for rows pass*TR .. pass*TR+TR-1, layout
-        // [residue a][group h][lane k][16 rows]: lane k's rows 16h..16h+15 sit at
-        // a*SLOT + h*T*16 + k*16, so the 8 lanes of a quarter-warp read 8
-        // consecutive 16-byte slots (no bank conflicts) and a lane's later
-        // groups are compile-time offsets from its first.  With R = 24 the
-        // second group holds 8 rows in the first half of its slot.
-        for (int w = tid; w < kProfRows * TR / 4; w += kCtaThreads) {
-            const int e0 = w * 4;
-            const int res = e0 / TR;
-            const int within = e0 % TR;
-            const int row0 = pass * TR + within;
-            const int kk = within / R, rr = within % R;
-            const int phys = res * SLOT + (rr >> 4) * (T * 16) + kk * 16 + (rr & 15);
-            uint32_t word = 0;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int row = row0 + c;
-                int v = -128;
-                if (row < a.m) {
-                    // device-resident queries are not validated on the host:
-                    // codes outside the table score as padding
-                    const int qc = a.query[row];
-                    if (qc < kProfRows) v = mat[res * kProfRows + qc];
-                }
-                word |= (uint32_t(uint8_t(int8_t(v)))) << (8 * c);
-            }
-            reinterpret_cast<uint32_t *>(prof)[phys / 4] = word;
-        }
-        __syncthreads();
-        if (Lw == 0) continue;
-
-        uint32_t E[R], Ho[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) { E[r] = BNEG_O2; Ho[r] = BNEG_O2; }
-        uint32_t hd = BNEG_O2;             // B(Ho(top-1, j-1))
-        // pub_h: B(Ho) of this lane's bottom row; pub_f: B(F) of the next lane's top row
-        uint32_t pub_h = BNEG_O2, pub_f = BNEG_O2, pub_c = 0;
-        const bool last_pass = (pass + 1 == npass);
-        const int steps = Lw + T - 1;
-        // Lane 0 reads codes and (after the first pass) the previous strip's
-        // bottom row in groups of 4 columns, one group ahead of use, so the
-        // global-load latency stays off the per-column critical path.
-        uint2 quad = make_uint2(0, 0), quad_next = make_uint2(0, 0);
-        uint2 *stg = bstage[sub];
-        if (Lp > 0) quad_next = __ldg(cptr);     // every lane of the subwarp: one broadcast load
-        if (k == 0 && Lp > 0 && pass > 0) {
-            cp_async16(stg + 0, bnd);
-            cp_async16(stg + 2, bnd + 1);
-            cp_async_commit();
-            if (4 < Lp) {
-                cp_async16(stg + 4, bnd + gstride);
-                cp_async16(stg + 6, bnd + gstride + 1);
-            }
-            cp_async_commit();
-        }
-
-        // Lane T-1's store of the strip's bottom row (H - o, F) at column jl;
-        // 4 consecutive columns fill one 32-byte sector.
-        auto bottom_index = [&](const int jl) -> size_t {
-            if (SLOTS) return size_t(jl);                           // per subwarp, [column]
-            return size_t(jl >> 2) * (gstride * 2) + (jl & 3);      // [column/4][slot][column%4]
-        };
-
-        // The cell work of one column step for this lane's R rows.
-        auto cells = [&](const uint32_t hin, const uint32_t fin, const uint32_t cin) {
-            const int ta = int(cin & 0xffu), tb = int((cin >> 8) & 0xffu);
-            const uint4 *pa = reinterpret_cast<const uint4 *>(prof + ta * SLOT + k * 16);
-            const uint4 *pb = reinterpret_cast<const uint4 *>(prof + tb * SLOT + k * 16);
-            uint32_t wa[R / 4], wb[R / 4];
-#pragma unroll
-            for (int v = 0; v < R / 16; ++v) {
-                const uint4 x = pa[v * T];
-                const uint4 y = pb[v * T];
-                wa[4 * v + 0] = x.x; wa[4 * v + 1] = x.y; wa[4 * v + 2] = x.z; wa[4 * v + 3] = x.w;
-                wb[4 * v + 0] = y.x; wb[4 * v + 1] = y.y; wb[4 * v + 2] = y.z; wb[4 * v + 3] = y.w;
-            }
-            if (R % 16) {                     // last group of 8 rows: an 8-byte load
-                const uint2 x = *reinterpret_cast<const uint2 *>(pa + (R / 16) * T);
-                const uint2 y = *reinterpret_cast<const uint2 *>(pb + (R / 16) * T);
-                wa[R / 4 - 2] = x.x; wa[R / 4 - 1] = x.y;
-                wb[R / 4 - 2] = y.x; wb[R / 4 - 1] = y.y;
-            }
-            uint32_t f = fin;                 // B(F) of this lane's top row
-            uint32_t d = hd;
-            uint32_t yprev = 0;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const uint32_t p = prmt(wa[r / 4], wb[r / 4], pair_sel(r % 4));
-                const uint32_t e_r = __viaddmax_u16x2(E[r], ADD_NEG_E, Ho[r]);
-                const uint32_t x = __viaddmax_u16x2(d, p, e_r);
-                const uint32_t y = __vimax3_u16x2(f, x, BZERO2);   // B(H)
-                const uint32_t ho = y - OO;                         // B(H - o), no borrow: y >= 0x8000
-                f = __viaddmax_u16x2(f, ADD_NEG_E, ho);           // B(F) of the row below
-                d = Ho[r];
-                E[r] = e_r;
-                Ho[r] = ho;
-                if (r & 1) mx = __vimax3_u16x2(mx, yprev, y);
-                yprev = y;
-            }
-            hd = hin;
-            pub_h = Ho[R - 1];
-            pub_f = f;
-            pub_c = cin;
-        };
-
-        // One column step of the subwarp with every check (lanes starting or
-        // finishing): the first and last columns.
-        auto step = [&](const int s) {
-            uint32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1, T);
-            uint32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1, T);
-            uint32_t cin = __shfl_up_sync(0xffffffffu, pub_c, 1, T);
-            const int j = s - k;
-            const bool act = (j >= 0) && (j < Lp);
-            if (k == 0 && act) {
-                const int s3 = s & 3;
-                if (s3 == 0) {
-                    quad = quad_next;
-                    if (s + 4 < Lp) quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
-                    if (pass > 0) cp_async_wait1();      // group s/4 has landed
-                }
-                const uint32_t w = (s3 & 2) ? quad.y : quad.x;
-                cin = (s3 & 1) ? (w >> 16) : (w & 0xffffu);
-                if (pass == 0) {          // H(0,j) = 0, F(1,j) = -o
-                    hin = BNEG_O2;
-                    fin = BNEG_O2;
-                } else {
-                    const uint2 bv = stg[((s >> 2) & 1) * 4 + s3];
-                    hin = bv.x;
-                    fin = bv.y;
-                    if (s3 == 3) {        // buffer of group s/4 is free: fetch group s/4 + 2 into it
-                        if (s + 5 < Lp) {
-                            const uint4 *g = bnd + size_t((s >> 2) + 2) * gstride;
-                            cp_async16(stg + ((s >> 2) & 1) * 4, g);
-                            cp_async16(stg + ((s >> 2) & 1) * 4 + 2, g + 1);
-                        }
-                        cp_async_commit();
+    // One pass (strip) of the query: rows pass*TR .. pass*TR + T*RP - 1, RP rows
+    // per lane.  Every pass but the last is a full strip (RP = R); the last one
+    // takes the fewest rows per lane (a multiple of 8) that cover the rest of
+    // the query, which cuts the padded rows a query's final strip computes.
+    auto run_pass = [&](const int pass, auto rp_c) {
+        constexpr int RP = decltype(rp_c)::value;
+        constexpr int TRP = T * RP;
+        constexpr int SLOTP = T * 16 * ((RP + 15) / 16);   // profile bytes per residue in this pass
+            __syncthreads();
+            // Profile strip for rows pass*TRP .. pass*TRP+TRP-1, layout
+            // [residue a][group h][lane k][16 rows]: lane k's rows 16h..16h+15 sit at
+            // a*SLOTP + h*T*16 + k*16, so the 8 lanes of a quarter-warp read 8
+            // consecutive 16-byte slots (no bank conflicts) and a lane's later
+            // groups are compile-time offsets from its first.  With RP = 24 the
+            // second group holds 8 rows in the first half of its slot.
+            for (int w = tid; w < kProfRows * TRP / 4; w += kCtaThreads) {
+                const int e0 = w * 4;
+                const int res = e0 / TRP;
+                const int within = e0 % TRP;
+                const int row0 = pass * TR + within;
+                const int kk = within / RP, rr = within % RP;
+                const int phys = res * SLOTP + (rr >> 4) * (T * 16) + kk * 16 + (rr & 15);
+                uint32_t word = 0;
+    #pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int row = row0 + c;
+                    int v = -128;
+                    if (row < a.m) {
+                        // device-resident queries are not validated on the host:
+                        // codes outside the table score as padding
+                        const int qc = a.query[row];
+                        if (qc < kProfRows) v = mat[res * kProfRows + qc];
                     }
+                    word |= (uint32_t(uint8_t(int8_t(v)))) << (8 * c);
                 }
+                reinterpret_cast<uint32_t *>(prof)[phys / 4] = word;
             }
-            if (act) {
-                cells(hin, fin, cin);
-                if (k == T - 1 && !last_pass)
-                    reinterpret_cast<uint2 *>(bnd)[bottom_index(s - (T - 1))] = make_uint2(pub_h, pub_f);
-            }
-        };
+            __syncthreads();
+            if (Lw == 0) return;
 
-        // One steady column step (every lane of the warp inside its sequence),
-        // U = s % 4: lane 0 takes its codes from quad and its top-row inputs
-        // from the broadcast load ib[U] with selects instead of a branch.
-        auto sstep = [&](const int s, const uint2 *ib, auto u_c) {
-            constexpr int U = decltype(u_c)::value;
-            uint32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1, T);
-            uint32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1, T);
-            uint32_t cin = __shfl_up_sync(0xffffffffu, pub_c, 1, T);
-            const uint2 v = ib[U];
-            const uint32_t w = (U & 2) ? quad.y : quad.x;
-            const uint32_t c0 = (U & 1) ? (w >> 16) : (w & 0xffffu);
-            const bool lane0 = k == 0;
-            hin = lane0 ? v.x : hin;
-            fin = lane0 ? v.y : fin;
-            cin = lane0 ? c0 : cin;
-            cells(hin, fin, cin);
-            if (k == T - 1 && !last_pass)
-                reinterpret_cast<uint2 *>(bnd)[bottom_index(s + U - (T - 1))] = make_uint2(pub_h, pub_f);
-        };
-        using U0 = std::integral_constant<int, 0>;
-        using U1 = std::integral_constant<int, 1>;
-        using U2 = std::integral_constant<int, 2>;
-        using U3 = std::integral_constant<int, 3>;
-        // Steady columns: s >= T-1 (every lane started) and s + 3 < Lmin (no lane
-        // of any subwarp in the warp has finished), in groups of 4 aligned to s % 4 == 0.
-        const int Lmin = __reduce_min_sync(0xffffffffu, Lp);
-        const int s_steady = (T + 2) & ~3;
-        int s = 0;
-        for (; s < s_steady && s < steps; ++s) step(s);
-        for (; s + 3 < Lmin; s += 4) {
-            quad = quad_next;
-            if (s + 4 < Lp) quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
-            const uint2 *ib = top4;
-            if (pass > 0) {
-                cp_async_wait1();                              // group s/4 has landed
-                ib = stg + ((s >> 2) & 1) * 4;
-            }
-            sstep(s, ib, U0());
-            sstep(s, ib, U1());
-            sstep(s, ib, U2());
-            sstep(s, ib, U3());
-            if (pass > 0) {                                    // fetch group s/4 + 2 into the freed half
-                if (k == 0 && s + 5 < Lp) {
-                    const uint4 *g = bnd + size_t((s >> 2) + 2) * gstride;
-                    cp_async16(stg + ((s >> 2) & 1) * 4, g);
-                    cp_async16(stg + ((s >> 2) & 1) * 4 + 2, g + 1);
+            uint32_t E[RP], Ho[RP];
+    #pragma unroll
+            for (int r = 0; r < RP; ++r) { E[r] = BNEG_O2; Ho[r] = BNEG_O2; }
+            uint32_t hd = BNEG_O2;             // B(Ho(top-1, j-1))
+            // pub_h: B(Ho) of this lane's bottom row; pub_f: B(F) of the next lane's top row
+            uint32_t pub_h = BNEG_O2, pub_f = BNEG_O2, pub_c = 0;
+            const bool last_pass = (pass + 1 == npass);
+            const int steps = Lw + T - 1;
+            // Lane 0 reads codes and (after the first pass) the previous strip's
+            // bottom row in groups of 4 columns, one group ahead of use, so the
+            // global-load latency stays off the per-column critical path.
+            uint2 quad = make_uint2(0, 0), quad_next = make_uint2(0, 0);
+            uint2 *stg = bstage[sub];
+            if (Lp > 0) quad_next = __ldg(cptr);     // every lane of the subwarp: one broadcast load
+            if (k == 0 && Lp > 0 && pass > 0) {
+                cp_async16(stg + 0, bnd);
+                cp_async16(stg + 2, bnd + 1);
+                cp_async_commit();
+                if (4 < Lp) {
+                    cp_async16(stg + 4, bnd + gstride);
+                    cp_async16(stg + 6, bnd + gstride + 1);
                 }
                 cp_async_commit();
             }
-        }
-        for (; s < steps; ++s) step(s);
-    }
 
+            // Lane T-1's store of the strip's bottom row (H - o, F) at column jl;
+            // 4 consecutive columns fill one 32-byte sector.
+            auto bottom_index = [&](const int jl) -> size_t {
+                if (SLOTS) return size_t(jl);                           // per subwarp, [column]
+                return size_t(jl >> 2) * (gstride * 2) + (jl & 3);      // [column/4][slot][column%4]
+            };
+
+            // The cell work of one column step for this lane's RP rows.
+            auto cells = [&](const uint32_t hin, const uint32_t fin, const uint32_t cin) {
+                const int ta = int(cin & 0xffu), tb = int((cin >> 8) & 0xffu);
+                const uint4 *pa = reinterpret_cast<const uint4 *>(prof + ta * SLOTP + k * 16);
+                const uint4 *pb = reinterpret_cast<const uint4 *>(prof + tb * SLOTP + k * 16);
+                uint32_t wa[RP / 4], wb[RP / 4];
+    #pragma unroll
+                for (int v = 0; v < RP / 16; ++v) {
+                    const uint4 x = pa[v * T];
+                    const uint4 y = pb[v * T];
+                    wa[4 * v + 0] = x.x; wa[4 * v + 1] = x.y; wa[4 * v + 2] = x.z; wa[4 * v + 3] = x.w;
+                    wb[4 * v + 0] = y.x; wb[4 * v + 1] = y.y; wb[4 * v + 2] = y.z; wb[4 * v + 3] = y.w;
+                }
+                if (RP % 16) {                     // last group of 8 rows: an 8-byte load
+                    const uint2 x = *reinterpret_cast<const uint2 *>(pa + (RP / 16) * T);
+                    const uint2 y = *reinterpret_cast<const uint2 *>(pb + (RP / 16) * T);
+                    wa[RP / 4 - 2] = x.x; wa[RP / 4 - 1] = x.y;
+                    wb[RP / 4 - 2] = y.x; wb[RP / 4 - 1] = y.y;
+                }
+                uint32_t f = fin;                 // B(F) of this lane's top row
+                uint32_t d = hd;
+                uint32_t yprev = 0;
+    #pragma unroll
+                for (int r = 0; r < RP; ++r) {
+                    const uint32_t p = prmt(wa[r / 4], wb[r / 4], pair_sel(r % 4));
+                    const uint32_t e_r = __viaddmax_u16x2(E[r], ADD_NEG_E, Ho[r]);
+                    const uint32_t x = __viaddmax_u16x2(d, p, e_r);
+                    const uint32_t y = __vimax3_u16x2(f, x, BZERO2);   // B(H)
+                    const uint32_t ho = y - OO;                         // B(H - o), no borrow: y >= 0x8000
+                    f = __viaddmax_u16x2(f, ADD_NEG_E, ho);           // B(F) of the row below
+                    d = Ho[r];
+                    E[r] = e_r;
+                    Ho[r] = ho;
+                    if (r & 1) mx = __vimax3_u16x2(mx, yprev, y);
+                    yprev = y;
+                }
+                hd = hin;
+                pub_h = Ho[RP - 1];
+                pub_f = f;
+                pub_c = cin;
+            };
+
+            // One column step of the subwarp with every check (lanes starting or
+            // finishing): the first and last columns.
+            auto step = [&](const int s) {
+                uint32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1, T);
+                uint32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1, T);
+                uint32_t cin = __shfl_up_sync(0xffffffffu, pub_c, 1, T);
+                const int j = s - k;
+                const bool act = (j >= 0) && (j < Lp);
+                if (k == 0 && act) {
+                    const int s3 = s & 3;
+                    if (s3 == 0) {
+                        quad = quad_next;
+                        if (s + 4 < Lp) quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
+                        if (pass > 0) cp_async_wait1();      // group s/4 has landed
+                    }
+                    const uint32_t w = (s3 & 2) ? quad.y : quad.x;
+                    cin = (s3 & 1) ? (w >> 16) : (w & 0xffffu);
+                    if (pass == 0) {          // H(0,j) = 0, F(1,j) = -o
+                        hin = BNEG_O2;
+                        fin = BNEG_O2;
+                    } else {
+                        const uint2 bv = stg[((s >> 2) & 1) * 4 + s3];
+                        hin = bv.x;
+                        fin = bv.y;
+                        if (s3 == 3) {        // buffer of group s/4 is free: fetch group s/4 + 2 into it
+                            if (s + 5 < Lp) {
+                                const uint4 *g = bnd + size_t((s >> 2) + 2) * gstride;
+                                cp_async16(stg + ((s >> 2) & 1) * 4, g);
+                                cp_async16(stg + ((s >> 2) & 1) * 4 + 2, g + 1);
+                            }
+                            cp_async_commit();
+                        }
+                    }
+                }
+                if (act) {
+                    cells(hin, fin, cin);
+                    if (k == T - 1 && !last_pass)
+                        reinterpret_cast<uint2 *>(bnd)[bottom_index(s - (T - 1))] = make_uint2(pub_h, pub_f);
+                }
+            };
+
+            // One steady column step (every lane of the warp inside its sequence),
+            // U = s % 4: lane 0 takes its codes from quad and its top-row inputs
+            // from the broadcast load ib[U] with selects instead of a branch.
+            auto sstep = [&](const int s, const uint2 *ib, auto u_c) {
+                constexpr int U = decltype(u_c)::value;
+                uint32_t hin = __shfl_up_sync(0xffffffffu, pub_h, 1, T);
+                uint32_t fin = __shfl_up_sync(0xffffffffu, pub_f, 1, T);
+                uint32_t cin = __shfl_up_sync(0xffffffffu, pub_c, 1, T);
+                const uint2 v = ib[U];
+                const uint32_t w = (U & 2) ? quad.y : quad.x;
+                const uint32_t c0 = (U & 1) ? (w >> 16) : (w & 0xffffu);
+                const bool lane0 = k == 0;
+                hin = lane0 ? v.x : hin;
+                fin = lane0 ? v.y : fin;
+                cin = lane0 ? c0 : cin;
+                cells(hin, fin, cin);
+                if (k == T - 1 && !last_pass)
+                    reinterpret_cast<uint2 *>(bnd)[bottom_index(s + U - (T - 1))] = make_uint2(pub_h, pub_f);
+            };
+            using U0 = std::integral_constant<int, 0>;
+            using U1 = std::integral_constant<int, 1>;
+            using U2 = std::integral_constant<int, 2>;
+            using U3 = std::integral_constant<int, 3>;
+            // Steady columns: s >= T-1 (every lane started) and s + 3 < Lmin (no lane
+            // of any subwarp in the warp has finished), in groups of 4 aligned to s % 4 == 0.
+            const int Lmin = __reduce_min_sync(0xffffffffu, Lp);
+            const int s_steady = (T + 2) & ~3;
+            int s = 0;
+            for (; s < s_steady && s < steps; ++s) step(s);
+            for (; s + 3 < Lmin; s += 4) {
+                quad = quad_next;
+                if (s + 4 < Lp) quad_next = __ldg(cptr + ((s >> 2) + 1) * kBundlePairs);
+                const uint2 *ib = top4;
+                if (pass > 0) {
+                    cp_async_wait1();                              // group s/4 has landed
+                    ib = stg + ((s >> 2) & 1) * 4;
+                }
+                sstep(s, ib, U0());
+                sstep(s, ib, U1());
+                sstep(s, ib, U2());
+                sstep(s, ib, U3());
+                if (pass > 0) {                                    // fetch group s/4 + 2 into the freed half
+                    if (k == 0 && s + 5 < Lp) {
+                        const uint4 *g = bnd + size_t((s >> 2) + 2) * gstride;
+                        cp_async16(stg + ((s >> 2) & 1) * 4, g);
+                        cp_async16(stg + ((s >> 2) & 1) * 4 + 2, g + 1);
+                    }
+                    cp_async_commit();
+                }
+            }
+            for (; s < steps; ++s) step(s);
+    };
+    using RFull = std::integral_constant<int, R>;
+    for (int pass = 0; pass + 1 < npass; ++pass) run_pass(pass, RFull());
+    if (npass > 0) {
+        const int rest = a.m - (npass - 1) * TR;           // rows of the last strip, 1 .. TR
+        bool ran = false;
+        if constexpr (R > 8) {
+            if (rest <= T * 8) { run_pass(npass - 1, std::integral_constant<int, 8>()); ran = true; }
+        }
+        if constexpr (R > 16) {
+            if (!ran && rest <= T * 16) { run_pass(npass - 1, std::integral_constant<int, 16>()); ran = true; }
+        }
+        if constexpr (R > 24) {
+            if (!ran && rest <= T * 24) { run_pass(npass - 1, std::integral_constant<int, 24>()); ran = true; }
+        }
+        if (!ran) run_pass(npass - 1, RFull());
+    }
 #pragma unroll
     for (int dd = T / 2; dd >= 1; dd >>= 1) {
         const uint32_t other = __shfl_xor_sync(0xffffffffu, mx, dd, T);

@@ -456,3 +456,18 @@ def test_batched_single_query_runs_plain(gpu):
         gpu.sw_search(d.handle, q.residues, q.offsets, S, 10, 1, 0, scores_out=scores, workspace=ws,
                       mode=gpu.SW_MODE_BATCHED)
     np.testing.assert_array_equal(scores, oracle.all_scores(q, db, S, 10, 1))
+
+
+@pytest.mark.parametrize("lanes,rows", [(8, 32), (8, 24), (8, 16), (32, 32), (4, 32)])
+def test_last_strip_heights(gpu, lanes, rows):
+    """The last strip of a query takes the fewest rows per lane (a multiple of
+    8) that cover its remaining rows: remainders at and around every such
+    boundary, after one and after several full strips, equal the oracle."""
+    rng = np.random.default_rng(66 + lanes + rows)
+    db = _db(rng, 120, 1, 500)
+    tr = lanes * rows
+    rems = sorted({r for b in range(8, rows + 1, 8) for r in (lanes * b - 1, lanes * b, lanes * b + 1)
+                   if 1 <= r <= tr} | {1, tr})
+    qlens = [r for r in rems] + [2 * tr + r for r in rems[::3]]
+    qs = synth.seqset_from_lengths(rng, qlens)
+    _check(gpu, qs, db, synth.blosum62(), 10, 1, lanes=lanes, rows_per_lane=rows)
