@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_inter_i16x2(
         constexpr int TRP = T * RP;
         constexpr int SLOTP = T * 16 * ((RP + 15) / 16);   // profile bytes per residue in this pass
             __syncthreads();
-            // Profile strip for rows pass*TRP .. pass*TRP+TRP-1, layout
+            // Profile strip for rows pass*TR .. pass*TR+TRP-1, layout
             // [residue a][group h][lane k][16 rows]: lane k's rows 16h..16h+15 sit at
             // a*SLOTP + h*T*16 + k*16, so the 8 lanes of a quarter-warp read 8
             // consecutive 16-byte slots (no bank conflicts) and a lane's later

@@ -471,3 +471,19 @@ def test_last_strip_heights(gpu, lanes, rows):
     qlens = [r for r in rems] + [2 * tr + r for r in rems[::3]]
     qs = synth.seqset_from_lengths(rng, qlens)
     _check(gpu, qs, db, synth.blosum62(), 10, 1, lanes=lanes, rows_per_lane=rows)
+
+
+@pytest.mark.parametrize("lanes,rows", [(8, 32), (8, 24), (8, 16), (16, 32)])
+def test_batched_last_strip_heights(gpu, lanes, rows):
+    """Batched pairs whose longer query leaves a remainder at and around every
+    8-row boundary of the last strip (one strip and several) equal the oracle."""
+    rng = np.random.default_rng(77 + lanes + rows)
+    db = _db(rng, 120, 1, 500)
+    tr = lanes * rows
+    rems = sorted({r for b in range(8, rows + 1, 8) for r in (lanes * b - 1, lanes * b, lanes * b + 1)
+                   if 1 <= r <= tr} | {1, tr})
+    qlens = rems + [2 * tr + r for r in rems[::2]] + [5]
+    qs = synth.seqset_from_lengths(rng, qlens)
+    st = _check(gpu, qs, db, synth.blosum62(), 10, 1, mode=gpu.SW_MODE_BATCHED, lanes=lanes,
+                rows_per_lane=rows)
+    assert st["mode_used"] == gpu.SW_MODE_BATCHED
