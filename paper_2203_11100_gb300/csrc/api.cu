@@ -231,16 +231,14 @@ void choose_shape(const ShapeTable &table, int64_t m, int *lanes, int *rows) {
     }
 }
 
-// Batched-kernel shapes (lanes, rows) with measured rates (GCUPS, GB300);
-// each query pair takes the one with the least predicted time.
-// Shapes of the int16x2 alignment-mode kernel (k_modes16.cu), same rule.
+// Shapes of the int16x2 alignment-mode kernel (k_modes16.cu), same rule (its
+// virtual rows on top of the query make up the same padded row count).
 constexpr ShapeRate kModeShapes[] = {{8, 16, 5000.0}, {8, 24, 5680.0}, {8, 32, 5900.0}};
 
 void choose_mode_shape(int64_t m, int *lanes, int *rows) {
     double best = 1e300;
     for (const ShapeRate &c : kModeShapes) {
-        const int64_t tr = int64_t(c.lanes) * c.rows;
-        const double t = double((m + tr - 1) / tr * tr) / c.gcups;
+        const double t = double(inter_padded_rows(m, c.lanes, c.rows)) / c.gcups;
         if (t < best) {
             best = t;
             *lanes = c.lanes;
@@ -258,6 +256,8 @@ constexpr int kLongInterRows = 256;
 // query taller than one strip sends longer sequences to the int32 kernel.
 constexpr int32_t kMode16Cols = 4096;
 
+// Batched-kernel shapes (lanes, rows) with measured rates (GCUPS, GB300);
+// each query pair takes the one with the least predicted time.
 constexpr ShapeRate kBatchShapes[] = {{8, 16, 5000.0}, {8, 24, 5850.0}, {8, 32, 5850.0}};
 
 ShapeTable batch_shapes(const sw_db *db) {
@@ -1219,7 +1219,7 @@ int sw_search(sw_db *db, const uint8_t *queries, const int64_t *q_offsets, int32
                 a16.pair_end = n_pairs;
                 a16.query = d_queries + q0;
                 a16.m = m;
-                a16.virt_rows = int32_t(round_up(m, tr) - m);
+                a16.virt_rows = int32_t(inter_padded_rows(m, lanes, rows) - m);
                 a16.gap_open = gap_open;
                 a16.gap_extend = gap_extend;
                 memcpy(a16.prof8, ia.prof8, sizeof a16.prof8);

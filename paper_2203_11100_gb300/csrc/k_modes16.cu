@@ -27,8 +27,10 @@
 //   when both bounds, widened by the largest addend, fit int16.  The other
 //   pairs (the longest) go to the int32 kernel.
 // * The query is padded at the TOP with P virtual rows so that m + P fills
-//   whole strips and row m is always the last row of the last lane: the
-//   last-row maximum and H(m, n) then read one fixed register.  The virtual
+//   whole strips, the last of which may be short (8, 16 or 24 rows per lane
+//   instead of R: the fewest that cover the rest), and row m is always the
+//   last row of the last lane: the last-row maximum and H(m, n) then read one
+//   fixed register.  The virtual
 //   rows reproduce the mode's first row exactly:
 //     semi-global, overlap: S = 0 and H(v, 0) = 0 give H(v, j) = 0 and
 //                           F(P + 1, j) = -o, as below a first row of zeros;
@@ -95,7 +97,8 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_modes_i16x2(
     const int o = a.gap_open;
     const int gmin = min(a.gap_open, a.gap_extend);
     const int P = a.virt_rows;
-    const int npass = (a.m + P) / TR;
+    const int npass = (a.m + P + TR - 1) / TR;
+    const int rest = a.m + P - (npass - 1) * TR;     // rows of the last strip: T x 8, 16, 24 or R
     const int g_m = o + (a.m - 1) * gmin;             // g(m), m >= 1
 
     // H(i, 0) of padded row i (row 0 is the strip above the first virtual row)
@@ -137,19 +140,23 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_modes_i16x2(
         uint32_t res = GLOBAL ? 0u : pack2(32768 + (OVERLAP ? 0 : -g_m));
         uint32_t mcol = 0;               // OVERLAP: maximum of B(H(i, n)) over this lane's rows
 
-        auto run_pass = [&](const int pass, auto last_c) {
+        // One pass (strip): padded rows pass*TR .. pass*TR + T*RP - 1, RP rows per
+        // lane (RP = R but in the last pass, which may be shorter).
+        auto run_pass = [&](const int pass, auto last_c, auto rp_c) {
             constexpr bool LAST = decltype(last_c)::value;
+            constexpr int RP = decltype(rp_c)::value;
+            constexpr int TRP = T * RP;
             __syncthreads();
-            // Profile of padded rows pass*TR .. pass*TR+TR-1, layout [residue][16-row
+            // Profile of padded rows pass*TR .. pass*TR+TRP-1, layout [residue][16-row
             // group][lane][16 rows] as in the local kernel; virtual rows (above the
             // query) score S = 0 (semi-global, overlap) or -min(o, e) (global).
             const int pv = GLOBAL ? (o - gmin) : o;
-            for (int w = tid; w < kProfRows * TR / 4; w += kCtaThreads) {
+            for (int w = tid; w < kProfRows * TRP / 4; w += kCtaThreads) {
                 const int e0 = w * 4;
-                const int res_code = e0 / TR;
-                const int within = e0 % TR;
+                const int res_code = e0 / TRP;
+                const int within = e0 % TRP;
                 const int row0 = pass * TR + within - P;     // query row of the first of the 4
-                const int kk = within / R, rr = within % R;
+                const int kk = within / RP, rr = within % RP;
                 const int phys = res_code * SLOT + (rr >> 4) * (T * 16) + kk * 16 + (rr & 15);
                 uint32_t word = 0;
 #pragma unroll
@@ -172,10 +179,10 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_modes_i16x2(
             __syncthreads();
             if (Lw == 0) return;
 
-            const int i0 = pass * TR + k * R;             // padded row above this lane's first row
-            uint32_t E[R], Ho[R];
+            const int i0 = pass * TR + k * RP;            // padded row above this lane's first row
+            uint32_t E[RP], Ho[RP];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
+            for (int r = 0; r < RP; ++r) {
                 Ho[r] = pack2(32768 + col0(i0 + r + 1) - o);
                 E[r] = Ho[r];
             }
@@ -200,31 +207,31 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_modes_i16x2(
                 cp_async_commit();
             }
 
-            // The cell work of column j (0-based) for this lane's R rows, with the
+            // The cell work of column j (0-based) for this lane's RP rows, with the
             // mode's bookkeeping of the last row and of column n.
             auto cells = [&](const int j, const uint32_t hin, const uint32_t fin, const uint32_t cin) {
                 const int ta = int(cin & 0xffu), tb = int((cin >> 8) & 0xffu);
                 const uint4 *pa = reinterpret_cast<const uint4 *>(prof + ta * SLOT + k * 16);
                 const uint4 *pb = reinterpret_cast<const uint4 *>(prof + tb * SLOT + k * 16);
-                uint32_t wa[R / 4], wb[R / 4];
+                uint32_t wa[RP / 4], wb[RP / 4];
 #pragma unroll
-                for (int v = 0; v < R / 16; ++v) {
+                for (int v = 0; v < RP / 16; ++v) {
                     const uint4 x = pa[v * T];
                     const uint4 y = pb[v * T];
                     wa[4 * v + 0] = x.x; wa[4 * v + 1] = x.y; wa[4 * v + 2] = x.z; wa[4 * v + 3] = x.w;
                     wb[4 * v + 0] = y.x; wb[4 * v + 1] = y.y; wb[4 * v + 2] = y.z; wb[4 * v + 3] = y.w;
                 }
-                if (R % 16) {                             // last group of 8 rows: an 8-byte load
-                    const uint2 x = *reinterpret_cast<const uint2 *>(pa + (R / 16) * T);
-                    const uint2 y = *reinterpret_cast<const uint2 *>(pb + (R / 16) * T);
-                    wa[R / 4 - 2] = x.x; wa[R / 4 - 1] = x.y;
-                    wb[R / 4 - 2] = y.x; wb[R / 4 - 1] = y.y;
+                if (RP % 16) {                            // last group of 8 rows: an 8-byte load
+                    const uint2 x = *reinterpret_cast<const uint2 *>(pa + (RP / 16) * T);
+                    const uint2 y = *reinterpret_cast<const uint2 *>(pb + (RP / 16) * T);
+                    wa[RP / 4 - 2] = x.x; wa[RP / 4 - 1] = x.y;
+                    wb[RP / 4 - 2] = y.x; wb[RP / 4 - 1] = y.y;
                 }
                 uint32_t f = fin;                         // B(F) of this lane's top row
                 uint32_t d = hd;
                 uint32_t ylast = 0;
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
+                for (int r = 0; r < RP; ++r) {
                     const uint32_t p = prmt(wa[r / 4], wb[r / 4], pair_sel(r % 4));
                     const uint32_t e_r = __viaddmax_u16x2(E[r], ADD_NEG_E, Ho[r]);
                     const uint32_t x = __viaddmax_u16x2(d, p, e_r);
@@ -234,7 +241,7 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_modes_i16x2(
                     d = Ho[r];
                     E[r] = e_r;
                     Ho[r] = ho;
-                    if (r == R - 1) ylast = y;
+                    if (r == RP - 1) ylast = y;
                 }
                 if (LAST) {                               // lane T-1: ylast = B(H(m, j + 1))
                     if (GLOBAL) {
@@ -248,13 +255,13 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_modes_i16x2(
                 if (OVERLAP && (j == na - 1 || j == nb - 1)) {   // column n of a half: its rows here
                     uint32_t cm = Ho[0];
 #pragma unroll
-                    for (int r = 1; r < R; ++r) cm = vmax2(cm, Ho[r]);
+                    for (int r = 1; r < RP; ++r) cm = vmax2(cm, Ho[r]);
                     cm += OO;                             // B(H) = B(Ho) + o, no carry
                     const uint32_t mask = (j == na - 1 ? 0xffffu : 0u) | (j == nb - 1 ? 0xffff0000u : 0u);
                     mcol = vmax2(mcol, cm & mask);
                 }
                 hd = hin;
-                pub_h = Ho[R - 1];
+                pub_h = Ho[RP - 1];
                 pub_f = f;
                 pub_c = cin;
                 if (!LAST && k == T - 1)                  // 4 consecutive columns fill one 32-byte sector
@@ -355,8 +362,19 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_modes_i16x2(
             }
             for (; s < steps; ++s) step(s);
         };
-        for (int pass = 0; pass + 1 < npass; ++pass) run_pass(pass, std::false_type());
-        run_pass(npass - 1, std::true_type());
+        using RFull = std::integral_constant<int, R>;
+        for (int pass = 0; pass + 1 < npass; ++pass) run_pass(pass, std::false_type(), RFull());
+        bool ran = false;
+        if constexpr (R > 8) {
+            if (rest == T * 8) { run_pass(npass - 1, std::true_type(), std::integral_constant<int, 8>()); ran = true; }
+        }
+        if constexpr (R > 16) {
+            if (rest == T * 16) { run_pass(npass - 1, std::true_type(), std::integral_constant<int, 16>()); ran = true; }
+        }
+        if constexpr (R > 24) {
+            if (rest == T * 24) { run_pass(npass - 1, std::true_type(), std::integral_constant<int, 24>()); ran = true; }
+        }
+        if (!ran) run_pass(npass - 1, std::true_type(), RFull());
 
         const uint32_t rlast = __shfl_sync(0xffffffffu, res, T - 1, T);   // lane T-1 holds row m
         if (OVERLAP) {
@@ -380,8 +398,11 @@ cudaError_t launch_one(const Mode16Args &a, int grid, cudaStream_t s) {
     constexpr int PAIRS_PER_CTA = kCtaThreads / T;
     const int64_t pairs = a.pair_end - a.pair_begin;
     if (pairs <= 0) return cudaSuccess;
-    if (!a.chunk_counter || grid <= 0 || a.m <= 0 || (a.m + a.virt_rows) % (T * R) != 0 ||
-        a.virt_rows < 0 || a.virt_rows >= T * R || ((a.m + a.virt_rows) > T * R && !a.boundary))
+    // m + virt_rows: whole strips of T*R rows, then a last one of T x 8, 16, 24 or R rows
+    const int64_t padded = int64_t(a.m) + a.virt_rows;
+    const int64_t last_rows = padded - (padded - 1) / (T * R) * (T * R);
+    if (!a.chunk_counter || grid <= 0 || a.m <= 0 || a.virt_rows < 0 || a.virt_rows >= T * R ||
+        last_rows % (T * 8) != 0 || (padded > T * R && !a.boundary))
         return cudaErrorInvalidValue;
     const int64_t chunks = (pairs + PAIRS_PER_CTA - 1) / PAIRS_PER_CTA;
     k_modes_i16x2<T, R, MODE><<<unsigned(std::min<int64_t>(grid, chunks)), kCtaThreads, 0, s>>>(a);

@@ -146,6 +146,23 @@ def test_packed_shapes_and_virtual_rows(gpu, mode, rows):
     assert st["long_cells"] == 0
 
 
+@pytest.mark.parametrize("rows", [16, 24, 32])
+@pytest.mark.parametrize("mode", sorted(MODES))
+def test_packed_last_strip_heights(gpu, mode, rows):
+    """The last strip takes the fewest rows per lane (8, 16, 24 or all) that
+    cover the rest, with the virtual rows on top making up the difference:
+    remainders at and around every 8-row boundary, in one strip and after
+    one and two full strips, equal the oracle."""
+    rng = np.random.default_rng(520 + rows + MODES[mode])
+    tr = 8 * rows
+    db = synth.seqset_from_lengths(rng, np.concatenate([rng.integers(1, 400, 90), [0, 1, 5, 300]]))
+    rems = sorted({r for b in range(8, rows + 1, 8) for r in (8 * b - 1, 8 * b, 8 * b + 1) if 1 <= r <= tr} | {1})
+    qs = synth.seqset_from_lengths(rng, rems + [tr + r for r in rems[::2]] + [2 * tr + r for r in rems[1::3]])
+    _, st = _check(gpu, qs, db, synth.blosum62(), 10, 1, mode, lanes=8, rows_per_lane=rows)
+    assert st["precision_used"] == gpu.SW_PREC_I16
+    assert st["long_cells"] == 0
+
+
 @pytest.mark.parametrize("mode", sorted(MODES))
 @pytest.mark.parametrize("o,e", [(10, 1), (3, 7), (0, 2), (5, 5)])
 def test_packed_equals_int32_and_oracle(gpu, mode, o, e):
