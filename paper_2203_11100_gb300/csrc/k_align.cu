@@ -38,6 +38,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "../../include/swdb.h"
 #include "swdb_internal.cuh"
 
@@ -128,6 +130,7 @@ __device__ __forceinline__ void st_release_cta(int *p, int v) {
 // in memory, so a writer never waits for a reader, and strips run as a
 // wavefront about kPub + 31 columns apart.  Each wait is bounded; when it
 // runs out the pair's status records a timeout and the CTA stops waiting.
+template <int MODE>
 __global__ void __launch_bounds__(kFW * 32) k_align_fwd(const AlignArgs a) {
     __shared__ int pub[kFW];
     __shared__ int abort_flag;
@@ -138,8 +141,8 @@ __global__ void __launch_bounds__(kFW * 32) k_align_fwd(const AlignArgs a) {
     const AlignPairDev P = a.pairs[blockIdx.x];
     AlignResultDev *R = a.results + blockIdx.x;
     const int m = P.m, n = P.n;
-    const int mode = a.mode;
-    const bool local = mode == SW_ALIGN_LOCAL;
+    constexpr int mode = MODE;              // a.mode, fixed per instance: no mode tests per cell
+    constexpr bool local = mode == SW_ALIGN_LOCAL;
     if (m <= 0 || n <= 0) {
         if (threadIdx.x == 0) {
             // only the first row or column: global ends at (m, n), semi-global
@@ -273,6 +276,7 @@ __global__ void __launch_bounds__(kFW * 32) k_align_fwd(const AlignArgs a) {
     }
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(32) k_align_bwd(const AlignArgs a) {
     __shared__ __align__(16) int32_t prof[kProfRows][kStrip];
     __shared__ int32_t mat[kProfRows * kProfRows];
@@ -281,8 +285,8 @@ __global__ void __launch_bounds__(32) k_align_bwd(const AlignArgs a) {
     AlignResultDev *R = a.results + blockIdx.x;
     for (int i = lane; i < kProfRows * kProfRows; i += 32) mat[i] = a.mat[i];
     const int m = P.m, n = P.n;
-    const int mode = a.mode;
-    const bool local = mode == SW_ALIGN_LOCAL;
+    constexpr int mode = MODE;              // a.mode, fixed per instance: no mode tests per cell
+    constexpr bool local = mode == SW_ALIGN_LOCAL;
     if (local && (R->score <= 0 || m <= 0 || n <= 0)) return;   // empty alignment, written by the forward pass
     const uint8_t *q = a.queries + P.q_off;
     const uint8_t *tb = target_base(a.db, P.t_sorted);
@@ -426,8 +430,18 @@ __global__ void __launch_bounds__(32) k_align_bwd(const AlignArgs a) {
 cudaError_t launch_align(const AlignArgs &a, int which, cudaStream_t s) {
     if (a.n_pairs <= 0) return cudaSuccess;
     if (a.n_pairs > 0x7fffffff) return cudaErrorInvalidValue;
-    if (which == 0) k_align_fwd<<<unsigned(a.n_pairs), kFW * 32, 0, s>>>(a);
-    else k_align_bwd<<<unsigned(a.n_pairs), 32, 0, s>>>(a);
+    auto go = [&](auto mode_c) {
+        constexpr int M = decltype(mode_c)::value;
+        if (which == 0) k_align_fwd<M><<<unsigned(a.n_pairs), kFW * 32, 0, s>>>(a);
+        else k_align_bwd<M><<<unsigned(a.n_pairs), 32, 0, s>>>(a);
+    };
+    switch (a.mode) {
+        case SW_ALIGN_LOCAL: go(std::integral_constant<int, SW_ALIGN_LOCAL>()); break;
+        case SW_ALIGN_GLOBAL: go(std::integral_constant<int, SW_ALIGN_GLOBAL>()); break;
+        case SW_ALIGN_SEMIGLOBAL: go(std::integral_constant<int, SW_ALIGN_SEMIGLOBAL>()); break;
+        case SW_ALIGN_OVERLAP: go(std::integral_constant<int, SW_ALIGN_OVERLAP>()); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
