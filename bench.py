@@ -86,7 +86,9 @@ def parse_args(argv=None):
     p.add_argument("--serve-db-scale", type=float, default=0.1,
                    help="fraction of the 20M-sequence serving database (0.1 = 2M sequences)")
     p.add_argument("--serve-requests", type=int, default=96)
-    p.add_argument("--serve-max-batch", type=int, default=16)
+    p.add_argument("--serve-max-batch", type=int, default=32,
+                   help="most requests per batch (the server's default; larger batches pair queries of closer "
+                        "lengths)")
     p.add_argument("--serve-point-requests", type=int, default=0,
                    help="requests per Poisson load point (0 = half of --serve-requests)")
     p.add_argument("--serve-check", type=int, default=8,

@@ -275,8 +275,9 @@ int choose_batch_shape(const ShapeTable &table, int64_t m) {
     double best = 1e300;
     int arg = 0;
     for (int i = 0; i < int(table.size()); ++i) {
-        const int64_t tr = int64_t(table[size_t(i)].lanes) * table[size_t(i)].rows;
-        const double t = double((m + tr - 1) / tr * tr) / table[size_t(i)].gcups;
+        // the batched kernel shapes its last strip like the inter-task kernel
+        const double t = double(inter_padded_rows(m, table[size_t(i)].lanes, table[size_t(i)].rows)) /
+                         table[size_t(i)].gcups;
         if (t < best) {
             best = t;
             arg = i;

@@ -99,18 +99,24 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_batch_i16x2(
         const int Lw = __reduce_max_sync(0xffffffffu, Lp);
         uint32_t mx = BZERO2;
 
-        for (int pass = 0; pass < npass; ++pass) {
+        // One pass (strip) of the pair: rows pass*TR .. pass*TR + T*RP - 1, RP
+        // rows per lane.  Every pass but the last is a full strip (RP = R); the
+        // last one takes the fewest rows per lane (a multiple of 8) that cover
+        // the rest of the longer query, which cuts the padded rows it computes.
+        auto run_pass = [&](const int pass, auto rp_c) {
+            constexpr int RP = decltype(rp_c)::value;
+            constexpr int TRP = T * RP;
             __syncthreads();
             // Profile strip, word layout [a][row group v][lane k][row%4]: lane k's
-            // rows 4v..4v+3 are one 16-byte slot at a*TR + v*4T + 4k (quarter-warp
+            // rows 4v..4v+3 are one 16-byte slot at a*TRP + v*4T + 4k (quarter-warp
             // lanes read consecutive slots).  Word = S(qa_i, a)+o | S(qb_i, a)+o << 16.
-            for (int w = tid; w < kProfRows * TR; w += kCtaThreads) {
-                const int res = w / TR;
-                const int rem = w % TR;
+            for (int w = tid; w < kProfRows * TRP; w += kCtaThreads) {
+                const int res = w / TRP;
+                const int rem = w % TRP;
                 const int v = rem / (4 * T);
                 const int rem2 = rem % (4 * T);
                 const int kk = rem2 >> 2;
-                const int row = pass * TR + kk * R + v * 4 + (rem2 & 3);
+                const int row = pass * TR + kk * RP + v * 4 + (rem2 & 3);
                 int lo = -128, hi = -128;
                 if (row < ma) {
                     const int c = a.queries[qa0 + row];
@@ -123,11 +129,11 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_batch_i16x2(
                 prof[w] = (uint32_t(lo) & 0xffffu) | (uint32_t(hi) << 16);
             }
             __syncthreads();
-            if (Lw == 0) continue;
+            if (Lw == 0) return;
 
-            uint32_t E[R], Ho[R];
+            uint32_t E[RP], Ho[RP];
 #pragma unroll
-            for (int r = 0; r < R; ++r) { E[r] = BNEG_O2; Ho[r] = BNEG_O2; }
+            for (int r = 0; r < RP; ++r) { E[r] = BNEG_O2; Ho[r] = BNEG_O2; }
             uint32_t hd = BNEG_O2;
             uint32_t pub_h = BNEG_O2, pub_f = BNEG_O2, pub_c = 0;
             const bool last_pass = (pass + 1 == npass);
@@ -147,13 +153,13 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_batch_i16x2(
             }
             const int steps = Lw + T - 1;
 
-            // The cell work of one column step for this lane's R rows (both
+            // The cell work of one column step for this lane's RP rows (both
             // queries of the pair in the two halves; cin = the sequence's code).
             auto cells = [&](const uint32_t hin, const uint32_t fin, const uint32_t cin) {
-                const uint4 *pp = reinterpret_cast<const uint4 *>(prof + cin * TR + k * 4);
-                uint32_t P[R];
+                const uint4 *pp = reinterpret_cast<const uint4 *>(prof + cin * TRP + k * 4);
+                uint32_t P[RP];
 #pragma unroll
-                for (int v = 0; v < R / 4; ++v) {
+                for (int v = 0; v < RP / 4; ++v) {
                     const uint4 x = pp[v * T];
                     P[4 * v + 0] = x.x; P[4 * v + 1] = x.y; P[4 * v + 2] = x.z; P[4 * v + 3] = x.w;
                 }
@@ -161,7 +167,7 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_batch_i16x2(
                 uint32_t d = hd;
                 uint32_t yprev = 0;
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
+                for (int r = 0; r < RP; ++r) {
                     const uint32_t e_r = __viaddmax_u16x2(E[r], ADD_NEG_E, Ho[r]);
                     const uint32_t x = __viaddmax_u16x2(d, P[r], e_r);
                     const uint32_t y = __vimax3_u16x2(f, x, BZERO2);
@@ -174,7 +180,7 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_batch_i16x2(
                     yprev = y;
                 }
                 hd = hin;
-                pub_h = Ho[R - 1];
+                pub_h = Ho[RP - 1];
                 pub_f = f;
                 pub_c = cin;
             };
@@ -266,6 +272,22 @@ __global__ void __launch_bounds__(kCtaThreads, (R <= 16 ? 3 : 2)) k_batch_i16x2(
                 }
             }
             for (; s < steps; ++s) step(s);
+        };
+        using RFull = std::integral_constant<int, R>;
+        for (int pass = 0; pass + 1 < npass; ++pass) run_pass(pass, RFull());
+        if (npass > 0) {
+            const int rest = m - (npass - 1) * TR;             // rows of the last strip, 1 .. TR
+            bool ran = false;
+            if constexpr (R > 8) {
+                if (rest <= T * 8) { run_pass(npass - 1, std::integral_constant<int, 8>()); ran = true; }
+            }
+            if constexpr (R > 16) {
+                if (!ran && rest <= T * 16) { run_pass(npass - 1, std::integral_constant<int, 16>()); ran = true; }
+            }
+            if constexpr (R > 24) {
+                if (!ran && rest <= T * 24) { run_pass(npass - 1, std::integral_constant<int, 24>()); ran = true; }
+            }
+            if (!ran) run_pass(npass - 1, RFull());
         }
 
 #pragma unroll

@@ -475,8 +475,9 @@ def test_last_strip_heights(gpu, lanes, rows):
 
 @pytest.mark.parametrize("lanes,rows", [(8, 32), (8, 24), (8, 16), (16, 32)])
 def test_batched_last_strip_heights(gpu, lanes, rows):
-    """Batched pairs whose longer query leaves a remainder at and around every
-    8-row boundary of the last strip (one strip and several) equal the oracle."""
+    """The batched kernel sizes a pair's last strip by its longer query, the
+    fewest rows per lane (a multiple of 8) that cover the rest: pairs whose
+    remainders sit at and around every such boundary equal the oracle."""
     rng = np.random.default_rng(77 + lanes + rows)
     db = _db(rng, 120, 1, 500)
     tr = lanes * rows
