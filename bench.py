@@ -438,10 +438,12 @@ def run_ours(args, dist: Dist):
         achieved = inter_cells / (inter_ms * 1e-3) / 1e9 if inter_ms > 0 else 0.0
         launch_ms = inter_ms / max(inter_launches, 1)
         extra = {}
-        if local and long_ms > inter_ms and not args.graph:
-            # the intra-task kernel (long sequences, side stream) dominates the step
+        long_cells = float(sum(s["long_cells"] for s in st_all))
+        if local and long_cells > inter_cells and long_ms > 0 and not args.graph:
+            # the intra-task kernel (long sequences, side stream) does most of the cells
             kernel, basis_note = "k_intra_i16x2", " (intra-task kernel: long sequences, on the side stream)"
-            long_cells = float(sum(s["long_cells"] for s in st_all))
+            ops_per_cell = DPX_OPS_PER_CELL
+            peak = rate_dpx * sms * mhz * 1e6 / ops_per_cell / 1e9
             achieved = long_cells / (long_ms * 1e-3) / 1e9
             launch_ms = long_ms / max(len(st_all), 1)
             extra["inter_task"] = {"kernel": "k_batch_i16x2" if batched else "k_inter_i16x2",
