@@ -256,9 +256,12 @@ constexpr int kLongInterRows = 256;
 // query taller than one strip sends longer sequences to the int32 kernel.
 constexpr int32_t kMode16Cols = 4096;
 
-// Batched-kernel shapes (lanes, rows) with measured rates (GCUPS, GB300);
-// each query pair takes the one with the least predicted time.
-constexpr ShapeRate kBatchShapes[] = {{8, 16, 5000.0}, {8, 24, 5850.0}, {8, 32, 5850.0}};
+// Batched-kernel shapes (lanes, rows) with measured rates (GCUPS, GB300: the
+// autotuner's padding-free probe on the 565,000- and 20M-sequence databases);
+// each query pair takes the one with the least predicted time.  With the
+// flexible last strip every 8-lane shape pads a pair to a multiple of 64 rows,
+// so the rate alone decides between them.
+constexpr ShapeRate kBatchShapes[] = {{8, 16, 6400.0}, {8, 24, 6980.0}, {8, 32, 7040.0}};
 
 ShapeTable batch_shapes(const sw_db *db) {
     if (db->tuning.n_batched > 0) {
