@@ -389,7 +389,6 @@ def run_ours(args, dist: Dist):
     t_ms, cells_all, gcups = combine_ranks(dist, local_ms, cells_step * args.steps)
 
     inter_ms = sum(s["inter_ms"] for s in st_all)
-    inter_launches = sum(s["inter_launches"] for s in st_all)
     launches = sum(s["launches"] for s in st_all)
     if args.graph:
         # A replayed graph reports no per-launch events: count the kernels of
@@ -423,38 +422,10 @@ def run_ours(args, dist: Dist):
         mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
         local = args.alignment == "local"
         packed = local or st0["precision_used"] == swdb.SW_PREC_I16
-        ops_per_cell = DPX_OPS_PER_CELL if local else (MODES16_OPS_PER_CELL if packed else I32_DPX_OPS_PER_CELL)
-        kernel = "k_inter_i16x2" if local else ("k_modes_i16x2" if packed else "k_modes_i32")
-        basis_note = ("" if local else
-                      " (int16x2 pairs: E, F, H and the profile permute, no running max)" if packed else
-                      " (int32: E, F and H, one cell per operation)")
         batched = st0["mode_used"] == swdb.SW_MODE_BATCHED
-        if local and batched:
-            ops_per_cell, kernel = BATCH_OPS_PER_CELL, "k_batch_i16x2"
-            basis_note = " (query pairs: one ready int16x2 profile word per row, no permute)"
-        peak = rate_dpx * sms * mhz * 1e6 / ops_per_cell / 1e9
+        roof = step_roofline(st_all, args.alignment, packed, batched, rate_dpx, sms, mhz,
+                             cells_step * args.steps / (t_ms * 1e-3) / 1e9, args.graph)
         ceiling = rate_cells * sms * mhz * 1e6 / 1e9
-        inter_cells = float(sum(s["inter_cells"] for s in st_all))
-        achieved = inter_cells / (inter_ms * 1e-3) / 1e9 if inter_ms > 0 else 0.0
-        launch_ms = inter_ms / max(inter_launches, 1)
-        extra = {}
-        long_cells = float(sum(s["long_cells"] for s in st_all))
-        if local and long_cells > inter_cells and long_ms > 0 and not args.graph:
-            # the intra-task kernel (long sequences, side stream) does most of the cells
-            kernel, basis_note = "k_intra_i16x2", " (intra-task kernel: long sequences, on the side stream)"
-            ops_per_cell = DPX_OPS_PER_CELL
-            peak = rate_dpx * sms * mhz * 1e6 / ops_per_cell / 1e9
-            achieved = long_cells / (long_ms * 1e-3) / 1e9
-            launch_ms = long_ms / max(len(st_all), 1)
-            extra["inter_task"] = {"kernel": "k_batch_i16x2" if batched else "k_inter_i16x2",
-                                   "achieved": inter_cells / (inter_ms * 1e-3) / 1e9 if inter_ms > 0 else 0.0}
-            # the two kernels share the SMs for most of the step, so each one's
-            # event time includes the other's work: the whole step against the peak
-            extra["both_kernels_frac_of_peak"] = cells_step * args.steps / (t_ms * 1e-3) / 1e9 / peak
-        if args.graph:
-            # Replayed graphs carry no per-kernel events: the rate is the whole
-            # step's (every kernel of the step counted as the scoring kernel's).
-            achieved = gcups
         traffic = traffic_per_launch(args)
         cb = None
         if not args.no_cpu_baseline:
@@ -478,17 +449,10 @@ def run_ours(args, dist: Dist):
                        "cuda_graph": "captured once, replayed every step (roofline achieved = whole step)"
                                      if args.graph else "no",
                        "autotune": tuned if tuned else "off (the library's measured shape tables)"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
-                         "frac": achieved / peak if peak else None,
-                         "traffic": traffic,
-                         "kernel": kernel,
-                         "peak_basis": f"measured {rate_dpx:.1f} DPX ops/SM/cycle x {sms} SMs x "
-                                       f"{mhz:.0f} MHz (median under load) / {ops_per_cell} ops per cell"
-                                       + basis_note,
+            "roofline": {**roof, "traffic": traffic,
                          "register_only_ceiling_gcups": ceiling,
                          "probe_cells_per_sm_cycle": {"int16x2_shipped_sequence": rate_cells,
-                                                      "int8x4_byte_simd": rate_u8x4},
-                         "avg_launch_ms": launch_ms, **extra},
+                                                      "int8x4_byte_simd": rate_u8x4}},
             "cpu_baseline": cb,
             "e2e": {"value": e2e_gcups, "unit": UNIT, "h2d_bytes_per_step": int(w.queries.residues.nbytes),
                     "d2h_bytes_per_step": int(nq * n * 4 + nq * w.top_k * 16), "ms_per_step": e2e_ms / args.e2e_steps},
@@ -572,6 +536,52 @@ def timed_steps(step, steps: int, warmup: int, stream, dev: int):
     ev1.record(stream)
     torch.cuda.synchronize()
     return ev0.elapsed_time(ev1), st_all, clocks.stop()
+
+
+def step_roofline(st_all, alignment: str, packed: bool, batched: bool, rate_dpx: float, sms: int, mhz: float,
+                  step_gcups: float, graph: bool) -> dict:
+    """Roofline of a step's dominant kernel: the kernel that computes most of
+    the step's cells (the intra-task launch on the side stream when the long
+    pairs hold most of them, else the main-stream scoring kernel), its own
+    cells over its own CUDA-event time, against the DPX-issue peak for that
+    kernel's ALU operations per cell.  A replayed graph has no per-kernel
+    events, so there the whole step's rate stands in."""
+    local = alignment == "local"
+    if local:
+        if batched:
+            kernel, opc = "k_batch_i16x2", BATCH_OPS_PER_CELL
+            note = " (query pairs: one ready int16x2 profile word per row, no permute)"
+        else:
+            kernel, opc, note = "k_inter_i16x2", DPX_OPS_PER_CELL, ""
+    elif packed:
+        kernel, opc = "k_modes_i16x2", MODES16_OPS_PER_CELL
+        note = " (int16x2 pairs: E, F, H and the profile permute, no running max)"
+    else:
+        kernel, opc, note = "k_modes_i32", I32_DPX_OPS_PER_CELL, " (int32: E, F and H, one cell per operation)"
+    inter_cells = float(sum(s["inter_cells"] for s in st_all))
+    inter_ms = sum(s["inter_ms"] for s in st_all)
+    long_cells = float(sum(s["long_cells"] for s in st_all))
+    long_ms = sum(s["intra_ms"] for s in st_all)
+    inter_rate = inter_cells / (inter_ms * 1e-3) / 1e9 if inter_ms > 0 else 0.0
+    achieved, launch_ms = inter_rate, inter_ms / max(sum(s["inter_launches"] for s in st_all), 1)
+    extra = {}
+    if local and long_cells > inter_cells and long_ms > 0 and not graph:
+        extra["inter_task"] = {"kernel": kernel, "achieved": inter_rate}
+        kernel, opc = "k_intra_i16x2", DPX_OPS_PER_CELL
+        note = " (intra-task kernel: long sequences, on the side stream)"
+        achieved, launch_ms = long_cells / (long_ms * 1e-3) / 1e9, long_ms / max(len(st_all), 1)
+    peak = rate_dpx * sms * mhz * 1e6 / opc / 1e9
+    if "inter_task" in extra:
+        # the two kernels share the SMs for most of the step, so each one's
+        # event time includes the other's work: the whole step against the peak
+        extra["both_kernels_frac_of_peak"] = step_gcups / peak
+    if graph:
+        achieved = step_gcups
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
+            "frac": achieved / peak if peak else None, "kernel": kernel,
+            "peak_basis": f"measured {rate_dpx:.1f} DPX ops/SM/cycle x {sms} SMs x {mhz:.0f} MHz (median under "
+                          f"load) / {opc} ops per cell" + note,
+            "avg_launch_ms": launch_ms, **extra}
 
 
 def kernel_roofline(st_all, family: str, kernel: str, ops_per_cell: float, rate_dpx: float, sms: int,

@@ -1,6 +1,7 @@
 """Host logic of bench.py (CPU only): the launch key and DRAM-traffic record
-lookup behind ``roofline.traffic``, and the reference arm's JSON line (the
-oracle on the host cores)."""
+lookup behind ``roofline.traffic``, the choice of the step's dominant kernel
+and its peak, and the reference arm's JSON line (the oracle on the host
+cores)."""
 import hashlib
 import importlib.util
 import json
@@ -112,3 +113,41 @@ def test_oracle_sample_flags_a_wrong_score():
     # a bounded sample of a larger workload: each query's best hit plus random pairs
     rec = b.oracle_sample(w, torch.from_numpy(want.astype(np.int32)), torch.from_numpy(hits), 1, max_cells=1e6)
     assert rec["bit_exact_vs_gpu"] and rec["what"].startswith("each query's best hit")
+
+
+def _stats(inter_cells, inter_ms, long_cells, intra_ms, launches=20):
+    return {"inter_cells": inter_cells, "inter_ms": inter_ms, "long_cells": long_cells, "intra_ms": intra_ms,
+            "inter_launches": launches}
+
+
+def test_step_roofline_names_the_kernel_that_computes_most_cells():
+    b = _bench()
+    peak_275 = 64.0 * 152 * 2070.0 * 1e6 / 2.75 / 1e9
+    # plain local step: the inter-task kernel, its cells over its own event time
+    r = b.step_roofline([_stats(6e12, 1000.0, 2e11, 60.0)] * 2, "local", True, False, 64.0, 152, 2070.0, 5900.0,
+                        False)
+    assert r["kernel"] == "k_inter_i16x2"
+    assert r["achieved"] == pytest.approx(6e12 * 2 / 2.0 / 1e9)
+    assert r["peak"] == pytest.approx(peak_275) and r["avg_launch_ms"] == pytest.approx(50.0)
+    # long pairs hold most cells: the intra-task kernel on its own 2.75-op peak, even in the
+    # batched form, with the main-stream kernel and the whole step beside it
+    r = b.step_roofline([_stats(1e12, 1200.0, 4.7e12, 1000.0)], "local", True, True, 64.0, 152, 2070.0, 5700.0,
+                        False)
+    assert r["kernel"] == "k_intra_i16x2" and r["peak"] == pytest.approx(peak_275)
+    assert r["achieved"] == pytest.approx(4.7e12 / 1.0 / 1e9)
+    assert r["inter_task"]["kernel"] == "k_batch_i16x2"
+    assert r["both_kernels_frac_of_peak"] == pytest.approx(5700.0 / peak_275)
+    # an intra-task launch whose event time spans the step but holds few cells is not dominant
+    r = b.step_roofline([_stats(2.5e14, 37000.0, 1e12, 37800.0, 1)], "local", True, True, 64.0, 152, 2070.0,
+                        6900.0, False)
+    assert r["kernel"] == "k_batch_i16x2"
+    assert r["peak"] == pytest.approx(64.0 * 152 * 2070.0 * 1e6 / 2.25 / 1e9)
+    assert "inter_task" not in r
+    # alignment modes: packed and int32 peaks; a replayed graph reports the step's rate
+    assert b.step_roofline([_stats(6e12, 950.0, 0.0, 0.0)], "global", True, False, 64.0, 152, 2070.0, 6300.0,
+                           False)["kernel"] == "k_modes_i16x2"
+    r = b.step_roofline([_stats(6e12, 3000.0, 0.0, 0.0)], "overlap", False, False, 64.0, 152, 2070.0, 1990.0,
+                        False)
+    assert r["kernel"] == "k_modes_i32" and r["peak"] == pytest.approx(64.0 * 152 * 2070.0 * 1e6 / 3.0 / 1e9)
+    r = b.step_roofline([_stats(0.0, 0.0, 0.0, 0.0)], "local", True, False, 64.0, 152, 2070.0, 6000.0, True)
+    assert r["achieved"] == 6000.0
