@@ -211,8 +211,10 @@ int sw_db_get_info(const sw_db *db, sw_db_info *out);
  * Section 3.2, and whose results depend on the work-group size, Section
  * 4.2).  sw_search picks, per query, the launch shape of the inter-task
  * kernel (plain form) or of the batched kernel (batched form: per query
- * pair) with the least predicted time, ceil(m / (lanes*rows)) * lanes*rows
- * / gcups, from a table of shapes and their cell rates; the library's
+ * pair) with the least predicted time, padded rows / gcups, from a table of
+ * shapes and their cell rates; the padded rows of a query of m rows are its
+ * full strips of lanes*rows rows plus a last strip of lanes x (the fewest
+ * rows per lane, a multiple of 8, that cover the rest).  The library's
  * tables hold rates measured on GB300.  An autotuner that measures the rates
  * on the caller's own GPU and database installs its tables here, with the
  * inter/intra-task length cutoff, the intra-task rows per lane and the form
