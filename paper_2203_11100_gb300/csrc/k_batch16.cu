@@ -14,7 +14,8 @@
 // A chunk is 256/T consecutive sorted sequences, one per subwarp of T lanes.
 // Queries longer than one strip (T*R rows) take several passes; the strip
 // boundary of each subwarp goes to a scratch region owned by the CTA slot,
-// reused tile after tile, so it stays in L2.
+// reused tile after tile, so it stays in L2.  A pair's last pass takes the
+// fewest rows per lane (8, 16, 24 or R) that cover its longer query.
 //
 // Saturated (query, sequence) results are appended to per-query lists, with
 // the two sequences of a database pair merged into one entry (pair*4 + mask)
