@@ -30,7 +30,8 @@
 //   whole strips, the last of which may be short (8, 16 or 24 rows per lane
 //   instead of R: the fewest that cover the rest), and row m is always the
 //   last row of the last lane: the last-row maximum and H(m, n) then read one
-//   fixed register.  The virtual rows reproduce the mode's first row exactly:
+//   fixed register.  The virtual
+//   rows reproduce the mode's first row exactly:
 //     semi-global, overlap: S = 0 and H(v, 0) = 0 give H(v, j) = 0 and
 //                           F(P + 1, j) = -o, as below a first row of zeros;
 //     global:               S = -min(o, e), H(v, 0) = -(o - min(o, e)) and
